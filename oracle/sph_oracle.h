@@ -1,0 +1,121 @@
+/*
+ * Serial FP64 CPU oracle for the weakly-compressible SPH hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header or constant table with the CUDA library; the two are independent
+ * restatements of the same method so that one can check the other.
+ *
+ * The method (the paper names the pieces; the equations are the published
+ * SPHinXsys WCSPH forms, see the per-function comments in sph_oracle.c):
+ *   - cell-linked list by cell key, stable sort, reorder and CSR cell offsets
+ *     (paper, section "Cell linked-list, direct search and sorting");
+ *   - direct search: kernel values recomputed from current positions for all
+ *     particles of the 3^d neighbouring cells (same section);
+ *   - Wendland C2 kernel, density summation with free-surface clamp,
+ *     viscous force, Riemann-based pressure and density relaxation, static
+ *     wall particles with a mirrored Riemann state, and the dual
+ *     (advection / acoustic) time-step criteria.
+ *
+ * Layout conventions:
+ *   positions / velocities passed in or out are n*dim doubles, particle-major
+ *   (x0,y0[,z0],x1,...), in USER order (the order given to set_particles).
+ */
+#ifndef SPH_ORACLE_H
+#define SPH_ORACLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct osim osim;
+
+/* --- kernel function (Wendland C2) ------------------------------------- */
+double osph_alpha(int dim, double h);
+double osph_W(int dim, double h, double r);
+double osph_dW(int dim, double h, double r);
+/* reference number density: sum of W over an unperturbed lattice of spacing dp,
+ * self included. */
+double osph_sigma0(int dim, double dp, double h);
+
+/* --- acoustic Riemann solver (fluid-fluid interface) ------------------- */
+void osph_riemann(double pL, double pR, double rhoL, double rhoR, double UL,
+                  double UR, double c0, double* Pstar, double* Ustar);
+
+/* --- simulation ---------------------------------------------------------- */
+osim* osph_create(int dim, const double lo[3], const double hi[3], double dp,
+                  double h, double rho0, double c0, double mu, double U_ref,
+                  const double g[3]);
+void osph_destroy(osim* s);
+
+/* kind 0 = fluid, 1 = wall.  vel / rho may be NULL (0 / rho0).  Wall velocity
+ * and density are ignored (static wall).  Returns 0 on success. */
+int osph_set_particles(osim* s, int kind, long n, const double* pos,
+                       const double* vel, const double* rho);
+/* set the carried density rate (user order, n values); default 0 */
+int osph_set_drho(osim* s, const double* drho);
+
+/* the full schedule: n acoustic steps */
+int osph_step(osim* s, long n);
+
+/* individual stages, for tests */
+void osph_rebuild(osim* s);
+void osph_density_summation(osim* s);
+void osph_viscous(osim* s);
+double osph_vmax2(const osim* s);
+void osph_half1(osim* s, double dt);
+void osph_pressure_relaxation(osim* s, double dt);
+void osph_half2(osim* s, double dt);
+
+/* field ids for osph_get_field */
+enum {
+  OSPH_POS = 0,    /* dim */
+  OSPH_VEL = 1,    /* dim */
+  OSPH_RHO = 2,    /* 1 */
+  OSPH_P = 3,      /* 1 */
+  OSPH_DRHO = 4,   /* 1 */
+  OSPH_ACC = 5,    /* dim: pressure acceleration of the last pressure stage */
+  OSPH_APRIOR = 6, /* dim: g + viscous acceleration */
+  OSPH_SIGMA = 7   /* 1: kernel sum of the last density summation */
+};
+/* copy a field out in user order; returns the component count or -1 */
+int osph_get_field(const osim* s, int field, double* out);
+
+/* scalars: t, tau, dt_ad, dt_ac, then n_ac, n_adv, flags */
+void osph_get_scalars(const osim* s, double* t, double* tau, double* dt_ad,
+                      double* dt_ac, long* n_ac, long* n_adv, int* flags);
+long osph_n(const osim* s);
+long osph_nw(const osim* s);
+long osph_ncell(const osim* s);
+void osph_grid(const osim* s, double* cs, long nc[3]);
+
+/* sorted state of the last rebuild (storage order): keys[n], perm[n]
+ * (storage index k came from pre-sort index perm[k]), ids[n] (user id of
+ * storage slot k), cell_begin[ncell+1].  Any pointer may be NULL. */
+void osph_neighbour_state(const osim* s, uint32_t* keys, uint32_t* perm,
+                          uint32_t* ids, uint32_t* cell_begin);
+/* same for the wall set (sorted once, when set) */
+void osph_wall_state(const osim* s, uint32_t* keys, uint32_t* ids,
+                     uint32_t* cell_begin);
+
+/* per fluid particle (user order): accepted fluid neighbours (self excluded),
+ * accepted wall neighbours, and an order-free hash of the accepted ids.
+ * brute = 1 scans all particles (O(N^2)) instead of the cell list. */
+void osph_neighbour_stats(const osim* s, int brute, uint32_t* cnt_f,
+                          uint32_t* cnt_w, uint64_t* hash);
+
+/* diagnostics: surge front (max x over fluid) and kinetic energy */
+void osph_front_ke(const osim* s, double* front, double* ke);
+
+/* sampled evaluation at full size: for m fluid particles given by user id,
+ * the kernel sum (density summation) with the current cell list. */
+void osph_sample_sigma(const osim* s, long m, const uint32_t* user_ids,
+                       double* sigma);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,72 @@
+"""Sensitivity of the oracle's pins: each plausible mistake below (a flipped
+sign, a dropped factor, a swapped index or operand) is planted in a copy of
+the oracle source on the CPU, compiled, and the pin tests must fail on it.
+The mutated copies live in a temporary folder and are loaded through the
+oracle loader's override variable; the real oracle is untouched."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
+PIN_FILES = ["tests/test_oracle_kernel.py", "tests/test_oracle_neighbours.py",
+             "tests/test_oracle_physics.py"]
+
+_WALL_P = ("double UR = -UL;\n        double Ps, Us;\n        osph_riemann(s->p[i], pw, s->rho[i], "
+           "rhow, UL, UR, c0, &Ps, &Us);\n        double f")
+MUTATIONS = {
+    "riemann_ustar_sign": ("*Ustar = 0.5 * (UL + UR) + (pL - pR)",
+                           "*Ustar = 0.5 * (UL + UR) + (pR - pL)"),
+    "riemann_limiter_direction": ("double jump = UL - UR;", "double jump = UR - UL;"),
+    "riemann_rho_bar": ("double rho_bar = 0.5 * (rhoL + rhoR);", "double rho_bar = rhoL;"),
+    "pressure_volume_index": ("double f = Ps * (s->m / s->rho[j])",
+                              "double f = Ps * (s->m / s->rho[i])"),
+    "pressure_direction": ("for (int k = 0; k < 3; ++k) a[k] += f * e[k];",
+                           "for (int k = 0; k < 3; ++k) a[k] -= f * e[k];"),
+    "wall_gravity_sign": ("gdot += (s->xw[w][k] - s->x[i][k]) * s->g[k];",
+                          "gdot += (s->x[i][k] - s->xw[w][k]) * s->g[k];"),
+    "wall_mirror_velocity": (_WALL_P, _WALL_P.replace("double UR = -UL;", "double UR = UL;")),
+    "continuity_sign": ("sum += (s->m / s->rho[j]) * osph_dW(s->dim, s->h, r) * (UL - Us);",
+                        "sum += (s->m / s->rho[j]) * osph_dW(s->dim, s->h, r) * (Us - UL);"),
+    "viscous_operands": ("a[k] += coef * (s->v[i][k] - s->v[j][k]);",
+                         "a[k] += coef * (s->v[j][k] - s->v[i][k]);"),
+    "viscous_regulariser": ("osph_dW(s->dim, s->h, r) / (r + eps);\n        for (int k = 0; k < 3; ++k) a[k] += coef * (s->v[i][k]",
+                            "osph_dW(s->dim, s->h, r) / (r + eps) / r;\n        for (int k = 0; k < 3; ++k) a[k] += coef * (s->v[i][k]"),
+    "half_step_drift": ("for (int k = 0; k < s->dim; ++k) s->x[i][k] += 0.5 * dt * s->v[i][k];\n  }",
+                        "for (int k = 0; k < s->dim; ++k) s->x[i][k] += dt * s->v[i][k];\n  }"),
+    "kick_prior_sign": ("s->v[i][k] += dt * (s->acc[i][k] + s->aprior[i][k]);",
+                        "s->v[i][k] += dt * (s->acc[i][k] - s->aprior[i][k]);"),
+    "summation_without_self": (
+        "        double r2 = dist2(s->x[i], s->x[j]);\n        if (r2 >= r2max) continue;\n        sig +=",
+        "        if (j == i) continue;\n        double r2 = dist2(s->x[i], s->x[j]);\n"
+        "        if (r2 >= r2max) continue;\n        sig +="),
+    "summation_no_clamp": ("s->rho[i] = s->rho0 * (ratio > 1.0 ? ratio : 1.0);",
+                           "s->rho[i] = s->rho0 * ratio;"),
+    "kernel_exponent": ("return osph_alpha(dim, h) * t * t * t * t * (2.0 * q + 1.0);",
+                        "return osph_alpha(dim, h) * t * t * t * (2.0 * q + 1.0);"),
+    "key_axis_swap": ("return (uint32_t)((c[2] * s->nc[1] + c[1]) * s->nc[0] + c[0]);",
+                      "return (uint32_t)((c[2] * s->nc[1] + c[0]) * s->nc[0] + c[1]);"),
+    "advection_criterion": ("s->dt_ad = 0.25 * s->h /", "s->dt_ad = 0.35 * s->h /"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    src = open(SRC).read()
+    old, new = MUTATIONS[name]
+    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
+    mutated = src.replace(old, new, 1).replace(
+        '#include "sph_oracle.h"', '#include "%s"' % os.path.join(ROOT, "oracle", "sph_oracle.h"))
+    c = tmp_path / "sph_oracle.c"
+    c.write_text(mutated)
+    so = tmp_path / "liboracle.so"
+    subprocess.run(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o",
+                    str(so), str(c), "-lm"], check=True)
+    env = dict(os.environ, ORACLE_LIB_OVERRIDE=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "-m", "not gpu", *PIN_FILES], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"pins did not catch {name}:\n{r.stdout[-2000:]}"

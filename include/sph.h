@@ -1,0 +1,199 @@
+/*
+ * sph.h - C ABI of the GB300 weakly-compressible SPH hot path (libsph.so).
+ *
+ * What the library computes.  Hu & Guarnieri, "Towards heterogeneous
+ * parallelism for SPHinXsys", describe a three-layer pattern: an outer layer
+ * that defines the problem (global parameters, particles generated from the
+ * geometry), a kernel-shell layer that hands per-particle arrays and scalars to
+ * the computing kernels, and the kernels themselves (section "Implementing
+ * SYCL kernels in SPHinXsys").  The calls below are that outer layer:
+ * sph_create takes the domain, the particle spacing, the smoothing length,
+ * the material and gravity; sph_set_particles hands over the particles;
+ * sph_step advances; sph_get_fields reads results back.  The device work is
+ * the paper's cell-linked list, particle sorting and direct search (section
+ * "Cell linked-list, direct search and sorting") driving the weakly
+ * compressible SPH interactions: Wendland C2 kernel, density summation,
+ * viscous force, Riemann-based pressure and density relaxation, static wall
+ * particles with a mirrored Riemann state, and the dual advection / acoustic
+ * time-step criteria.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an sph_status (0 = SPH_OK) unless stated otherwise.
+ *  - Host arrays are read or written synchronously during the call; the
+ *    caller keeps ownership.  Vector fields are particle-major, n * dim
+ *    doubles (x0, y0[, z0], x1, ...), in USER order: the order given to
+ *    sph_set_particles.
+ *  - Device state belongs to the context.  It is allocated through the
+ *    caller's allocator (or cudaMalloc when none is given) on the
+ *    context's stream, and freed by sph_destroy.
+ *  - Work is queued on the caller's CUDA stream (NULL = legacy default
+ *    stream).  sph_step returns once the work is queued; device-side errors
+ *    (particle outside the domain, non-finite state) are sticky and reported
+ *    by the next call that synchronises (sph_synchronize, sph_get_fields,
+ *    sph_get_scalars, sph_debug_*).
+ *  - There is no CPU path: without a usable CUDA device the calls fail with
+ *    SPH_E_CUDA.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_ctx sph_ctx;
+
+/* Axis-aligned box covered by the cell grid.  Cells have edge 2h (the cut-off
+ * radius); the grid has ceil((hi - lo) / 2h) cells per axis.  Components
+ * beyond dim are ignored.  Particles must stay inside [lo, hi). */
+typedef struct {
+  int dim;       /* 2 or 3 */
+  double lo[3];
+  double hi[3];
+} sph_domain;
+
+/* Weakly-compressible fluid: p = c0^2 (rho - rho0). */
+typedef struct {
+  double rho0;   /* reference density (> 0)                            */
+  double c0;     /* artificial sound speed (> 0)                        */
+  double mu;     /* dynamic viscosity (>= 0)                            */
+  double U_ref;  /* reference speed of the advection criterion (> 0)   */
+} sph_material;
+
+/* Device memory provider.  alloc returns device memory of at least `bytes`
+ * bytes usable on `stream` (NULL on failure: the call then returns
+ * SPH_E_OOM); free releases a block obtained from alloc. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* user);
+  void* user;
+} sph_allocator;
+
+enum sph_precision {
+  SPH_FP64 = 0,  /* every stage in double precision                                    */
+  SPH_MIXED = 1  /* pair interactions in float with float sums; positions, cell keys,
+                    velocity and density state in double                               */
+};
+
+enum sph_status {
+  SPH_OK = 0,
+  SPH_E_INVALID = 1,        /* bad argument, or call out of order                     */
+  SPH_E_OOM = 2,            /* allocation failed                                       */
+  SPH_E_CUDA = 3,           /* CUDA runtime error (see sph_last_error)                 */
+  SPH_E_OUT_OF_DOMAIN = 4,  /* a particle left the box: it was clamped into the edge cell */
+  SPH_E_NONFINITE = 5,      /* a velocity or density became NaN or infinite            */
+  SPH_E_TIMEOUT = 6,        /* sph_synchronize gave up waiting                         */
+  SPH_E_STATE = 7           /* no fluid particles set yet                              */
+};
+
+enum sph_kind { SPH_FLUID = 0, SPH_WALL = 1 };
+
+/* Field bits for sph_get_fields; fields are written one after another in
+ * increasing bit order, each n values (scalars) or n * dim values (vectors). */
+enum sph_field {
+  SPH_F_POS = 1u << 0,    /* position (vector)                                      */
+  SPH_F_VEL = 1u << 1,    /* velocity (vector)                                      */
+  SPH_F_RHO = 1u << 2,    /* density                                                */
+  SPH_F_P = 1u << 3,      /* pressure of the last first half-step                   */
+  SPH_F_DRHO = 1u << 4,   /* density rate of the last density relaxation            */
+  SPH_F_ACC = 1u << 5,    /* pressure acceleration of the last step (vector; needs
+                             SPH_OPT_RECORD_DIAGNOSTICS, else zeros)                 */
+  SPH_F_APRIOR = 1u << 6, /* gravity + viscous acceleration (vector)                */
+  SPH_F_SIGMA = 1u << 7   /* kernel sum of the last density summation (needs
+                             SPH_OPT_RECORD_DIAGNOSTICS, else zeros)                 */
+};
+
+enum sph_option {
+  SPH_OPT_RECORD_DIAGNOSTICS = 1, /* 0/1: also store SPH_F_ACC and SPH_F_SIGMA        */
+  SPH_OPT_USE_GRAPH = 2,          /* 0/1 (default 1): replay each step as a CUDA graph */
+  SPH_OPT_BLOCK = 3,              /* threads per block of the neighbour loops: 64..1024,
+                                     multiple of 32 (default from the tuner)           */
+  SPH_OPT_RADIX_BITS = 4          /* digit width of the radix sort: 4..11 (default 8)  */
+};
+
+/* Creates a context.
+ *   domain   box of the cell grid (see sph_domain)
+ *   dp       initial particle spacing: fluid mass is rho0 dp^dim
+ *   h        smoothing length; cut-off radius 2h, cell edge 2h
+ *   mat      material (see sph_material)
+ *   gravity  body acceleration, dim components used
+ *   precision  SPH_FP64 or SPH_MIXED
+ *   alloc    device allocator, or NULL for cudaMalloc / cudaFree
+ *   stream   cudaStream_t for all work, or NULL
+ *   out      receives the context
+ * Fails with SPH_E_INVALID for dim not 2/3, non-positive dp/h/rho0/c0/U_ref,
+ * negative mu, an empty box, or more than 2^32 - 2 cells. */
+int sph_create(const sph_domain* domain, double dp, double h, const sph_material* mat,
+               const double gravity[3], int precision, const sph_allocator* alloc,
+               void* stream, sph_ctx** out);
+
+/* Sets the particles of one kind (host arrays, n * dim positions).
+ *   SPH_FLUID: vel (n * dim) and rho (n) may be NULL (rest, rho0).  Resets
+ *     time and step counters, the carried density rate and the schedule; the
+ *     particles are binned and sorted once.  User order is the given order.
+ *   SPH_WALL: static wall particles; vel and rho must be NULL.  Sorted once.
+ * n may be 0.  Fails with SPH_E_INVALID on a NULL pos with n > 0. */
+int sph_set_particles(sph_ctx* ctx, int kind, size_t n, const double* pos, const double* vel,
+                      const double* rho);
+
+/* Queues n acoustic steps of the dual-criteria schedule.  Each step: when the
+ * elapsed time of the current advection step has reached its length (or on
+ * the first step), a new advection step begins (length 0.25 h / max(U_ref,
+ * Vmax); cell keys, stable radix sort, reorder, cell offsets, density
+ * summation, viscous force); then the acoustic step of length
+ * 0.6 h / (c0 + Vmax): density and position half-updates, Riemann pressure
+ * relaxation and velocity kick, position half-update and Riemann density
+ * relaxation.  The schedule is decided on the device.  Returns SPH_E_STATE
+ * before fluid particles are set, SPH_E_INVALID for n < 0. */
+int sph_step(sph_ctx* ctx, int n);
+
+/* Waits for queued work and copies the fields selected by `mask` (sph_field
+ * bits) to the host buffer `out`, in user order.  Returns a sticky device
+ * error if one was raised. */
+int sph_get_fields(sph_ctx* ctx, unsigned mask, double* out);
+
+/* Waits and reads the schedule scalars; any pointer may be NULL. */
+int sph_get_scalars(sph_ctx* ctx, double* t, double* dt_ad, double* dt_ac, long* n_ac,
+                    long* n_adv);
+
+/* Number of fluid / wall particles and cells (no synchronisation). */
+size_t sph_count(const sph_ctx* ctx, int kind);
+size_t sph_cell_count(const sph_ctx* ctx);
+
+/* Sorted neighbour structure of the last rebuild (storage order), for parity
+ * checks: keys[n] cell key of each storage slot, perm[n] pre-sort slot of
+ * each storage slot, ids[n] user index of each storage slot,
+ * cell_begin[ncell + 1] CSR offsets.  Any pointer may be NULL. */
+int sph_debug_neighbour_state(sph_ctx* ctx, uint32_t* keys, uint32_t* perm, uint32_t* ids,
+                              uint32_t* cell_begin);
+
+/* Per fluid particle (user order), with the current positions and the cell
+ * list of the last rebuild: accepted fluid neighbours (r < 2h, self
+ * excluded), accepted wall particles, and an order-free fingerprint (sum of
+ * SplitMix64 of the neighbours' user ids, wall ids offset by 2^40).
+ * Positions are compared in double precision in both precision modes. */
+int sph_debug_neighbour_stats(sph_ctx* ctx, uint32_t* cnt_fluid, uint32_t* cnt_wall,
+                              uint64_t* hash);
+
+/* Sets an sph_option; takes effect at the next sph_step. */
+int sph_set_option(sph_ctx* ctx, int option, long value);
+
+/* Waits for the context's queued work, giving up after timeout_s seconds
+ * (<= 0: no limit) with SPH_E_TIMEOUT; the work is not cancelled.  Returns a
+ * sticky device error if one was raised. */
+int sph_synchronize(sph_ctx* ctx, double timeout_s);
+
+/* Text of the last error on this context (never NULL; "" when none). */
+const char* sph_last_error(const sph_ctx* ctx);
+
+/* Frees the context and all its device memory (synchronises first). */
+void sph_destroy(sph_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,700 @@
+// C ABI of the GB300 SPH library (declared in include/sph.h): context
+// management, device memory through the caller's allocator, stream ordering
+// with the caller's stream, CUDA-graph replay of the acoustic step, and field
+// transfer in user order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "sph.h"
+#include "sph_internal.cuh"
+
+using namespace sphgb;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct Block {
+  void* p;
+  size_t bytes;
+};
+
+}  // namespace
+
+struct sph_ctx {
+  Params P{};
+  LaunchCfg L{};
+  DevBuffers B{};
+  int precision = SPH_MIXED;
+  sph_allocator alloc{};
+  bool has_alloc = false;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;  // internal, non-blocking
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  bool use_graph = true;
+  int device = 0;
+  double dp = 0;
+  size_t cap_n = 0;   // capacity of per-particle buffers
+  size_t cap_nw = 0;  // capacity of wall buffers
+  std::vector<Block> fluid_blocks, wall_blocks, fixed_blocks;
+  std::string err;
+  bool fluid_set = false;
+};
+
+namespace {
+
+int set_err(sph_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_err(sph_ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return SPH_OK;
+  return set_err(c, SPH_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                  \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_err(c, e_, #call); \
+  } while (0)
+
+void* dev_alloc(sph_ctx* c, size_t bytes, std::vector<Block>& list) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (c->has_alloc) {
+    p = c->alloc.alloc(bytes, (void*)c->stream, c->alloc.user);
+  } else {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+  }
+  if (p) list.push_back({p, bytes});
+  return p;
+}
+
+void dev_free_list(sph_ctx* c, std::vector<Block>& list) {
+  for (auto& b : list) {
+    if (c->has_alloc)
+      c->alloc.free(b.p, b.bytes, (void*)c->stream, c->alloc.user);
+    else
+      cudaFree(b.p);
+  }
+  list.clear();
+}
+
+void drop_graph(sph_ctx* c) {
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  c->graph_exec = nullptr;
+  c->graph = nullptr;
+}
+
+// Reference number density of the unperturbed lattice (self included).
+double lattice_sigma0(int dim, double dp, double h, double walpha) {
+  const int K = (int)std::ceil(2.0 * h / dp) + 1;
+  const int kz = dim == 3 ? K : 0;
+  double s = 0.0;
+  for (int c = -kz; c <= kz; ++c)
+    for (int b = -K; b <= K; ++b)
+      for (int a = -K; a <= K; ++a) {
+        const double r = dp * std::sqrt((double)(a * a + b * b + c * c));
+        const double q = r / h;
+        if (q >= 2.0) continue;
+        const double t = 1.0 - 0.5 * q;
+        s += walpha * t * t * t * t * (2.0 * q + 1.0);
+      }
+  return s;
+}
+
+size_t tsize(const sph_ctx* c) { return c->precision == SPH_FP64 ? 8 : 4; }
+
+StageArgs args(const sph_ctx* c) {
+  StageArgs a;
+  a.P = c->P;
+  a.B = c->B;
+  a.L = c->L;
+  return a;
+}
+
+void enqueue_step(sph_ctx* c, cudaStream_t s) {
+  if (c->precision == SPH_FP64)
+    enqueue_step_fp64(args(c), s);
+  else
+    enqueue_step_mixed(args(c), s);
+}
+
+void configure_launch(sph_ctx* c) {
+  LaunchCfg& L = c->L;
+  if (L.block_loop <= 0) L.block_loop = 128;
+  L.blocks_loop = L.sms * (2048 / L.block_loop);
+  L.block_stream = 256;
+  L.blocks_stream = L.sms * 8;
+  L.key_bits = bits_for(c->P.ncell);
+  L.radix_passes = radix_passes_for(L.key_bits, L.radix_bits);
+  c->B.sorted_buf = L.radix_passes % 2;
+}
+
+// The caller's stream -> internal stream ordering.
+int enter(sph_ctx* c) {
+  CK(cudaEventRecord(c->ev_in, c->user_stream));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+  return SPH_OK;
+}
+int leave(sph_ctx* c) {
+  CK(cudaEventRecord(c->ev_out, c->stream));
+  CK(cudaStreamWaitEvent(c->user_stream, c->ev_out, 0));
+  return SPH_OK;
+}
+
+int read_scalars(sph_ctx* c, DevScalars* hs) {
+  CK(cudaMemcpyAsync(hs, c->B.sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SPH_OK;
+}
+
+int flags_status(sph_ctx* c, const DevScalars& hs) {
+  if (hs.flags & kFlagNonFinite)
+    return set_err(c, SPH_E_NONFINITE, "a velocity or density became non-finite");
+  if (hs.flags & kFlagOutOfDomain)
+    return set_err(c, SPH_E_OUT_OF_DOMAIN, "a particle left the domain (clamped to the edge cell)");
+  return SPH_OK;
+}
+
+int sync_status(sph_ctx* c, DevScalars* out = nullptr) {
+  DevScalars hs;
+  int rc = read_scalars(c, &hs);
+  if (rc) return rc;
+  CK(cudaGetLastError());
+  if (out) *out = hs;
+  return flags_status(c, hs);
+}
+
+// user-order scatter of one field: out[id[k] * comps + q] = src_q[k * stride + off]
+__global__ void k_scatter_field(const void* s0, const void* s1, const void* s2, int is_float,
+                                int stride, int off, int comps, const uint32_t* __restrict__ id,
+                                int n, double* __restrict__ out) {
+  const void* src[3] = {s0, s1, s2};
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const size_t u = id[k];
+    for (int q = 0; q < comps; ++q) {
+      const size_t e = (size_t)k * stride + off;
+      out[u * comps + q] = is_float ? (double)((const float*)src[q])[e] : ((const double*)src[q])[e];
+    }
+  }
+}
+
+int scatter_out(sph_ctx* c, const void* s0, const void* s1, const void* s2, int is_float,
+                int stride, int off, int comps, int par, double* host) {
+  const int n = c->P.n;
+  int blocks = (n + 255) / 256;
+  if (blocks > c->L.blocks_stream) blocks = c->L.blocks_stream;
+  if (blocks < 1) blocks = 1;
+  k_scatter_field<<<blocks, 256, 0, c->stream>>>(s0, s1, s2, is_float, stride, off, comps,
+                                                 c->B.id[par], n, c->B.io);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(host, c->B.io, (size_t)n * comps * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return SPH_OK;
+}
+
+int alloc_fluid(sph_ctx* c, size_t n) {
+  if (n <= c->cap_n && !c->fluid_blocks.empty()) return SPH_OK;
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  dev_free_list(c, c->fluid_blocks);
+  DevBuffers& B = c->B;
+  const size_t ts = tsize(c);
+  const int d = c->P.dim;
+  const size_t nn = n ? n : 1;
+  auto A = [&](size_t bytes) { return dev_alloc(c, bytes, c->fluid_blocks); };
+  bool ok = true;
+  for (int p = 0; p < 2; ++p) {
+    for (int k = 0; k < 3; ++k) {
+      B.x[p][k] = k < d ? (double*)A(nn * 8) : nullptr;
+      B.v[p][k] = k < d ? (double*)A(nn * 8) : nullptr;
+      ok &= k >= d || (B.x[p][k] && B.v[p][k]);
+    }
+    B.rho[p] = (double*)A(nn * 8);
+    B.drho[p] = A(nn * ts);
+    B.id[p] = (uint32_t*)A(nn * 4);
+    ok &= B.rho[p] && B.drho[p] && B.id[p];
+  }
+  for (int k = 0; k < 3; ++k) {
+    B.aprior[k] = k < d ? A(nn * ts) : nullptr;
+    B.acc[k] = k < d ? A(nn * ts) : nullptr;
+    ok &= k >= d || (B.aprior[k] && B.acc[k]);
+  }
+  B.sigma = A(nn * ts);
+  const size_t pbytes = 4 * ts;
+  const size_t sbytes = (d == 3 ? 4 : 2) * ts;
+  for (int p = 0; p < 2; ++p) {
+    B.recP[p] = A(nn * pbytes);
+    B.recS[p] = A(nn * sbytes);
+    B.keys[p] = (uint32_t*)A(nn * 4);
+    B.vals[p] = (uint32_t*)A(nn * 4);
+    ok &= B.recP[p] && B.recS[p] && B.keys[p] && B.vals[p];
+  }
+  const size_t tiles = (nn + kSortTile - 1) / kSortTile;
+  B.tile_hist = (uint32_t*)A(tiles * ((size_t)1 << kMaxRadixBits) * 4);
+  B.io = (double*)A(nn * 3 * 8);
+  ok &= B.sigma && B.tile_hist && B.io;
+  if (!ok) {
+    dev_free_list(c, c->fluid_blocks);
+    c->cap_n = 0;
+    return set_err(c, SPH_E_OOM, "device allocation failed (fluid buffers)");
+  }
+  c->cap_n = n;
+  return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sph_create(const sph_domain* domain, double dp, double h, const sph_material* mat,
+               const double gravity[3], int precision, const sph_allocator* alloc, void* stream,
+               sph_ctx** out) {
+  if (!out) return SPH_E_INVALID;
+  *out = nullptr;
+  if (!domain || !mat || !gravity) return SPH_E_INVALID;
+  const int dim = domain->dim;
+  if (dim != 2 && dim != 3) return SPH_E_INVALID;
+  if (!(dp > 0) || !(h > 0) || !(mat->rho0 > 0) || !(mat->c0 > 0) || !(mat->mu >= 0) ||
+      !(mat->U_ref > 0))
+    return SPH_E_INVALID;
+  if (precision != SPH_FP64 && precision != SPH_MIXED) return SPH_E_INVALID;
+  if (alloc && (!alloc->alloc || !alloc->free)) return SPH_E_INVALID;
+  const double cs = 2.0 * h;
+  long long nc[3] = {1, 1, 1};
+  long long ncell = 1;
+  for (int k = 0; k < dim; ++k) {
+    if (!(domain->hi[k] > domain->lo[k])) return SPH_E_INVALID;
+    nc[k] = (long long)std::ceil((domain->hi[k] - domain->lo[k]) / cs);
+    if (nc[k] < 1) nc[k] = 1;
+    if (nc[k] > (1ll << 30)) return SPH_E_INVALID;
+    ncell *= nc[k];
+    if (ncell > 0xfffffffell) return SPH_E_INVALID;
+  }
+  sph_ctx* c = new sph_ctx();
+  c->precision = precision;
+  c->dp = dp;
+  if (alloc) {
+    c->alloc = *alloc;
+    c->has_alloc = true;
+  }
+  c->user_stream = (cudaStream_t)stream;
+  Params& P = c->P;
+  P.dim = dim;
+  P.nx = (int)nc[0];
+  P.ny = (int)nc[1];
+  P.nz = (int)nc[2];
+  P.ncell = (uint32_t)ncell;
+  for (int k = 0; k < 3; ++k) {
+    P.lo[k] = k < dim ? domain->lo[k] : 0.0;
+    P.g[k] = k < dim ? gravity[k] : 0.0;
+  }
+  P.cs = cs;
+  P.h = h;
+  P.r2max = 4.0 * h * h;
+  P.rho0 = mat->rho0;
+  P.c0 = mat->c0;
+  P.c0sq = mat->c0 * mat->c0;
+  P.mu = mat->mu;
+  P.U_ref = mat->U_ref;
+  P.V = dim == 2 ? dp * dp : dp * dp * dp;
+  P.m = mat->rho0 * P.V;
+  P.walpha = dim == 2 ? 7.0 / (4.0 * kPi * h * h) : 21.0 / (16.0 * kPi * h * h * h);
+  P.sigma0 = lattice_sigma0(dim, dp, h, P.walpha);
+  P.eps = 0.01 * h;
+  P.diag = 0;
+
+  int rc = SPH_OK;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->L.sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = configure_sort_kernels();
+  if (e != cudaSuccess) {
+    rc = cuda_err(c, e, "sph_create");
+    sph_destroy(c);
+    return rc;
+  }
+  c->L.radix_bits = 8;
+  c->L.block_loop = 128;
+  configure_launch(c);
+  // fixed buffers: scalars and the two CSR offset arrays
+  c->B.sc = (DevScalars*)dev_alloc(c, sizeof(DevScalars), c->fixed_blocks);
+  c->B.cell_begin = (uint32_t*)dev_alloc(c, ((size_t)P.ncell + 1) * 4, c->fixed_blocks);
+  c->B.wall_cb = (uint32_t*)dev_alloc(c, ((size_t)P.ncell + 1) * 4, c->fixed_blocks);
+  c->B.digit_total = (uint32_t*)dev_alloc(c, ((size_t)1 << kMaxRadixBits) * 4, c->fixed_blocks);
+  if (!c->B.sc || !c->B.cell_begin || !c->B.wall_cb || !c->B.digit_total) {
+    sph_destroy(c);
+    return SPH_E_OOM;
+  }
+  DevScalars z{};
+  e = cudaMemcpyAsync(c->B.sc, &z, sizeof(z), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(c->B.wall_cb, 0, ((size_t)P.ncell + 1) * 4, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->B.digit_total, 0, ((size_t)1 << kMaxRadixBits) * 4, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    rc = cuda_err(c, e, "sph_create");
+    sph_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return SPH_OK;
+}
+
+int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const double* vel,
+                      const double* rho) {
+  if (!c) return SPH_E_INVALID;
+  if (n > 0 && !pos) return set_err(c, SPH_E_INVALID, "pos is NULL");
+  if (n > 0x7fffffffull) return set_err(c, SPH_E_INVALID, "too many particles");
+  const int d = c->P.dim;
+  if (kind == SPH_FLUID) {
+    int rc = enter(c);
+    if (rc) return rc;
+    rc = alloc_fluid(c, n);
+    if (rc) return rc;
+    drop_graph(c);
+    c->P.n = (int)n;
+    configure_launch(c);
+    DevBuffers& B = c->B;
+    if (n > 0) {
+      std::vector<double> soa(n * 3, 0.0);
+      for (int k = 0; k < d; ++k) {
+        for (size_t i = 0; i < n; ++i) soa[k * n + i] = pos[i * d + k];
+        CK(cudaMemcpyAsync(B.x[0][k], &soa[k * n], n * 8, cudaMemcpyHostToDevice, c->stream));
+      }
+      CK(cudaStreamSynchronize(c->stream));
+      for (int k = 0; k < d; ++k) {
+        for (size_t i = 0; i < n; ++i) soa[k * n + i] = vel ? vel[i * d + k] : 0.0;
+        CK(cudaMemcpyAsync(B.v[0][k], &soa[k * n], n * 8, cudaMemcpyHostToDevice, c->stream));
+      }
+      CK(cudaStreamSynchronize(c->stream));
+      for (size_t i = 0; i < n; ++i) soa[i] = rho ? rho[i] : c->P.rho0;
+      CK(cudaMemcpyAsync(B.rho[0], soa.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
+      std::vector<uint32_t> iota(n);
+      for (size_t i = 0; i < n; ++i) iota[i] = (uint32_t)i;
+      CK(cudaMemcpyAsync(B.id[0], iota.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+      CK(cudaMemsetAsync(B.drho[0], 0, n * tsize(c), c->stream));
+      for (int k = 0; k < d; ++k) {
+        CK(cudaMemsetAsync(B.acc[k], 0, n * tsize(c), c->stream));
+        CK(cudaMemsetAsync(B.aprior[k], 0, n * tsize(c), c->stream));
+      }
+      CK(cudaMemsetAsync(B.sigma, 0, n * tsize(c), c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
+    DevScalars z{};
+    CK(cudaMemcpyAsync(B.sc, &z, sizeof(z), cudaMemcpyHostToDevice, c->stream));
+    if (n > 0) {
+      if (c->precision == SPH_FP64)
+        enqueue_initial_sort_fp64(args(c), c->stream);
+      else
+        enqueue_initial_sort_mixed(args(c), c->stream);
+      launch_vmax_reset(c->P, c->L, c->B, c->stream);
+    } else {
+      CK(cudaMemsetAsync(B.cell_begin, 0, ((size_t)c->P.ncell + 1) * 4, c->stream));
+    }
+    CK(cudaGetLastError());
+    c->fluid_set = n > 0;
+    CK(cudaStreamSynchronize(c->stream));
+    return leave(c);
+  }
+  if (kind == SPH_WALL) {
+    if (vel || rho) return set_err(c, SPH_E_INVALID, "wall particles take positions only");
+    int rc = enter(c);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    drop_graph(c);
+    dev_free_list(c, c->wall_blocks);
+    c->cap_nw = 0;
+    c->P.nw = (int)n;
+    if (n == 0) {
+      c->B.wallP = nullptr;
+      c->B.wall_id = nullptr;
+      c->B.wall_xyz = nullptr;
+      CK(cudaMemsetAsync(c->B.wall_cb, 0, ((size_t)c->P.ncell + 1) * 4, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      return leave(c);
+    }
+    auto A = [&](size_t bytes) { return dev_alloc(c, bytes, c->wall_blocks); };
+    const size_t ts = tsize(c);
+    c->B.wallP = A(n * (d == 3 ? 4 : 2) * ts);
+    c->B.wall_id = (uint32_t*)A(n * 4);
+    c->B.wall_xyz = (double*)A(n * 3 * 8);
+    std::vector<Block> tmp;
+    DevBuffers W = c->B;
+    W.io = (double*)dev_alloc(c, n * 3 * 8, tmp);
+    for (int p = 0; p < 2; ++p) {
+      W.keys[p] = (uint32_t*)dev_alloc(c, n * 4, tmp);
+      W.vals[p] = (uint32_t*)dev_alloc(c, n * 4, tmp);
+    }
+    const size_t tiles = (n + kSortTile - 1) / kSortTile;
+    W.tile_hist = (uint32_t*)dev_alloc(c, tiles * ((size_t)1 << kMaxRadixBits) * 4, tmp);
+    bool ok = c->B.wallP && c->B.wall_id && c->B.wall_xyz && W.io && W.keys[0] && W.keys[1] &&
+              W.vals[0] && W.vals[1] && W.tile_hist;
+    if (!ok) {
+      dev_free_list(c, tmp);
+      dev_free_list(c, c->wall_blocks);
+      c->P.nw = 0;
+      return set_err(c, SPH_E_OOM, "device allocation failed (wall buffers)");
+    }
+    std::vector<double> soa(n * 3, 0.0);
+    for (int k = 0; k < d; ++k)
+      for (size_t i = 0; i < n; ++i) soa[k * n + i] = pos[i * d + k];
+    CK(cudaMemcpyAsync(W.io, soa.data(), n * 3 * 8, cudaMemcpyHostToDevice, c->stream));
+    StageArgs a = args(c);
+    a.B = W;
+    if (c->precision == SPH_FP64)
+      enqueue_wall_setup_fp64(a, c->stream);
+    else
+      enqueue_wall_setup_mixed(a, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    dev_free_list(c, tmp);
+    c->cap_nw = n;
+    return leave(c);
+  }
+  return set_err(c, SPH_E_INVALID, "unknown particle kind");
+}
+
+int sph_step(sph_ctx* c, int n) {
+  if (!c) return SPH_E_INVALID;
+  if (n < 0) return set_err(c, SPH_E_INVALID, "negative step count");
+  if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
+  if (n == 0) return SPH_OK;
+  int rc = enter(c);
+  if (rc) return rc;
+  if (c->use_graph) {
+    if (!c->graph_exec) {
+      CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      enqueue_step(c, c->stream);
+      cudaError_t e = cudaStreamEndCapture(c->stream, &c->graph);
+      if (e != cudaSuccess) {
+        c->graph = nullptr;
+        return cuda_err(c, e, "graph capture");
+      }
+      e = cudaGraphInstantiate(&c->graph_exec, c->graph, 0);
+      if (e != cudaSuccess) {
+        drop_graph(c);
+        return cuda_err(c, e, "graph instantiate");
+      }
+    }
+    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(c->graph_exec, c->stream));
+  } else {
+    for (int i = 0; i < n; ++i) enqueue_step(c, c->stream);
+    CK(cudaGetLastError());
+  }
+  return leave(c);
+}
+
+int sph_synchronize(sph_ctx* c, double timeout_s) {
+  if (!c) return SPH_E_INVALID;
+  CK(cudaEventRecord(c->ev_out, c->stream));
+  if (timeout_s > 0) {
+    auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+      cudaError_t e = cudaEventQuery(c->ev_out);
+      if (e == cudaSuccess) break;
+      if (e != cudaErrorNotReady) return cuda_err(c, e, "sph_synchronize");
+      double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > timeout_s) return set_err(c, SPH_E_TIMEOUT, "queued work did not finish in time");
+      std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+  }
+  return sync_status(c);
+}
+
+int sph_get_fields(sph_ctx* c, unsigned mask, double* out) {
+  if (!c || (!out && mask)) return SPH_E_INVALID;
+  if (mask & ~0xffu) return set_err(c, SPH_E_INVALID, "unknown field bit");
+  if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
+  int rc = enter(c);
+  if (rc) return rc;
+  DevScalars hs;
+  rc = read_scalars(c, &hs);
+  if (rc) return rc;
+  const int par = hs.par, d = c->P.dim, n = c->P.n;
+  const DevBuffers& B = c->B;
+  const int isf = c->precision == SPH_MIXED;
+  double* o = out;
+  for (unsigned bit = 1; bit <= SPH_F_SIGMA; bit <<= 1) {
+    if (!(mask & bit)) continue;
+    int comps = 1;
+    switch (bit) {
+      case SPH_F_POS:
+        comps = d;
+        rc = scatter_out(c, B.x[par][0], B.x[par][1], B.x[par][2], 0, 1, 0, d, par, o);
+        break;
+      case SPH_F_VEL:
+        comps = d;
+        rc = scatter_out(c, B.v[par][0], B.v[par][1], B.v[par][2], 0, 1, 0, d, par, o);
+        break;
+      case SPH_F_RHO:
+        rc = scatter_out(c, B.rho[par], nullptr, nullptr, 0, 1, 0, 1, par, o);
+        break;
+      case SPH_F_P:
+        // pressure of the last first half-step, kept in the records of buffer 0
+        if (d == 3)
+          rc = scatter_out(c, B.recP[0], nullptr, nullptr, isf, 4, 3, 1, par, o);
+        else
+          rc = scatter_out(c, B.recS[0], nullptr, nullptr, isf, 2, 0, 1, par, o);
+        break;
+      case SPH_F_DRHO:
+        rc = scatter_out(c, B.drho[par], nullptr, nullptr, isf, 1, 0, 1, par, o);
+        break;
+      case SPH_F_ACC:
+        comps = d;
+        rc = scatter_out(c, B.acc[0], B.acc[1], B.acc[2], isf, 1, 0, d, par, o);
+        break;
+      case SPH_F_APRIOR:
+        comps = d;
+        rc = scatter_out(c, B.aprior[0], B.aprior[1], B.aprior[2], isf, 1, 0, d, par, o);
+        break;
+      case SPH_F_SIGMA:
+        rc = scatter_out(c, B.sigma, nullptr, nullptr, isf, 1, 0, 1, par, o);
+        break;
+    }
+    if (rc) return rc;
+    o += (size_t)n * comps;
+  }
+  rc = leave(c);
+  if (rc) return rc;
+  return flags_status(c, hs);
+}
+
+int sph_get_scalars(sph_ctx* c, double* t, double* dt_ad, double* dt_ac, long* n_ac,
+                    long* n_adv) {
+  if (!c) return SPH_E_INVALID;
+  int rc = enter(c);
+  if (rc) return rc;
+  DevScalars hs;
+  rc = read_scalars(c, &hs);
+  if (rc) return rc;
+  if (t) *t = hs.t;
+  if (dt_ad) *dt_ad = hs.dt_ad;
+  if (dt_ac) *dt_ac = hs.dt_ac;
+  if (n_ac) *n_ac = (long)hs.n_ac;
+  if (n_adv) *n_adv = (long)hs.n_adv;
+  return flags_status(c, hs);
+}
+
+size_t sph_count(const sph_ctx* c, int kind) {
+  if (!c) return 0;
+  return kind == SPH_WALL ? (size_t)c->P.nw : (size_t)c->P.n;
+}
+
+size_t sph_cell_count(const sph_ctx* c) { return c ? (size_t)c->P.ncell : 0; }
+
+int sph_debug_neighbour_state(sph_ctx* c, uint32_t* keys, uint32_t* perm, uint32_t* ids,
+                              uint32_t* cell_begin) {
+  if (!c) return SPH_E_INVALID;
+  if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
+  int rc = enter(c);
+  if (rc) return rc;
+  DevScalars hs;
+  rc = read_scalars(c, &hs);
+  if (rc) return rc;
+  const size_t n = c->P.n;
+  const int sb = c->B.sorted_buf;
+  if (keys) CK(cudaMemcpyAsync(keys, c->B.keys[sb], n * 4, cudaMemcpyDeviceToHost, c->stream));
+  if (perm) CK(cudaMemcpyAsync(perm, c->B.vals[sb], n * 4, cudaMemcpyDeviceToHost, c->stream));
+  if (ids) CK(cudaMemcpyAsync(ids, c->B.id[hs.par], n * 4, cudaMemcpyDeviceToHost, c->stream));
+  if (cell_begin)
+    CK(cudaMemcpyAsync(cell_begin, c->B.cell_begin, ((size_t)c->P.ncell + 1) * 4,
+                       cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  rc = leave(c);
+  if (rc) return rc;
+  return flags_status(c, hs);
+}
+
+int sph_debug_neighbour_stats(sph_ctx* c, uint32_t* cnt_fluid, uint32_t* cnt_wall,
+                              uint64_t* hash) {
+  if (!c || !cnt_fluid || !cnt_wall || !hash) return SPH_E_INVALID;
+  if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
+  int rc = enter(c);
+  if (rc) return rc;
+  const size_t n = c->P.n;
+  std::vector<Block> tmp;
+  uint32_t* cf = (uint32_t*)dev_alloc(c, n * 4, tmp);
+  uint32_t* cw = (uint32_t*)dev_alloc(c, n * 4, tmp);
+  unsigned long long* hs = (unsigned long long*)dev_alloc(c, n * 8, tmp);
+  if (!cf || !cw || !hs) {
+    dev_free_list(c, tmp);
+    return set_err(c, SPH_E_OOM, "device allocation failed (neighbour stats)");
+  }
+  launch_neighbour_stats(c->P, c->L, c->B, c->B.wall_xyz, cf, cw, hs, c->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt_fluid, cf, n * 4, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt_wall, cw, n * 4, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hash, hs, n * 8, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dev_free_list(c, tmp);
+  if (e != cudaSuccess) return cuda_err(c, e, "sph_debug_neighbour_stats");
+  rc = leave(c);
+  if (rc) return rc;
+  return sync_status(c);
+}
+
+int sph_set_option(sph_ctx* c, int option, long value) {
+  if (!c) return SPH_E_INVALID;
+  switch (option) {
+    case SPH_OPT_RECORD_DIAGNOSTICS:
+      c->P.diag = value ? 1 : 0;
+      break;
+    case SPH_OPT_USE_GRAPH:
+      c->use_graph = value != 0;
+      break;
+    case SPH_OPT_BLOCK:
+      if (value < 64 || value > 256 || value % 32)
+        return set_err(c, SPH_E_INVALID, "block size must be 64..256, a multiple of 32");
+      c->L.block_loop = (int)value;
+      configure_launch(c);
+      break;
+    case SPH_OPT_RADIX_BITS:
+      if (value < 4 || value > kMaxRadixBits)
+        return set_err(c, SPH_E_INVALID, "radix bits must be 4..11");
+      c->L.radix_bits = (int)value;
+      configure_launch(c);
+      break;
+    default:
+      return set_err(c, SPH_E_INVALID, "unknown option");
+  }
+  drop_graph(c);
+  return SPH_OK;
+}
+
+const char* sph_last_error(const sph_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void sph_destroy(sph_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  drop_graph(c);
+  dev_free_list(c, c->fluid_blocks);
+  dev_free_list(c, c->wall_blocks);
+  dev_free_list(c, c->fixed_blocks);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+}  // extern "C"

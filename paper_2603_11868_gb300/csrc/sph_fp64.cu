@@ -1,0 +1,27 @@
+// FP64 path: every stage in double precision (records hold absolute positions).
+#include "sph_stages.cuh"
+
+namespace sphgb {
+
+void enqueue_step_fp64(const StageArgs& a, cudaStream_t s) {
+  if (a.P.dim == 2)
+    stages::enqueue_step_t<2, double>(a, s);
+  else
+    stages::enqueue_step_t<3, double>(a, s);
+}
+
+void enqueue_initial_sort_fp64(const StageArgs& a, cudaStream_t s) {
+  if (a.P.dim == 2)
+    stages::enqueue_initial_sort_t<2, double>(a, s);
+  else
+    stages::enqueue_initial_sort_t<3, double>(a, s);
+}
+
+void enqueue_wall_setup_fp64(const StageArgs& a, cudaStream_t s) {
+  if (a.P.dim == 2)
+    stages::enqueue_wall_setup_t<2, double>(a, s);
+  else
+    stages::enqueue_wall_setup_t<3, double>(a, s);
+}
+
+}  // namespace sphgb

@@ -1,0 +1,186 @@
+// Internal layout of the GB300 SPH library: parameters, device scalars,
+// state buffers and the launch interface shared by the translation units.
+//
+// Data layout in HBM (n fluid particles, storage order = sorted by cell key of
+// the last rebuild):
+//   state, two copies (ping-pong, `par` selects the live one; the reorder
+//   after each sort gathers from one copy into the other):
+//     x[3], v[3]   double SoA
+//     rho          double
+//     drho         T (double in FP64 mode, float in mixed mode)
+//     id           uint32 user index
+//   aprior[3]      T   gravity + viscous acceleration (recomputed per rebuild)
+//   records, two buffers (written by one stage, read by the next neighbour loop):
+//     3D  P = (x, y, z, p)   S = (vx, vy, vz, rho)      T4 / T4
+//     2D  P = (x, y, vx, vy) S = (p, rho)               T4 / T2
+//   with positions absolute in FP64 mode and cell-local offsets
+//   x - (lo + c 2h) of the binned cell c in mixed mode.
+//   keys (sorted cell keys), perm, cell_begin[ncell + 1]   uint32
+//   wall: positions (T4 / T2, same convention), cell_begin, ids
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace sphgb {
+
+constexpr int kMaxRadixBits = 11;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;  // keys per thread per tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kOffsetsChunk = 2048;  // cells per block of the offsets kernel
+
+// error flag bits (sticky, device)
+constexpr int kFlagOutOfDomain = 1;
+constexpr int kFlagNonFinite = 2;
+
+struct Params {
+  int dim;
+  int n;        // fluid particles
+  int nw;       // wall particles
+  int nx, ny, nz;
+  uint32_t ncell;
+  double lo[3];
+  double cs;     // cell edge = 2h
+  double h;
+  double r2max;  // (2h)^2, computed as 4.0 * h * h
+  double rho0, c0, c0sq, mu, U_ref;
+  double g[3];
+  double m;       // fluid particle mass rho0 dp^dim
+  double V;       // dp^dim
+  double sigma0;  // lattice kernel sum
+  double walpha;  // Wendland alpha_d
+  double eps;     // 0.01 h viscous regulariser
+  int diag;       // store acc / sigma
+};
+
+// Schedule scalars, resident on the device.
+struct DevScalars {
+  double t, tau, dt_ad, dt_ac;
+  unsigned long long vmax2_cur;   // bit pattern of max |v|^2 of the current velocities
+  unsigned long long vmax2_next;  // accumulated by the pressure stage
+  long long n_ac, n_adv;
+  int new_adv;  // this step begins an advection step
+  int started;
+  int par;      // live state copy
+  int flags;    // sticky error bits
+};
+
+template <class T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  using type = float4;
+};
+template <>
+struct Vec4<double> {
+  using type = double4_32a;
+};
+template <class T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+
+// Raw device pointers of one context (all owned by the context).
+struct DevBuffers {
+  double* x[2][3];
+  double* v[2][3];
+  double* rho[2];
+  void* drho[2];  // T
+  uint32_t* id[2];
+  void* aprior[3];  // T
+  void* acc[3];     // T, diagnostics
+  void* sigma;      // T, diagnostics
+  void* recP[2];    // T4
+  void* recS[2];    // T4 (3D) or T2 (2D)
+  uint32_t* keys[2];  // sort ping-pong; keys[sorted_buf] holds the sorted keys
+  uint32_t* vals[2];
+  int sorted_buf;
+  uint32_t* tile_hist;  // bins x tiles
+  uint32_t* digit_total;
+  uint32_t* cell_begin;  // ncell + 1
+  // wall
+  void* wallP;  // T4 / T2
+  uint32_t* wall_cb;
+  uint32_t* wall_id;
+  double* wall_xyz;  // sorted wall positions, double SoA (3 nw)
+  DevScalars* sc;
+  double* io;  // staging, n * dim doubles (also wall staging)
+  uint32_t* u32_io;
+  unsigned long long* u64_io;
+};
+
+struct LaunchCfg {
+  int sms;           // multiprocessors
+  int block_loop;    // threads per block of the neighbour loops
+  int blocks_loop;   // persistent grid of the neighbour loops
+  int block_stream;  // threads per block of the streaming kernels
+  int blocks_stream;
+  int radix_bits;
+  int radix_passes;
+  int key_bits;
+  int tiles;  // radix tiles
+};
+
+// --- launch interface implemented per precision (sph_fp64.cu / sph_mixed.cu)
+struct StageArgs {
+  Params P;
+  DevBuffers B;
+  LaunchCfg L;
+};
+
+// Queue one acoustic step (device-decided rebuild included).
+void enqueue_step_fp64(const StageArgs& a, cudaStream_t s);
+void enqueue_step_mixed(const StageArgs& a, cudaStream_t s);
+// Initial binning / sort after set_particles (forces a rebuild of the cell
+// list and builds the records without changing the schedule).
+void enqueue_initial_sort_fp64(const StageArgs& a, cudaStream_t s);
+void enqueue_initial_sort_mixed(const StageArgs& a, cudaStream_t s);
+// Wall setup: keys, sort, wall records and wall cell offsets from the
+// staging buffer io (double SoA [x | y | z], nw each, user order).  The sort
+// runs in the keys / vals / tile_hist buffers of `a.B`, which the caller sets
+// to scratch of its own so that the fluid's sorted keys survive.
+void enqueue_wall_setup_fp64(const StageArgs& a, cudaStream_t s);
+void enqueue_wall_setup_mixed(const StageArgs& a, cudaStream_t s);
+
+// --- neighbour search (sph_nsearch.cu), precision independent
+// keys from positions x[par] (or an explicit coordinate set), vals = iota
+void launch_cell_keys(const Params& P, const LaunchCfg& L, const double* const x[3],
+                      uint32_t* keys, uint32_t* vals, int n, DevScalars* sc, int gated,
+                      uint32_t* digit_total, cudaStream_t s);
+void launch_cell_keys_par(const Params& P, const LaunchCfg& L, double* const x[2][3],
+                          uint32_t* keys, uint32_t* vals, int n, DevScalars* sc, int gated,
+                          uint32_t* digit_total, cudaStream_t s);
+// dynamic shared memory limits of the sort kernels (call once per device)
+cudaError_t configure_sort_kernels();
+// stable LSD radix sort of (keys[0], vals[0]) with ping-pong into [1];
+// returns the buffer index that holds the result
+int launch_radix_sort(const LaunchCfg& L, uint32_t* keys[2], uint32_t* vals[2], int n,
+                      uint32_t* tile_hist, uint32_t* digit_total, const DevScalars* sc,
+                      int gated, cudaStream_t s);
+// CSR offsets from sorted keys; if flip_par, thread 0 flips sc->par afterwards
+void launch_cell_offsets(const uint32_t* keys, int n, uint32_t ncell, uint32_t* cell_begin,
+                         DevScalars* sc, int gated, int flip_par, cudaStream_t s);
+// schedule control kernel (one thread)
+void launch_control(const Params& P, DevScalars* sc, cudaStream_t s);
+// fresh max |v|^2 of x[par] copy into vmax2_cur
+void launch_vmax_reset(const Params& P, const LaunchCfg& L, const DevBuffers& B,
+                       cudaStream_t s);
+// debug neighbour statistics (double positions of the live copy)
+void launch_neighbour_stats(const Params& P, const LaunchCfg& L, const DevBuffers& B,
+                            const double* wall_xyz, uint32_t* cnt_f, uint32_t* cnt_w,
+                            unsigned long long* hash, cudaStream_t s);
+
+int radix_passes_for(int key_bits, int radix_bits);
+int bits_for(uint32_t ncell);
+
+}  // namespace sphgb

@@ -1,0 +1,734 @@
+// Interaction stages of the weakly-compressible SPH step, templated on the
+// dimension D and the pair-arithmetic type T.
+//   T = double: FP64 path; records hold absolute positions.
+//   T = float : mixed path; records hold float cell-local offsets
+//               o = x - (lo + c 2h) of the binned cell c, so a pair distance is
+//               o_i - o_j - d 2h with d the cell offset (-1, 0, 1 per axis);
+//               state (x, v, rho) stays double.
+//
+// Direct search (paper, section "Cell linked-list, direct search and
+// sorting"): each neighbour loop recomputes kernel values for every particle
+// of the 3^D cells around the particle's binned cell; a pair is accepted when
+// r^2 < (2h)^2.  Equations (Wendland C2; [Z17] Riemann pressure and density
+// relaxation; [Z20] dual time stepping; Adami-style mirrored wall state):
+//   density summation  sigma_i = sum_{r<2h} W(r_ij) (fluid + wall, self incl.),
+//                      rho_i = rho0 max(sigma_i / sigma0, 1)
+//   viscous            a_prior_i = g + (2 mu / rho_i) sum_j V_j (v_i - v_j) W'/(r + 0.01h)
+//   half 1             rho += dt/2 drho; p = c0^2 (rho - rho0); x += dt/2 v
+//   pressure           a_i = -(2/rho_i) sum_j P*_ij V_j W' e_ij; v += dt (a + a_prior);
+//                      x += dt/2 v (first half of the density stage, fused)
+//   density            drho_i = -2 rho_i sum_j V_j W' (U_L - U*_ij); rho += dt/2 drho
+// with V_j = m / rho_j (walls: V_w = m / rho_w of the mirrored state).
+#pragma once
+
+#include "sph_internal.cuh"
+
+namespace sphgb {
+
+namespace stages {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+template <int D, class T>
+struct Rec;
+
+template <class T>
+struct Rec<3, T> {
+  using PV = typename Vec4<T>::type;  // (x, y, z, p)
+  using SV = typename Vec4<T>::type;  // (vx, vy, vz, rho)
+  __device__ static PV makeP(T x, T y, T z, T vx, T vy, T vz, T p) {
+    PV r;
+    r.x = x; r.y = y; r.z = z; r.w = p;
+    return r;
+  }
+  __device__ static SV makeS(T vx, T vy, T vz, T rho, T p) {
+    SV r;
+    r.x = vx; r.y = vy; r.z = vz; r.w = rho;
+    return r;
+  }
+  __device__ static T px(const PV& a) { return a.x; }
+  __device__ static T py(const PV& a) { return a.y; }
+  __device__ static T pz(const PV& a) { return a.z; }
+  __device__ static T vx(const PV&, const SV& b) { return b.x; }
+  __device__ static T vy(const PV&, const SV& b) { return b.y; }
+  __device__ static T vz(const PV&, const SV& b) { return b.z; }
+  __device__ static T pres(const PV& a, const SV&) { return a.w; }
+  __device__ static T rho(const PV&, const SV& b) { return b.w; }
+  __device__ static void set_rho(SV& b, T r) { b.w = r; }
+};
+
+template <class T>
+struct Rec<2, T> {
+  using PV = typename Vec4<T>::type;  // (x, y, vx, vy)
+  using SV = typename Vec2<T>::type;  // (p, rho)
+  __device__ static PV makeP(T x, T y, T, T vx, T vy, T, T) {
+    PV r;
+    r.x = x; r.y = y; r.z = vx; r.w = vy;
+    return r;
+  }
+  __device__ static SV makeS(T, T, T, T rho, T p) {
+    SV r;
+    r.x = p; r.y = rho;
+    return r;
+  }
+  __device__ static T px(const PV& a) { return a.x; }
+  __device__ static T py(const PV& a) { return a.y; }
+  __device__ static T pz(const PV&) { return T(0); }
+  __device__ static T vx(const PV& a, const SV&) { return a.z; }
+  __device__ static T vy(const PV& a, const SV&) { return a.w; }
+  __device__ static T vz(const PV&, const SV&) { return T(0); }
+  __device__ static T pres(const PV&, const SV& b) { return b.x; }
+  __device__ static T rho(const PV&, const SV& b) { return b.y; }
+  __device__ static void set_rho(SV& b, T r) { b.y = r; }
+};
+
+// wall record: position (absolute or cell-local offset)
+template <int D, class T>
+struct WallRec;
+template <class T>
+struct WallRec<3, T> {
+  using WV = typename Vec4<T>::type;
+  __device__ static WV make(T x, T y, T z) {
+    WV r;
+    r.x = x; r.y = y; r.z = z; r.w = T(0);
+    return r;
+  }
+  __device__ static T z(const WV& a) { return a.z; }
+};
+template <class T>
+struct WallRec<2, T> {
+  using WV = typename Vec2<T>::type;
+  __device__ static WV make(T x, T y, T) {
+    WV r;
+    r.x = x; r.y = y;
+    return r;
+  }
+  __device__ static T z(const WV&) { return T(0); }
+};
+
+// constants in the pair type
+template <class T>
+struct KC {
+  T r2max, inv_h, cW, cdW, m, c0, inv_c0, rho0, inv_c0sq, eps, two_mu, cs, half;
+  T g[3];
+};
+
+template <class T>
+__host__ KC<T> make_kc(const Params& P) {
+  KC<T> k;
+  k.r2max = (T)P.r2max;
+  k.inv_h = (T)(1.0 / P.h);
+  k.cW = (T)P.walpha;
+  k.cdW = (T)(-5.0 * P.walpha / P.h);
+  k.m = (T)P.m;
+  k.c0 = (T)P.c0;
+  k.inv_c0 = (T)(1.0 / P.c0);
+  k.rho0 = (T)P.rho0;
+  k.inv_c0sq = (T)(1.0 / P.c0sq);
+  k.eps = (T)P.eps;
+  k.two_mu = (T)(2.0 * P.mu);
+  k.cs = (T)P.cs;
+  k.half = (T)0.5;
+  for (int d = 0; d < 3; ++d) k.g[d] = (T)P.g[d];
+  return k;
+}
+
+// pair-type helpers
+__device__ __forceinline__ float inv_sqrt_t(float a) { return rsqrtf(a); }
+__device__ __forceinline__ double inv_sqrt_t(double a) { return 1.0 / sqrt(a); }
+__device__ __forceinline__ float div_t(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_t(double a, double b) { return a / b; }
+
+// r^2 of the pair: FP64 uses an uncontracted sum (bit-identical acceptance with
+// a serial evaluation); float uses ordinary fused arithmetic.
+__device__ __forceinline__ double r2_of(double dx, double dy, double dz) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+__device__ __forceinline__ float r2_of(float dx, float dy, float dz) {
+  return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float dsub(float a, float b) { return a - b; }
+
+template <class T>
+__device__ __forceinline__ T wendland(const KC<T>& k, T r) {
+  T q = r * k.inv_h;
+  T t = T(1) - k.half * q;
+  T t2 = t * t;
+  return k.cW * t2 * t2 * (T(2) * q + T(1));
+}
+template <class T>
+__device__ __forceinline__ T wendland_dr(const KC<T>& k, T r) {
+  T q = r * k.inv_h;
+  T t = T(1) - k.half * q;
+  return k.cdW * q * t * t * t;
+}
+
+// Binned cell of a storage slot from its sorted key.
+struct Cell {
+  int x, y, z;
+};
+__device__ __forceinline__ Cell decode(uint32_t key, const Params& P) {
+  Cell c;
+  uint32_t r = key / (uint32_t)P.nx;
+  c.x = (int)(key - r * (uint32_t)P.nx);
+  c.y = (int)(r % (uint32_t)P.ny);
+  c.z = (int)(r / (uint32_t)P.ny);
+  return c;
+}
+
+// Iterate the 3^D cells around a binned cell in the order dz, dy, dx; f gets
+// (cell index, dx, dy, dz).
+template <int D, class F>
+__device__ __forceinline__ void for_each_cell(const Params& P, Cell c, F&& f) {
+  const int kz = D == 3 ? 1 : 0;
+  for (int dz = -kz; dz <= kz; ++dz) {
+    const int z = c.z + dz;
+    if (z < 0 || z >= P.nz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int y = c.y + dy;
+      if (y < 0 || y >= P.ny) continue;
+      const uint32_t row = ((uint32_t)z * (uint32_t)P.ny + (uint32_t)y) * (uint32_t)P.nx;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int x = c.x + dx;
+        if (x < 0 || x >= P.nx) continue;
+        f(row + (uint32_t)x, dx, dy, dz);
+      }
+    }
+  }
+}
+
+// Position of a state slot in record form: absolute (FP64) or cell-local offset.
+template <class T>
+struct Local;
+template <>
+struct Local<double> {
+  static constexpr bool kLocal = false;
+  __device__ static void enc(const Params&, Cell, double x, double y, double z, double& ox,
+                             double& oy, double& oz) {
+    ox = x; oy = y; oz = z;
+  }
+};
+template <>
+struct Local<float> {
+  static constexpr bool kLocal = true;
+  __device__ static void enc(const Params& P, Cell c, double x, double y, double z, float& ox,
+                             float& oy, float& oz) {
+    ox = (float)(x - (P.lo[0] + (double)c.x * P.cs));
+    oy = (float)(y - (P.lo[1] + (double)c.y * P.cs));
+    oz = (float)(z - (P.lo[2] + (double)c.z * P.cs));
+  }
+};
+
+// Pointers of one state copy, chosen with selects (runtime indexing into the
+// kernel-parameter arrays would force them into local memory).
+template <class T>
+struct Live {
+  double *x0, *x1, *x2, *v0, *v1, *v2, *rho;
+  T* drho;
+  uint32_t* id;
+};
+template <class T>
+__device__ __forceinline__ Live<T> live(const DevBuffers& B, int par) {
+  Live<T> L;
+  L.x0 = par ? B.x[1][0] : B.x[0][0];
+  L.x1 = par ? B.x[1][1] : B.x[0][1];
+  L.x2 = par ? B.x[1][2] : B.x[0][2];
+  L.v0 = par ? B.v[1][0] : B.v[0][0];
+  L.v1 = par ? B.v[1][1] : B.v[0][1];
+  L.v2 = par ? B.v[1][2] : B.v[0][2];
+  L.rho = par ? B.rho[1] : B.rho[0];
+  L.drho = (T*)(par ? B.drho[1] : B.drho[0]);
+  L.id = par ? B.id[1] : B.id[0];
+  return L;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFullMask, v, o));
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Reorder after the sort: gather the live state copy into the other copy and
+// write the loop records of buffer 0 (positions; velocity; old p; old rho).
+template <int D, class T>
+__global__ void k_reorder(Params P, DevBuffers B, int gated) {
+  using R = Rec<D, T>;
+  DevScalars* sc = B.sc;
+  if (gated && !sc->new_adv) return;
+  const int par = sc->par;
+  const Live<T> S = live<T>(B, par), Dd = live<T>(B, par ^ 1);
+  const uint32_t* __restrict__ perm = B.vals[B.sorted_buf];
+  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  typename R::PV* recP = (typename R::PV*)B.recP[0];
+  typename R::SV* recS = (typename R::SV*)B.recS[0];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.n; k += gridDim.x * blockDim.x) {
+    const uint32_t j = perm[k];
+    double x = S.x0[j], y = S.x1[j], z = D == 3 ? S.x2[j] : 0.0;
+    double vx = S.v0[j], vy = S.v1[j], vz = D == 3 ? S.v2[j] : 0.0;
+    double rho = S.rho[j];
+    Dd.x0[k] = x;
+    Dd.x1[k] = y;
+    Dd.v0[k] = vx;
+    Dd.v1[k] = vy;
+    if (D == 3) {
+      Dd.x2[k] = z;
+      Dd.v2[k] = vz;
+    }
+    Dd.rho[k] = rho;
+    Dd.drho[k] = S.drho[j];
+    Dd.id[k] = S.id[j];
+    T ox, oy, oz;
+    Local<T>::enc(P, decode(keys[k], P), x, y, z, ox, oy, oz);
+    T p = (T)(P.c0sq * (rho - P.rho0));
+    recP[k] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p);
+    recS[k] = R::makeS((T)vx, (T)vy, (T)vz, (T)rho, p);
+  }
+}
+
+// Density summation: reads records P of buffer 0; writes rho (state) and the
+// rho slot of records S of buffer 0.
+template <int D, class T>
+__global__ void __launch_bounds__(256) k_density_summation(Params P, DevBuffers B, KC<T> k,
+                                                           int gated) {
+  using R = Rec<D, T>;
+  using WR = WallRec<D, T>;
+  DevScalars* sc = B.sc;
+  if (gated && !sc->new_adv) return;
+  double* rho_live = sc->par ? B.rho[1] : B.rho[0];
+  const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
+  typename R::SV* recS = (typename R::SV*)B.recS[0];
+  const typename WR::WV* __restrict__ wall = (const typename WR::WV*)B.wallP;
+  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  const uint32_t* __restrict__ cb = B.cell_begin;
+  const uint32_t* __restrict__ wcb = B.wall_cb;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    const Cell ci = decode(keys[i], P);
+    const typename R::PV pi = recP[i];
+    const T xi = R::px(pi), yi = R::py(pi), zi = R::pz(pi);
+    T sig = T(0);
+    for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
+      const T sx = Local<T>::kLocal ? T(dx) * k.cs : T(0);
+      const T sy = Local<T>::kLocal ? T(dy) * k.cs : T(0);
+      const T sz = Local<T>::kLocal ? T(dz) * k.cs : T(0);
+      const T bx = xi - sx, by = yi - sy, bz = zi - sz;
+      const uint32_t e = cb[c + 1];
+      for (uint32_t j = cb[c]; j < e; ++j) {
+        const typename R::PV pj = recP[j];
+        const T r2 = r2_of(dsub(bx, R::px(pj)), dsub(by, R::py(pj)), dsub(bz, R::pz(pj)));
+        if (r2 < k.r2max) sig += wendland(k, sqrt(r2));
+      }
+      if (P.nw > 0) {
+        const uint32_t we = wcb[c + 1];
+        for (uint32_t w = wcb[c]; w < we; ++w) {
+          const typename WR::WV pw = wall[w];
+          const T r2 = r2_of(dsub(bx, pw.x), dsub(by, pw.y), dsub(bz, WR::z(pw)));
+          if (r2 < k.r2max) sig += wendland(k, sqrt(r2));
+        }
+      }
+    });
+    double ratio = (double)sig / P.sigma0;
+    double rho = P.rho0 * (ratio > 1.0 ? ratio : 1.0);
+    rho_live[i] = rho;
+    typename R::SV s = recS[i];
+    R::set_rho(s, (T)rho);
+    recS[i] = s;
+    if (P.diag) ((T*)B.sigma)[i] = sig;
+  }
+}
+
+// Viscous force: reads records P, S of buffer 0 (S carries the new rho);
+// writes a_prior = g + viscous acceleration.
+template <int D, class T>
+__global__ void __launch_bounds__(256) k_viscous(Params P, DevBuffers B, KC<T> k, int gated) {
+  using R = Rec<D, T>;
+  using WR = WallRec<D, T>;
+  DevScalars* sc = B.sc;
+  if (gated && !sc->new_adv) return;
+  const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
+  const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
+  const typename WR::WV* __restrict__ wall = (const typename WR::WV*)B.wallP;
+  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  const uint32_t* __restrict__ cb = B.cell_begin;
+  const uint32_t* __restrict__ wcb = B.wall_cb;
+  T* ap0 = (T*)B.aprior[0];
+  T* ap1 = (T*)B.aprior[1];
+  T* ap2 = (T*)B.aprior[2];
+  const T wallV = (T)P.V;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    const Cell ci = decode(keys[i], P);
+    const typename R::PV pi = recP[i];
+    const typename R::SV si = recS[i];
+    const T xi = R::px(pi), yi = R::py(pi), zi = R::pz(pi);
+    const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
+    T ax = 0, ay = 0, az = 0;
+    for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
+      const T sx = Local<T>::kLocal ? T(dx) * k.cs : T(0);
+      const T sy = Local<T>::kLocal ? T(dy) * k.cs : T(0);
+      const T sz = Local<T>::kLocal ? T(dz) * k.cs : T(0);
+      const T bx = xi - sx, by = yi - sy, bz = zi - sz;
+      const uint32_t e = cb[c + 1];
+      for (uint32_t j = cb[c]; j < e; ++j) {
+        const typename R::PV pj = recP[j];
+        const T rx = dsub(bx, R::px(pj)), ry = dsub(by, R::py(pj)), rz = dsub(bz, R::pz(pj));
+        const T r2 = r2_of(rx, ry, rz);
+        if (r2 < k.r2max && (int)j != i) {
+          const typename R::SV sj = recS[j];
+          const T r = sqrt(r2);
+          const T coef = div_t(k.m, R::rho(pj, sj)) * wendland_dr(k, r) / (r + k.eps);
+          ax += coef * (vxi - R::vx(pj, sj));
+          ay += coef * (vyi - R::vy(pj, sj));
+          az += coef * (vzi - R::vz(pj, sj));
+        }
+      }
+      if (P.nw > 0) {
+        const uint32_t we = wcb[c + 1];
+        for (uint32_t w = wcb[c]; w < we; ++w) {
+          const typename WR::WV pw = wall[w];
+          const T r2 = r2_of(dsub(bx, pw.x), dsub(by, pw.y), dsub(bz, WR::z(pw)));
+          if (r2 < k.r2max) {
+            const T r = sqrt(r2);
+            const T coef = wallV * wendland_dr(k, r) / (r + k.eps);
+            ax += coef * vxi;
+            ay += coef * vyi;
+            az += coef * vzi;
+          }
+        }
+      }
+    });
+    const T f = div_t(k.two_mu, R::rho(pi, si));
+    ap0[i] = k.g[0] + f * ax;
+    ap1[i] = k.g[1] + f * ay;
+    if (D == 3) ap2[i] = k.g[2] + f * az;
+  }
+}
+
+// First half of the acoustic step; writes records of buffer 0.
+template <int D, class T>
+__global__ void k_half1(Params P, DevBuffers B) {
+  using R = Rec<D, T>;
+  DevScalars* sc = B.sc;
+  const int par = sc->par;
+  const double dt = sc->dt_ac;
+  const double hdt = 0.5 * dt;
+  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  typename R::PV* recP = (typename R::PV*)B.recP[0];
+  typename R::SV* recS = (typename R::SV*)B.recS[0];
+  const Live<T> S = live<T>(B, par);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    double rho = S.rho[i] + hdt * (double)S.drho[i];
+    double p = P.c0sq * (rho - P.rho0);
+    double vx = S.v0[i], vy = S.v1[i], vz = D == 3 ? S.v2[i] : 0.0;
+    double x = S.x0[i] + hdt * vx;
+    double y = S.x1[i] + hdt * vy;
+    double z = D == 3 ? S.x2[i] + hdt * vz : 0.0;
+    S.rho[i] = rho;
+    S.x0[i] = x;
+    S.x1[i] = y;
+    if (D == 3) S.x2[i] = z;
+    T ox, oy, oz;
+    Local<T>::enc(P, decode(keys[i], P), x, y, z, ox, oy, oz);
+    recP[i] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, (T)p);
+    recS[i] = R::makeS((T)vx, (T)vy, (T)vz, (T)rho, (T)p);
+  }
+}
+
+// Riemann pressure relaxation + kick + the drift that opens the density stage.
+// Reads records of buffer 0, writes records of buffer 1.
+template <int D, class T>
+__global__ void __launch_bounds__(256) k_pressure(Params P, DevBuffers B, KC<T> k) {
+  using R = Rec<D, T>;
+  using WR = WallRec<D, T>;
+  DevScalars* sc = B.sc;
+  const int par = sc->par;
+  const double dt = sc->dt_ac;
+  const double hdt = 0.5 * dt;
+  const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
+  const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
+  typename R::PV* outP = (typename R::PV*)B.recP[1];
+  typename R::SV* outS = (typename R::SV*)B.recS[1];
+  const typename WR::WV* __restrict__ wall = (const typename WR::WV*)B.wallP;
+  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  const uint32_t* __restrict__ cb = B.cell_begin;
+  const uint32_t* __restrict__ wcb = B.wall_cb;
+  const T* ap0 = (const T*)B.aprior[0];
+  const T* ap1 = (const T*)B.aprior[1];
+  const T* ap2 = (const T*)B.aprior[2];
+  const Live<T> S = live<T>(B, par);
+  double vmax2 = 0.0;
+  int bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    const Cell ci = decode(keys[i], P);
+    const typename R::PV pi = recP[i];
+    const typename R::SV si = recS[i];
+    const T xi = R::px(pi), yi = R::py(pi), zi = R::pz(pi);
+    const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
+    const T p_i = R::pres(pi, si), rho_i = R::rho(pi, si);
+    T ax = 0, ay = 0, az = 0;
+    for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
+      const T sx = Local<T>::kLocal ? T(dx) * k.cs : T(0);
+      const T sy = Local<T>::kLocal ? T(dy) * k.cs : T(0);
+      const T sz = Local<T>::kLocal ? T(dz) * k.cs : T(0);
+      const T bx = xi - sx, by = yi - sy, bz = zi - sz;
+      const uint32_t e = cb[c + 1];
+      for (uint32_t j = cb[c]; j < e; ++j) {
+        const typename R::PV pj = recP[j];
+        const T rx = dsub(bx, R::px(pj)), ry = dsub(by, R::py(pj)), rz = dsub(bz, R::pz(pj));
+        const T r2 = r2_of(rx, ry, rz);
+        if (r2 < k.r2max && (int)j != i) {
+          const typename R::SV sj = recS[j];
+          const T inv_r = inv_sqrt_t(r2);
+          const T r = r2 * inv_r;
+          const T ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
+          const T UL = -(vxi * ex + vyi * ey + vzi * ez);
+          const T UR = -(R::vx(pj, sj) * ex + R::vy(pj, sj) * ey + R::vz(pj, sj) * ez);
+          const T rho_j = R::rho(pj, sj);
+          const T rbar = k.half * (rho_i + rho_j);
+          const T jump = UL - UR;
+          T beta = T(3) * (jump > T(0) ? jump : T(0)) * k.inv_c0;
+          beta = beta < T(1) ? beta : T(1);
+          const T Ps = k.half * (p_i + R::pres(pj, sj)) + k.half * beta * rbar * k.c0 * jump;
+          const T f = Ps * div_t(k.m, rho_j) * wendland_dr(k, r);
+          ax += f * ex;
+          ay += f * ey;
+          az += f * ez;
+        }
+      }
+      if (P.nw > 0) {
+        const uint32_t we = wcb[c + 1];
+        for (uint32_t w = wcb[c]; w < we; ++w) {
+          const typename WR::WV pw = wall[w];
+          const T rx = dsub(bx, pw.x), ry = dsub(by, pw.y), rz = dsub(bz, WR::z(pw));
+          const T r2 = r2_of(rx, ry, rz);
+          if (r2 < k.r2max) {
+            const T inv_r = inv_sqrt_t(r2);
+            const T r = r2 * inv_r;
+            const T ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
+            // mirrored state: p_w = p_i + rho_i (x_w - x_i).g, x_w - x_i = -r_vec
+            const T gdot = -(rx * k.g[0] + ry * k.g[1] + rz * k.g[2]);
+            const T pw_ = p_i + rho_i * gdot;
+            const T rho_w = k.rho0 + pw_ * k.inv_c0sq;
+            const T UL = -(vxi * ex + vyi * ey + vzi * ez);
+            const T jump = UL + UL;
+            const T rbar = k.half * (rho_i + rho_w);
+            T beta = T(3) * (jump > T(0) ? jump : T(0)) * k.inv_c0;
+            beta = beta < T(1) ? beta : T(1);
+            const T Ps = k.half * (p_i + pw_) + k.half * beta * rbar * k.c0 * jump;
+            const T f = Ps * div_t(k.m, rho_w) * wendland_dr(k, r);
+            ax += f * ex;
+            ay += f * ey;
+            az += f * ez;
+          }
+        }
+      }
+    });
+    const T s = div_t(T(-2), rho_i);
+    ax *= s;
+    ay *= s;
+    az *= s;
+    if (P.diag) {
+      ((T*)B.acc[0])[i] = ax;
+      ((T*)B.acc[1])[i] = ay;
+      if (D == 3) ((T*)B.acc[2])[i] = az;
+    }
+    double vx = S.v0[i] + dt * (double)(ax + ap0[i]);
+    double vy = S.v1[i] + dt * (double)(ay + ap1[i]);
+    double vz = D == 3 ? S.v2[i] + dt * (double)(az + ap2[i]) : 0.0;
+    double x = S.x0[i] + hdt * vx;
+    double y = S.x1[i] + hdt * vy;
+    double z = D == 3 ? S.x2[i] + hdt * vz : 0.0;
+    S.v0[i] = vx;
+    S.v1[i] = vy;
+    S.x0[i] = x;
+    S.x1[i] = y;
+    if (D == 3) {
+      S.v2[i] = vz;
+      S.x2[i] = z;
+    }
+    double s2 = __dadd_rn(__dadd_rn(__dmul_rn(vx, vx), __dmul_rn(vy, vy)), __dmul_rn(vz, vz));
+    if (!(s2 <= 1e300)) bad = 1;  // NaN or overflow
+    vmax2 = s2 > vmax2 ? s2 : vmax2;
+    T ox, oy, oz;
+    Local<T>::enc(P, ci, x, y, z, ox, oy, oz);
+    outP[i] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p_i);
+    outS[i] = R::makeS((T)vx, (T)vy, (T)vz, rho_i, p_i);
+  }
+  vmax2 = warp_max(vmax2);
+  __shared__ double wm[32];
+  if (threadIdx.x % 32 == 0) wm[threadIdx.x / 32] = vmax2;
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&sc->flags, kFlagNonFinite);
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x / 32); ++q) vmax2 = fmax(vmax2, wm[q]);
+    if (!(vmax2 <= 1e300)) vmax2 = 1e300;
+    atomicMax(&sc->vmax2_next, (unsigned long long)__double_as_longlong(vmax2));
+  }
+}
+
+// Riemann density relaxation: reads records of buffer 1; drho and rho (state).
+template <int D, class T>
+__global__ void __launch_bounds__(256) k_density_relax(Params P, DevBuffers B, KC<T> k) {
+  using R = Rec<D, T>;
+  using WR = WallRec<D, T>;
+  DevScalars* sc = B.sc;
+  const int par = sc->par;
+  const double hdt = 0.5 * sc->dt_ac;
+  const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[1];
+  const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[1];
+  const typename WR::WV* __restrict__ wall = (const typename WR::WV*)B.wallP;
+  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  const uint32_t* __restrict__ cb = B.cell_begin;
+  const uint32_t* __restrict__ wcb = B.wall_cb;
+  const Live<T> S = live<T>(B, par);
+  int bad = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc->vmax2_cur = sc->vmax2_next;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    const Cell ci = decode(keys[i], P);
+    const typename R::PV pi = recP[i];
+    const typename R::SV si = recS[i];
+    const T xi = R::px(pi), yi = R::py(pi), zi = R::pz(pi);
+    const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
+    const T p_i = R::pres(pi, si), rho_i = R::rho(pi, si);
+    T sum = 0;
+    for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
+      const T sx = Local<T>::kLocal ? T(dx) * k.cs : T(0);
+      const T sy = Local<T>::kLocal ? T(dy) * k.cs : T(0);
+      const T sz = Local<T>::kLocal ? T(dz) * k.cs : T(0);
+      const T bx = xi - sx, by = yi - sy, bz = zi - sz;
+      const uint32_t e = cb[c + 1];
+      for (uint32_t j = cb[c]; j < e; ++j) {
+        const typename R::PV pj = recP[j];
+        const T rx = dsub(bx, R::px(pj)), ry = dsub(by, R::py(pj)), rz = dsub(bz, R::pz(pj));
+        const T r2 = r2_of(rx, ry, rz);
+        if (r2 < k.r2max && (int)j != i) {
+          const typename R::SV sj = recS[j];
+          const T inv_r = inv_sqrt_t(r2);
+          const T r = r2 * inv_r;
+          const T ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
+          const T UL = -(vxi * ex + vyi * ey + vzi * ez);
+          const T UR = -(R::vx(pj, sj) * ex + R::vy(pj, sj) * ey + R::vz(pj, sj) * ez);
+          const T rho_j = R::rho(pj, sj);
+          const T rbar = k.half * (rho_i + rho_j);
+          const T Us = k.half * (UL + UR) + div_t(p_i - R::pres(pj, sj), T(2) * rbar * k.c0);
+          sum += div_t(k.m, rho_j) * wendland_dr(k, r) * (UL - Us);
+        }
+      }
+      if (P.nw > 0) {
+        const uint32_t we = wcb[c + 1];
+        for (uint32_t w = wcb[c]; w < we; ++w) {
+          const typename WR::WV pw = wall[w];
+          const T rx = dsub(bx, pw.x), ry = dsub(by, pw.y), rz = dsub(bz, WR::z(pw));
+          const T r2 = r2_of(rx, ry, rz);
+          if (r2 < k.r2max) {
+            const T inv_r = inv_sqrt_t(r2);
+            const T r = r2 * inv_r;
+            const T ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
+            const T gdot = -(rx * k.g[0] + ry * k.g[1] + rz * k.g[2]);
+            const T pw_ = p_i + rho_i * gdot;
+            const T rho_w = k.rho0 + pw_ * k.inv_c0sq;
+            const T UL = -(vxi * ex + vyi * ey + vzi * ez);
+            const T rbar = k.half * (rho_i + rho_w);
+            // U_R = -U_L, so (U_L + U_R)/2 = 0
+            const T Us = div_t(p_i - pw_, T(2) * rbar * k.c0);
+            sum += div_t(k.m, rho_w) * wendland_dr(k, r) * (UL - Us);
+          }
+        }
+      }
+    });
+    const T dr = T(-2) * rho_i * sum;
+    S.drho[i] = dr;
+    double rho = S.rho[i] + hdt * (double)dr;
+    if (!(fabs(rho) <= 1e300)) bad = 1;
+    S.rho[i] = rho;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&sc->flags, kFlagNonFinite);
+}
+
+// Wall setup: gather sorted wall positions (double SoA for the parity kernel,
+// records for the loops) and ids from the unsorted staging copy.
+template <int D, class T>
+__global__ void k_wall_gather(Params P, DevBuffers B, const double* __restrict__ ux,
+                              const double* __restrict__ uy, const double* __restrict__ uz,
+                              double* wx, double* wy, double* wz) {
+  using WR = WallRec<D, T>;
+  const uint32_t* perm = B.vals[B.sorted_buf];
+  const uint32_t* keys = B.keys[B.sorted_buf];
+  typename WR::WV* out = (typename WR::WV*)B.wallP;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.nw; k += gridDim.x * blockDim.x) {
+    uint32_t j = perm[k];
+    double x = ux[j], y = uy[j], z = D == 3 ? uz[j] : 0.0;
+    wx[k] = x;
+    wy[k] = y;
+    if (D == 3) wz[k] = z;
+    B.wall_id[k] = j;
+    T ox, oy, oz;
+    Local<T>::enc(P, decode(keys[k], P), x, y, z, ox, oy, oz);
+    out[k] = WR::make(ox, oy, oz);
+  }
+}
+
+// ---------------------------------------------------------------------------
+inline int grid_for(int n, int block, int cap) {
+  int b = (n + block - 1) / block;
+  if (b > cap) b = cap;
+  return b < 1 ? 1 : b;
+}
+
+template <int D, class T>
+void enqueue_rebuild(const StageArgs& a, cudaStream_t s, int gated) {
+  const Params& P = a.P;
+  const LaunchCfg& L = a.L;
+  DevBuffers B = a.B;
+  uint32_t* keys[2] = {B.keys[0], B.keys[1]};
+  uint32_t* vals[2] = {B.vals[0], B.vals[1]};
+  launch_cell_keys_par(P, L, B.x, keys[0], vals[0], P.n, B.sc, gated, B.digit_total, s);
+  B.sorted_buf = launch_radix_sort(L, keys, vals, P.n, B.tile_hist, B.digit_total, B.sc, gated, s);
+  k_reorder<D, T><<<grid_for(P.n, L.block_stream, L.blocks_stream), L.block_stream, 0, s>>>(
+      P, B, gated);
+  launch_cell_offsets(B.keys[B.sorted_buf], P.n, P.ncell, B.cell_begin, B.sc, gated, 1, s);
+}
+
+template <int D, class T>
+void enqueue_step_t(const StageArgs& a, cudaStream_t s) {
+  const Params& P = a.P;
+  const LaunchCfg& L = a.L;
+  const DevBuffers& B = a.B;
+  const KC<T> k = make_kc<T>(P);
+  launch_control(P, B.sc, s);
+  enqueue_rebuild<D, T>(a, s, 1);
+  const int gl = grid_for(P.n, L.block_loop, L.blocks_loop);
+  const int gs = grid_for(P.n, L.block_stream, L.blocks_stream);
+  k_density_summation<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, 1);
+  k_viscous<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, 1);
+  k_half1<D, T><<<gs, L.block_stream, 0, s>>>(P, B);
+  k_pressure<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k);
+  k_density_relax<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k);
+}
+
+template <int D, class T>
+void enqueue_initial_sort_t(const StageArgs& a, cudaStream_t s) {
+  enqueue_rebuild<D, T>(a, s, 0);
+}
+
+template <int D, class T>
+void enqueue_wall_setup_t(const StageArgs& a, cudaStream_t s) {
+  const Params& P = a.P;
+  const LaunchCfg& L = a.L;
+  DevBuffers B = a.B;
+  const double* ux = B.io;
+  const double* uy = B.io + P.nw;
+  const double* uz = B.io + 2 * (size_t)P.nw;
+  double* wx = B.wall_xyz;
+  double* wy = wx + P.nw;
+  double* wz = wy + P.nw;
+  const double* xs[3] = {ux, uy, uz};
+  uint32_t* keys[2] = {B.keys[0], B.keys[1]};
+  uint32_t* vals[2] = {B.vals[0], B.vals[1]};
+  launch_cell_keys(P, L, xs, keys[0], vals[0], P.nw, nullptr, 0, B.digit_total, s);
+  B.sorted_buf = launch_radix_sort(L, keys, vals, P.nw, B.tile_hist, B.digit_total, B.sc, 0, s);
+  k_wall_gather<D, T><<<grid_for(P.nw, 256, L.blocks_stream), 256, 0, s>>>(P, B, ux, uy, uz, wx,
+                                                                          wy, wz);
+  launch_cell_offsets(B.keys[B.sorted_buf], P.nw, P.ncell, B.wall_cb, B.sc, 0, 0, s);
+}
+
+}  // namespace stages
+}  // namespace sphgb

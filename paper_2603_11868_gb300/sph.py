@@ -1,0 +1,314 @@
+"""Python binding of libsph.so (include/sph.h).
+
+Argument marshalling only: every step of the SPH path runs in the library's
+CUDA kernels.  The functions keep the C names (sph_create, sph_set_particles,
+sph_step, sph_get_fields, ...); ``Solver`` wraps one context for convenience.
+
+PyTorch is used for plumbing only: device memory comes from its caching
+allocator (through the allocator callbacks of the C ABI) and work is queued on
+its current CUDA stream.  There is no CPU path: if the library or a CUDA
+device is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsph.so")
+
+# enums of include/sph.h
+SPH_FP64, SPH_MIXED = 0, 1
+SPH_FLUID, SPH_WALL = 0, 1
+SPH_OK, SPH_E_INVALID, SPH_E_OOM, SPH_E_CUDA, SPH_E_OUT_OF_DOMAIN, SPH_E_NONFINITE, \
+    SPH_E_TIMEOUT, SPH_E_STATE = range(8)
+SPH_F_POS, SPH_F_VEL, SPH_F_RHO, SPH_F_P, SPH_F_DRHO, SPH_F_ACC, SPH_F_APRIOR, SPH_F_SIGMA = \
+    (1 << k for k in range(8))
+SPH_OPT_RECORD_DIAGNOSTICS, SPH_OPT_USE_GRAPH, SPH_OPT_BLOCK, SPH_OPT_RADIX_BITS = 1, 2, 3, 4
+_VECTOR_FIELDS = (SPH_F_POS, SPH_F_VEL, SPH_F_ACC, SPH_F_APRIOR)
+FIELD_NAMES = {"pos": SPH_F_POS, "vel": SPH_F_VEL, "rho": SPH_F_RHO, "p": SPH_F_P,
+               "drho": SPH_F_DRHO, "acc": SPH_F_ACC, "aprior": SPH_F_APRIOR,
+               "sigma": SPH_F_SIGMA}
+STATUS_NAMES = {0: "SPH_OK", 1: "SPH_E_INVALID", 2: "SPH_E_OOM", 3: "SPH_E_CUDA",
+                4: "SPH_E_OUT_OF_DOMAIN", 5: "SPH_E_NONFINITE", 6: "SPH_E_TIMEOUT",
+                7: "SPH_E_STATE"}
+
+# every symbol include/sph.h declares
+EXPORTS = ("sph_create", "sph_set_particles", "sph_step", "sph_get_fields", "sph_get_scalars",
+           "sph_count", "sph_cell_count", "sph_debug_neighbour_state",
+           "sph_debug_neighbour_stats", "sph_set_option", "sph_synchronize", "sph_last_error",
+           "sph_destroy")
+
+
+class sph_domain(C.Structure):
+    _fields_ = [("dim", C.c_int), ("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+
+
+class sph_material(C.Structure):
+    _fields_ = [("rho0", C.c_double), ("c0", C.c_double), ("mu", C.c_double),
+                ("U_ref", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class sph_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+class SphError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load libsph.so (built in-tree by paper_2603_11868_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libsph.so not built ({p}); run __graft_entry__.build() or "
+                               "python -m paper_2603_11868_gb300.build")
+        L = C.CDLL(p)
+        vp, i, sz, d = C.c_void_p, C.c_int, C.c_size_t, C.c_double
+        L.sph_create.restype = i
+        L.sph_create.argtypes = [C.POINTER(sph_domain), d, d, C.POINTER(sph_material), vp, i,
+                                 C.POINTER(sph_allocator), vp, C.POINTER(vp)]
+        L.sph_set_particles.restype = i
+        L.sph_set_particles.argtypes = [vp, i, sz, vp, vp, vp]
+        L.sph_step.restype = i
+        L.sph_step.argtypes = [vp, i]
+        L.sph_get_fields.restype = i
+        L.sph_get_fields.argtypes = [vp, C.c_uint, vp]
+        L.sph_get_scalars.restype = i
+        L.sph_get_scalars.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.sph_count.restype = sz
+        L.sph_count.argtypes = [vp, i]
+        L.sph_cell_count.restype = sz
+        L.sph_cell_count.argtypes = [vp]
+        L.sph_debug_neighbour_state.restype = i
+        L.sph_debug_neighbour_state.argtypes = [vp, vp, vp, vp, vp]
+        L.sph_debug_neighbour_stats.restype = i
+        L.sph_debug_neighbour_stats.argtypes = [vp, vp, vp, vp]
+        L.sph_set_option.restype = i
+        L.sph_set_option.argtypes = [vp, i, C.c_long]
+        L.sph_synchronize.restype = i
+        L.sph_synchronize.argtypes = [vp, d]
+        L.sph_last_error.restype = C.c_char_p
+        L.sph_last_error.argtypes = [vp]
+        L.sph_destroy.restype = None
+        L.sph_destroy.argtypes = [vp]
+        _lib = L
+        return L
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(ctx, rc):
+    if rc != SPH_OK:
+        msg = load().sph_last_error(ctx).decode() if ctx else ""
+        raise SphError(rc, msg)
+
+
+# --- the C entry points, same names --------------------------------------
+def sph_create(dim, lo, hi, dp, h, rho0, c0, mu, U_ref, gravity, precision=SPH_MIXED,
+               allocator: sph_allocator | None = None, stream: int = 0):
+    L = load()
+    dom = sph_domain(int(dim), (C.c_double * 3)(*list(lo) + [0.0] * (3 - len(lo))),
+                     (C.c_double * 3)(*list(hi) + [0.0] * (3 - len(hi))))
+    mat = sph_material(rho0, c0, mu, U_ref)
+    g = np.zeros(3)
+    g[: len(gravity)] = gravity
+    out = C.c_void_p()
+    rc = L.sph_create(C.byref(dom), dp, h, C.byref(mat), _ptr(g), int(precision),
+                      C.byref(allocator) if allocator is not None else None,
+                      C.c_void_p(stream) if stream else None, C.byref(out))
+    _check(None, rc)
+    return out.value
+
+
+def sph_set_particles(ctx, kind, pos, vel=None, rho=None):
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    vel = None if vel is None else np.ascontiguousarray(vel, dtype=np.float64)
+    rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+    _check(ctx, load().sph_set_particles(ctx, int(kind), len(pos), _ptr(pos), _ptr(vel),
+                                         _ptr(rho)))
+
+
+def sph_step(ctx, n):
+    _check(ctx, load().sph_step(ctx, int(n)))
+
+
+def sph_get_fields(ctx, mask, n, dim):
+    comps = sum(dim if (mask & b) and b in _VECTOR_FIELDS else (1 if mask & b else 0)
+                for b in (1 << k for k in range(8)))
+    out = np.empty(n * comps, dtype=np.float64)
+    _check(ctx, load().sph_get_fields(ctx, int(mask), _ptr(out)))
+    res, off = {}, 0
+    for name, b in FIELD_NAMES.items():
+        if mask & b:
+            c = dim if b in _VECTOR_FIELDS else 1
+            a = out[off: off + n * c]
+            res[name] = a.reshape(n, dim) if c > 1 else a
+            off += n * c
+    return res
+
+
+def sph_get_scalars(ctx):
+    t, dta, dtc = C.c_double(), C.c_double(), C.c_double()
+    nac, nad = C.c_long(), C.c_long()
+    _check(ctx, load().sph_get_scalars(ctx, C.byref(t), C.byref(dta), C.byref(dtc),
+                                       C.byref(nac), C.byref(nad)))
+    return dict(t=t.value, dt_ad=dta.value, dt_ac=dtc.value, n_ac=nac.value, n_adv=nad.value)
+
+
+def sph_count(ctx, kind=SPH_FLUID):
+    return load().sph_count(ctx, int(kind))
+
+
+def sph_cell_count(ctx):
+    return load().sph_cell_count(ctx)
+
+
+def sph_debug_neighbour_state(ctx, n, ncell):
+    keys = np.empty(n, np.uint32); perm = np.empty(n, np.uint32)
+    ids = np.empty(n, np.uint32); cb = np.empty(ncell + 1, np.uint32)
+    _check(ctx, load().sph_debug_neighbour_state(ctx, _ptr(keys), _ptr(perm), _ptr(ids),
+                                                 _ptr(cb)))
+    return dict(keys=keys, perm=perm, ids=ids, cell_begin=cb)
+
+
+def sph_debug_neighbour_stats(ctx, n):
+    cf = np.empty(n, np.uint32); cw = np.empty(n, np.uint32); hs = np.empty(n, np.uint64)
+    _check(ctx, load().sph_debug_neighbour_stats(ctx, _ptr(cf), _ptr(cw), _ptr(hs)))
+    return cf, cw, hs
+
+
+def sph_set_option(ctx, option, value):
+    _check(ctx, load().sph_set_option(ctx, int(option), int(value)))
+
+
+def sph_synchronize(ctx, timeout_s=0.0):
+    _check(ctx, load().sph_synchronize(ctx, float(timeout_s)))
+
+
+def sph_last_error(ctx):
+    return load().sph_last_error(ctx).decode()
+
+
+def sph_destroy(ctx):
+    load().sph_destroy(ctx)
+
+
+# --- PyTorch plumbing ------------------------------------------------------
+class TorchAllocator:
+    """Allocator callbacks backed by torch's CUDA caching allocator."""
+
+    def __init__(self, device: int | None = None):
+        import torch
+        self._torch = torch
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self._alloc = ALLOC_FN(self._on_alloc)
+        self._free = FREE_FN(self._on_free)
+        self.struct = sph_allocator(self._alloc, self._free, None)
+
+    def _on_alloc(self, nbytes, stream, user):
+        try:
+            return self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                            stream=int(stream or 0))
+        except Exception:  # out of memory -> NULL -> SPH_E_OOM
+            return None
+
+    def _on_free(self, ptr, nbytes, stream, user):
+        self._torch.cuda.caching_allocator_delete(int(ptr))
+
+
+class Solver:
+    """One SPH context.  ``case`` is a ``cases.Case`` (or anything with the same
+    attributes).  ``precision`` is "fp64" or "mixed"."""
+
+    def __init__(self, case, precision: str = "mixed", torch_memory: bool = True,
+                 stream: int | None = None):
+        self.case = case
+        self.dim = case.dim
+        self.precision = SPH_FP64 if precision == "fp64" else SPH_MIXED
+        self._allocator = None
+        if torch_memory:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("no CUDA device: the SPH library has no CPU path")
+            self._allocator = TorchAllocator()
+            if stream is None:
+                stream = torch.cuda.current_stream().cuda_stream
+        self.ctx = sph_create(case.dim, case.lo, case.hi, case.dp, case.h, case.rho0, case.c0,
+                              case.mu, case.U_ref, case.gravity, self.precision,
+                              self._allocator.struct if self._allocator else None, stream or 0)
+        if case.wall is not None and len(case.wall):
+            sph_set_particles(self.ctx, SPH_WALL, case.wall)
+        sph_set_particles(self.ctx, SPH_FLUID, case.fluid, case.vel, case.rho)
+
+    @property
+    def n(self):
+        return sph_count(self.ctx, SPH_FLUID)
+
+    @property
+    def nw(self):
+        return sph_count(self.ctx, SPH_WALL)
+
+    @property
+    def ncell(self):
+        return sph_cell_count(self.ctx)
+
+    def set_fluid(self, pos, vel=None, rho=None):
+        sph_set_particles(self.ctx, SPH_FLUID, pos, vel, rho)
+
+    def step(self, n: int = 1):
+        sph_step(self.ctx, n)
+
+    def fields(self, *names):
+        mask = 0
+        for nm in names:
+            mask |= FIELD_NAMES[nm]
+        return sph_get_fields(self.ctx, mask, self.n, self.dim)
+
+    def field(self, name):
+        return self.fields(name)[name]
+
+    def scalars(self):
+        return sph_get_scalars(self.ctx)
+
+    def set_option(self, option, value):
+        sph_set_option(self.ctx, option, value)
+
+    def neighbour_state(self):
+        return sph_debug_neighbour_state(self.ctx, self.n, self.ncell)
+
+    def neighbour_stats(self):
+        return sph_debug_neighbour_stats(self.ctx, self.n)
+
+    def synchronize(self, timeout_s=0.0):
+        sph_synchronize(self.ctx, timeout_s)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            sph_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,326 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Bars (stated per field):
+  - cell keys, sort permutation, user ids, CSR offsets, neighbour counts and
+    neighbour fingerprints: bit-exact;
+  - FP64 path after one acoustic step: every field within 1e-10 relative
+    (max-norm error / max-norm of the reference field);
+  - mixed path after one step: pressure and prior accelerations within 1e-5 of
+    max(|a_ref|_inf, g); other fields within the tolerances written below;
+  - mixed path over the run: surge front and kinetic energy within 1% at
+    common times (linear interpolation of the oracle series).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2603_11868_gb300 import cases
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def sph():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2603_11868_gb300 import build
+    build.build()
+    from paper_2603_11868_gb300 import sph as S
+    S.load()
+    return S
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.lib()
+    return oracle
+
+
+def small_3d():
+    return cases.dam_break_3d(dp=0.02, seed=1)  # 20 x 34 x 15 = 10 200 fluid
+
+
+def rel(got, want):
+    den = np.abs(want).max()
+    return np.abs(got - want).max() / (den if den > 0 else 1.0)
+
+
+SORT_CASES = {
+    "dam_break_2d": lambda: cases.dam_break_2d(),
+    "dam_break_3d_small": small_3d,
+    "cloud_2d_ragged": lambda: cases.random_cloud(2, 4097, seed=3, dp=0.02),
+    "cloud_3d_ragged": lambda: cases.random_cloud(3, 12345, seed=4, dp=0.05),
+    "single_particle": lambda: cases.random_cloud(3, 1, seed=5),
+    "one_cell_crowd": lambda: cases.random_cloud(2, 5000, seed=6, box=0.01, dp=0.05),
+}
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("name", sorted(SORT_CASES))
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sort_state_bit_exact(sph, O, name, precision):
+    case = SORT_CASES[name]()
+    s = sph.Solver(case, precision=precision)
+    o = O.Oracle.from_case(case)
+    got, want = s.neighbour_state(), o.neighbour_state()
+    for k in ("keys", "perm", "ids", "cell_begin"):
+        assert np.array_equal(got[k], want[k]), k
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["dam_break_2d", "dam_break_3d_small", "cloud_3d_ragged"])
+def test_neighbour_sets_bit_exact(sph, O, name):
+    case = SORT_CASES[name]()
+    o = O.Oracle.from_case(case)
+    want = o.neighbour_stats()
+    for precision in ("fp64", "mixed"):
+        s = sph.Solver(case, precision=precision)
+        got = s.neighbour_stats()
+        for g, w in zip(got, want):
+            assert np.array_equal(g, w)
+        s.close()
+
+
+def test_resort_of_evolved_positions_bit_exact(sph, O):
+    """Positions after 30 steps (non-lattice, moved particles) re-binned by both."""
+    case = cases.dam_break_2d()
+    s = sph.Solver(case, precision="fp64")
+    s.step(30)
+    f = s.fields("pos", "vel", "rho")
+    s.set_fluid(f["pos"], f["vel"], f["rho"])
+    o = O.Oracle.from_case(case, set_particles=False)
+    o.set_wall(case.wall)
+    o.set_fluid(f["pos"], f["vel"], f["rho"])
+    got, want = s.neighbour_state(), o.neighbour_state()
+    for k in ("keys", "perm", "ids", "cell_begin"):
+        assert np.array_equal(got[k], want[k]), k
+    for g, w in zip(s.neighbour_stats(), o.neighbour_stats()):
+        assert np.array_equal(g, w)
+    s.close()
+
+
+# --------------------------------------------------------------------------
+def _oracle_fields(o, O):
+    return {"pos": o.field(O.POS), "vel": o.field(O.VEL), "rho": o.field(O.RHO),
+            "p": o.field(O.P), "drho": o.field(O.DRHO), "acc": o.field(O.ACC),
+            "aprior": o.field(O.APRIOR), "sigma": o.field(O.SIGMA)}
+
+
+def _run_pair(sph, O, case, precision, steps, diag=True, graph=True):
+    s = sph.Solver(case, precision=precision)
+    if diag:
+        s.set_option(sph.SPH_OPT_RECORD_DIAGNOSTICS, 1)
+    s.set_option(sph.SPH_OPT_USE_GRAPH, 1 if graph else 0)
+    s.step(steps)
+    got = s.fields(*sph.FIELD_NAMES)
+    sc = s.scalars()
+    s.close()
+    o = O.Oracle.from_case(case)
+    o.step(steps)
+    return got, _oracle_fields(o, O), sc, o.scalars()
+
+
+@pytest.mark.parametrize("name", ["dam_break_2d", "dam_break_3d_small"])
+def test_fp64_one_step(sph, O, name):
+    case = SORT_CASES[name]()
+    got, want, sc, osc = _run_pair(sph, O, case, "fp64", 1)
+    for k in want:
+        assert rel(got[k], want[k]) <= 1e-10, (k, rel(got[k], want[k]))
+    assert sc["n_ac"] == osc["n_ac"] == 1 and sc["n_adv"] == osc["n_adv"] == 1
+    assert sc["dt_ac"] == osc["dt_ac"] and sc["dt_ad"] == osc["dt_ad"] and sc["t"] == osc["t"]
+
+
+def test_fp64_many_steps(sph, O):
+    """40 steps = 8 advection steps (8 rebuilds) of the 2D dam break."""
+    case = cases.dam_break_2d()
+    got, want, sc, osc = _run_pair(sph, O, case, "fp64", 40)
+    for k in ("pos", "vel", "rho", "p", "drho", "aprior", "acc"):
+        assert rel(got[k], want[k]) <= 1e-8, (k, rel(got[k], want[k]))
+    assert sc["n_adv"] == osc["n_adv"] and sc["n_ac"] == osc["n_ac"]
+    assert abs(sc["t"] - osc["t"]) <= 1e-12 * osc["t"]
+
+
+@pytest.mark.parametrize("name", ["dam_break_2d", "dam_break_3d_small"])
+def test_mixed_one_step(sph, O, name):
+    case = SORT_CASES[name]()
+    got, want, sc, osc = _run_pair(sph, O, case, "mixed", 1)
+    g = np.abs(case.gravity).max()
+    for k in ("acc", "aprior"):
+        den = max(np.abs(want[k]).max(), g)
+        err = np.abs(got[k] - want[k]).max() / den
+        assert err <= 1e-5, (k, err)
+    assert np.abs(got["pos"] - want["pos"]).max() <= 1e-6 * case.dp
+    assert rel(got["vel"], want["vel"]) <= 1e-5
+    assert rel(got["rho"], want["rho"]) <= 1e-6
+    assert rel(got["sigma"], want["sigma"]) <= 1e-6
+    assert rel(got["drho"], want["drho"]) <= 1e-4
+    assert sc["n_adv"] == osc["n_adv"] == 1
+
+
+def test_graph_and_eager_identical(sph):
+    case = cases.dam_break_2d()
+    out = []
+    for graph in (True, False):
+        s = sph.Solver(case, precision="fp64")
+        s.set_option(sph.SPH_OPT_USE_GRAPH, 1 if graph else 0)
+        s.step(12)
+        out.append(s.fields("pos", "vel", "rho"))
+        s.close()
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_deterministic(sph, precision):
+    case = small_3d()
+    out = []
+    for _ in range(2):
+        s = sph.Solver(case, precision=precision)
+        s.step(15)
+        out.append(s.fields("pos", "vel", "rho"))
+        s.close()
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k])
+
+
+def _series(path):
+    a = np.loadtxt(path)
+    return a[:, 1], a[:, 2], a[:, 3]
+
+
+def _front_ke_run(sph, case, steps, precision="mixed", chunk=1):
+    s = sph.Solver(case, precision=precision)
+    t, f, k = [0.0], [case.fluid[:, 0].max()], [0.0]
+    m = case.rho0 * case.dp ** case.dim
+    done = 0
+    while done < steps:
+        s.step(chunk)
+        done += chunk
+        d = s.fields("pos", "vel")
+        t.append(s.scalars()["t"])
+        f.append(d["pos"][:, 0].max())
+        k.append(0.5 * m * (d["vel"] ** 2).sum())
+    s.close()
+    return np.array(t), np.array(f), np.array(k)
+
+
+def _compare_series(t, f, k, ot, of, ok, x0):
+    tc = t[(t > 0) & (t <= ot[-1])]
+    f_ref = np.interp(tc, ot, of)
+    k_ref = np.interp(tc, ot, ok)
+    f_got = np.interp(tc, t, f)
+    k_got = np.interp(tc, t, k)
+    ferr = np.abs(f_got - f_ref) / np.maximum(np.abs(f_ref - x0), 1e-12)
+    # the front moves from x0; relative to the travelled distance once it has moved
+    moved = np.abs(f_ref - x0) > 0.05 * np.abs(of[-1] - x0)
+    kerr = np.abs(k_got - k_ref) / np.maximum(k_ref, 1e-300)
+    late = k_ref > 0.05 * ok.max()
+    return ferr[moved].max(initial=0.0), kerr[late].max(initial=0.0)
+
+
+def test_mixed_front_and_energy_2d(sph):
+    path = os.path.join(HERE, "golden", "dam_break_2d_front_ke.txt")
+    ot, of, ok = _series(path)
+    case = cases.dam_break_2d()
+    t, f, k = _front_ke_run(sph, case, 200, chunk=5)
+    ferr, kerr = _compare_series(t, f, k, ot, of, ok, of[0])
+    assert ferr <= 0.01 and kerr <= 0.01, (ferr, kerr)
+
+
+def test_mixed_front_and_energy_3d(sph):
+    path = os.path.join(HERE, "golden", "dam_break_3d_front_ke.txt")
+    if not os.path.exists(path):
+        pytest.skip("3D golden series not generated")
+    ot, of, ok = _series(path)
+    case = cases.dam_break_3d()
+    t, f, k = _front_ke_run(sph, case, 1000, chunk=25)
+    ferr, kerr = _compare_series(t, f, k, ot, of, ok, of[0])
+    assert ferr <= 0.01 and kerr <= 0.01, (ferr, kerr)
+
+
+# --------------------------------------------------------------------------
+def test_errors_and_state(sph):
+    case = cases.dam_break_2d(dp=0.05)
+    s = sph.Solver(case, precision="mixed")
+    with pytest.raises(sph.SphError) as e:
+        s.set_option(sph.SPH_OPT_BLOCK, 100)
+    assert e.value.code == sph.SPH_E_INVALID
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_step(s.ctx, -1)
+    assert e.value.code == sph.SPH_E_INVALID
+    s.close()
+    ctx = sph.sph_create(2, case.lo, case.hi, case.dp, case.h, 1.0, 20.0, 0.0, 2.0, (0, -1))
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_step(ctx, 1)
+    assert e.value.code == sph.SPH_E_STATE
+    sph.sph_destroy(ctx)
+
+
+def test_out_of_domain_flag(sph):
+    case = cases.dam_break_2d(dp=0.05)
+    pos = case.fluid.copy()
+    pos[3] = [100.0, 100.0]
+    case.fluid = pos
+    s = sph.Solver(case, precision="fp64")
+    with pytest.raises(sph.SphError) as e:
+        s.synchronize()
+    assert e.value.code == sph.SPH_E_OUT_OF_DOMAIN
+    s.close()
+
+
+def test_nonfinite_flag(sph):
+    case = cases.dam_break_2d(dp=0.05)
+    vel = np.zeros_like(case.fluid)
+    vel[5, 0] = np.nan
+    case.vel = vel
+    s = sph.Solver(case, precision="mixed")
+    s.step(1)
+    with pytest.raises(sph.SphError) as e:
+        s.synchronize()
+    assert e.value.code == sph.SPH_E_NONFINITE
+    s.close()
+
+
+def test_bounded_wait_times_out_then_completes(sph):
+    case = small_3d()
+    s = sph.Solver(case, precision="fp64")
+    s.step(200)
+    with pytest.raises(sph.SphError) as e:
+        s.synchronize(timeout_s=1e-6)
+    assert e.value.code == sph.SPH_E_TIMEOUT
+    s.synchronize(timeout_s=0)
+    assert s.scalars()["n_ac"] == 200
+    s.close()
+
+
+# --------------------------------------------------------------------------
+def test_full_size_sampled_density(sph, O):
+    """5.1 M-particle 3D dam break in the benchmark's launch configuration
+    (mixed, graph replay): the kernel sums of the first density summation on
+    2000 sampled particles against the oracle, plus invariants at full size."""
+    case = cases.dam_break_3d(dp=0.0025, seed=2)
+    s = sph.Solver(case, precision="mixed")
+    s.set_option(sph.SPH_OPT_RECORD_DIAGNOSTICS, 1)
+    s.step(1)
+    sig = s.field("sigma")
+    o = O.Oracle.from_case(case)
+    rng = np.random.default_rng(0)
+    ids = rng.choice(case.n, 2000, replace=False).astype(np.uint32)
+    want = o.sample_sigma(ids)
+    assert rel(sig[ids], want) <= 1e-6
+    del o
+    st = s.neighbour_state()
+    assert np.array_equal(np.sort(st["ids"]), np.arange(case.n, dtype=np.uint32))
+    assert np.all(np.diff(st["keys"].astype(np.int64)) >= 0)
+    s.set_option(sph.SPH_OPT_RECORD_DIAGNOSTICS, 0)
+    s.step(20)
+    f = s.fields("pos", "vel", "rho")
+    assert np.isfinite(f["pos"]).all() and np.isfinite(f["vel"]).all()
+    assert f["rho"].min() > 0.98 * case.rho0 and f["rho"].max() < 1.05 * case.rho0
+    s.close()

@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Particle-steps/s of the weakly-compressible SPH hot path on GB300.
+
+Workload (default): the 3D dam break at dp = 0.0025 -- tank 1.6 x 0.67 x 0.6,
+water column 0.4 x 0.67 x 0.3 (160 x 268 x 120 = 5 145 600 fluid particles on a
+lattice with seeded +-0.01 dp jitter), 3 open-top wall layers (1 847 172 wall
+particles), Wendland C2 with h = 1.3 dp, rho0 = 1000, g = 9.81,
+c0 = 10 sqrt(2 g H), mixed precision (float pair arithmetic, double state).
+
+One bench step = sph_step(SUBSTEPS) = SUBSTEPS acoustic steps (default 10),
+which always spans at least two advection steps, so every stage of the hot
+path (cell keys, radix sort, reorder, cell offsets, density summation,
+viscous force, both half-steps, pressure and density relaxation, time-step
+reductions) runs inside every bench step.  value = fluid particles x acoustic
+steps / device time, summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Inputs stay resident in HBM (about 1.5 GB of state, far above the 129 MB L2,
+so no L2 flush is needed between steps).  Under torchrun each rank runs its
+own replica (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s, 5M-particle 3D dam break, FP32-mixed vs FP64 on one GB300"
+SUBSTEPS = 10
+
+# Algorithmic (compulsory) bytes per fluid particle and launch of each stage
+# in mixed precision, 3D: every per-particle array read / written once, each
+# neighbour record read once (neighbour re-reads are meant to hit L2), plus
+# the cell offsets and the static wall records.  Derivation in the design doc.
+BYTES_PER_PARTICLE_MIXED_3D = {
+    "keys": 24 + 8,                     # read x; write key, index
+    "sort": 3 * (4 + 8 + 8),            # per pass: histogram read, scatter read + write
+    "reorder": 4 + 48 + 8 + 4 + 4 + 4 + 48 + 8 + 4 + 4 + 32,  # gather state, write state + records
+    "offsets": 4 + 2,                   # keys, offsets (about 0.5 cells per particle)
+    "density_sum": 4 + 16 + 8 + 32 + 4,  # key, own record, rho, record S r/w, offsets
+    "viscous": 4 + 32 + 12 + 4,         # key, records, a_prior, offsets
+    "half1": 24 + 24 + 8 + 4 + 4 + 24 + 8 + 32,  # x, v, rho, drho, key; x, rho, records
+    "pressure": 4 + 32 + 12 + 24 + 24 + 24 + 24 + 32 + 4,  # + records out, offsets
+    "density_relax": 4 + 32 + 8 + 4 + 8 + 4,  # key, records, rho r/w, drho, offsets
+    "control": 0,
+}
+WALL_RECORD_BYTES_3D = 16  # read once per neighbour loop
+
+
+def source_fingerprint() -> str:
+    h = hashlib.sha1()
+    for f in ("sph_stages.cuh", "sph_nsearch.cu", "sph_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2603_11868_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+# dram read + write bytes per launch from an ncu capture of the named kernel,
+# keyed by the fingerprint of the kernel sources it was taken on (see
+# profiles/); a stale fingerprint reports traffic as null.
+NCU_TRAFFIC = {}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+# --------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self) -> dict:
+        rows = [r.split(",") for r in self.out.strip().splitlines() if r.count(",") >= 5]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].strip().replace(".", "").isdigit()]
+        smax = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[2 + k].strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(name: str):
+    from paper_2603_11868_gb300 import cases
+    if name == "dam_break_3d_5m":
+        return cases.dam_break_3d(dp=0.0025, seed=2), "3D dam break, dp=0.0025"
+    if name == "dam_break_3d_80k":
+        return cases.dam_break_3d(dp=0.01, seed=1), "3D dam break, dp=0.01"
+    if name == "dam_break_2d":
+        return cases.dam_break_2d(), "2D dam break, dp=0.025"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def cpu_oracle_sample(seconds_cap: float = 30.0) -> dict:
+    """The FP64 oracle as it stands, serial, on the host: the same 3D dam break
+    at dp = 0.01 (80 400 fluid + 120 234 wall particles: same lattice, h / dp,
+    wall layers and per-particle neighbour counts as the 5.1 M workload), one
+    initial bin/sort + acoustic steps (with their rebuilds) until about 10 s."""
+    from oracle import oracle
+    from paper_2603_11868_gb300 import cases
+    case = cases.dam_break_3d(dp=0.01, seed=1)
+    o = oracle.Oracle.from_case(case)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < 200:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > 10.0 or el * (steps + 1) / steps > seconds_cap:
+            break
+    el = time.perf_counter() - t0
+    return {"value": case.n * steps / el, "unit": "particle-steps/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"serial FP64 oracle, 3D dam break dp=0.01 ({case.n} fluid + {case.nw} "
+                      f"wall), {steps} acoustic steps incl. rebuilds, {el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    warm = max(0, args.warmup)
+    from oracle import oracle
+    from paper_2603_11868_gb300 import cases
+    case = cases.dam_break_3d(dp=0.01, seed=1)
+    o = oracle.Oracle.from_case(case)
+    # each reference step: one acoustic step of the sample (bounded CPU work)
+    o.step(warm)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    value = case.n * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": warm,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "3D dam break (serial FP64 oracle on host cores; bounded "
+                               "sample dp=0.01, 80 400 fluid + 120 234 wall)",
+                   "precision": "fp64", "sample_fluid": case.n},
+        "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"{args.steps} acoustic steps of the dp=0.01 3D dam break"},
+        "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_steps(solver, steps, substeps, torch):
+    """Device time of `steps` bench steps (events on the caller's stream,
+    which waits on the library's stream)."""
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(steps):
+        solver.step(substeps)
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_ours(args):
+    import torch
+    from paper_2603_11868_gb300 import build, sph
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    sph.load()
+    case, wname = make_workload(args.workload)
+    solver = sph.Solver(case, precision=args.precision)
+    n, nw = case.n, case.nw
+    mean_nb = None
+    if rank == 0 and not args.quick:
+        cf, cw, _ = solver.neighbour_stats()
+        mean_nb = float(cf.mean() + cw.mean())
+    for _ in range(args.warmup):
+        solver.step(args.substeps)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        el = time_steps(solver, args.steps, args.substeps, torch)
+    if dist:
+        t = torch.tensor([el], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el = float(t.item())
+        dist.barrier()
+    acoustic = args.steps * args.substeps
+    value = ws * n * acoustic / el
+    clocks = clk.summary()
+    kps = solver.kernels_per_step()
+    sc = solver.scalars()
+
+    # per-stage device times (stage-by-stage launches with events on the
+    # library stream; the state keeps advancing) -> dominant kernel roofline
+    prof_steps = 2 * args.substeps
+    ms, rebuilds = solver.profile_stages(prof_steps)
+    per_step = {k: v / prof_steps for k, v in ms.items()}
+    rebuild_stages = ("keys", "sort", "reorder", "offsets", "density_sum", "viscous")
+    launches = {k: (rebuilds if k in rebuild_stages else prof_steps) for k in ms}
+    dom = max(ms, key=lambda k: ms[k])
+    peaks = measured_peaks()
+    fp = source_fingerprint()
+    dom_bytes = BYTES_PER_PARTICLE_MIXED_3D.get(dom, 0) * n
+    if dom in ("density_sum", "viscous", "pressure", "density_relax"):
+        dom_bytes += WALL_RECORD_BYTES_3D * nw
+    avg_s = ms[dom] / 1e3 / max(1, launches[dom])
+    achieved = dom_bytes / avg_s / 1e9
+    traffic = NCU_TRAFFIC.get((dom, fp))
+
+    # FP64 path on the same workload for the speed-up (fewer steps)
+    fp64 = None
+    if args.precision == "mixed" and not args.quick and rank == 0:
+        s64 = sph.Solver(case, precision="fp64")
+        s64.step(args.substeps)
+        el64 = time_steps(s64, args.fp64_steps, args.substeps, torch)
+        fp64 = n * args.fp64_steps * args.substeps / el64
+        s64.close()
+
+    # end to end through the C ABI: pinned host input -> set_particles ->
+    # sph_step -> sph_get_fields -> pinned host output, every bench step
+    e2e = None
+    if not args.quick:
+        d = case.dim
+        pin_in = {k: torch.empty(sh, dtype=torch.float64, pin_memory=True).numpy()
+                  for k, sh in (("pos", (n, d)), ("vel", (n, d)), ("rho", (n,)))}
+        pin_in["pos"][:] = case.fluid
+        pin_in["vel"][:] = 0.0
+        pin_in["rho"][:] = case.rho0
+        outbuf = torch.empty(n * (2 * d + 1), dtype=torch.float64, pin_memory=True).numpy()
+        L = sph.load()
+        mask = sph.SPH_F_POS | sph.SPH_F_VEL | sph.SPH_F_RHO
+        ptr = lambda a: a.ctypes.data  # noqa: E731
+        e2e_steps = max(2, args.steps // 5)
+
+        def e2e_step():
+            rc = L.sph_set_particles(solver.ctx, sph.SPH_FLUID, n, ptr(pin_in["pos"]),
+                                     ptr(pin_in["vel"]), ptr(pin_in["rho"]))
+            rc = rc or L.sph_step(solver.ctx, args.substeps)
+            rc = rc or L.sph_get_fields(solver.ctx, mask, ptr(outbuf))
+            if rc:
+                raise RuntimeError(f"e2e step failed: {rc} {sph.sph_last_error(solver.ctx)}")
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        el_e2e = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el_e2e = float(t.item())
+        e2e = {"value": ws * n * e2e_steps * args.substeps / el_e2e, "unit": "particle-steps/s",
+               "h2d_bytes_per_step": n * (2 * d + 1) * 8,
+               "d2h_bytes_per_step": n * (2 * d + 1) * 8}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.quick and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample()
+    solver.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": f"{wname}: {n} fluid + {nw} wall particles, "
+                                   f"{args.substeps} acoustic steps per bench step",
+                       "precision": args.precision, "fluid_particles": n,
+                       "wall_particles": nw, "acoustic_steps_timed": acoustic,
+                       "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                         "peak_source": peaks["source"],
+                         "bytes_per_launch": dom_bytes, "avg_launch_ms": avg_s * 1e3},
+            "stage_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
+            "rebuilds_per_step": rebuilds / prof_steps,
+            "clocks": clocks,
+            "gpu_launches": int(kps * acoustic) if kps > 0 else None,
+            "kernels_per_acoustic_step": kps,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "fp64_value": fp64,
+            "speedup_vs_fp64": (value / ws / fp64) if fp64 else None,
+            "gpips": (value * mean_nb * 2 / 1e9) if mean_nb else None,
+            "sim_time": sc["t"], "source_fingerprint": fp,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="dam_break_3d_5m",
+                    choices=["dam_break_3d_5m", "dam_break_3d_80k", "dam_break_2d"])
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--substeps", type=int, default=SUBSTEPS)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="main number only")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

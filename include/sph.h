@@ -110,8 +110,8 @@ enum sph_field {
 enum sph_option {
   SPH_OPT_RECORD_DIAGNOSTICS = 1, /* 0/1: also store SPH_F_ACC and SPH_F_SIGMA        */
   SPH_OPT_USE_GRAPH = 2,          /* 0/1 (default 1): replay each step as a CUDA graph */
-  SPH_OPT_BLOCK = 3,              /* threads per block of the neighbour loops: 64..1024,
-                                     multiple of 32 (default from the tuner)           */
+  SPH_OPT_BLOCK = 3,              /* threads per block of the neighbour loops: 64..256,
+                                     multiple of 32 (default 128)                      */
   SPH_OPT_RADIX_BITS = 4          /* digit width of the radix sort: 4..11 (default 8)  */
 };
 
@@ -178,6 +178,32 @@ int sph_debug_neighbour_state(sph_ctx* ctx, uint32_t* keys, uint32_t* perm, uint
  * Positions are compared in double precision in both precision modes. */
 int sph_debug_neighbour_stats(sph_ctx* ctx, uint32_t* cnt_fluid, uint32_t* cnt_wall,
                               uint64_t* hash);
+
+/* Stages of one acoustic step, in launch order (sph_profile_stages). */
+enum sph_stage {
+  SPH_STAGE_CONTROL = 0,        /* schedule scalars (one thread)                   */
+  SPH_STAGE_KEYS = 1,           /* cell keys from positions                        */
+  SPH_STAGE_SORT = 2,           /* radix sort, all passes                          */
+  SPH_STAGE_REORDER = 3,        /* gather of the state into sorted order + records */
+  SPH_STAGE_OFFSETS = 4,        /* CSR cell offsets                                */
+  SPH_STAGE_DENSITY_SUM = 5,    /* density summation                               */
+  SPH_STAGE_VISCOUS = 6,        /* viscous force                                   */
+  SPH_STAGE_HALF1 = 7,          /* first half-step                                 */
+  SPH_STAGE_PRESSURE = 8,       /* pressure relaxation + kick + drift              */
+  SPH_STAGE_DENSITY_RELAX = 9,  /* density relaxation                              */
+  SPH_STAGE_COUNT = 10
+};
+
+/* Runs n acoustic steps launched stage by stage (no graph) with CUDA events
+ * around every stage on the context's stream, and adds each stage's device
+ * time in milliseconds to ms[stage] (SPH_STAGE_COUNT entries).  *rebuilds
+ * receives how many of the n steps began an advection step (the stages KEYS
+ * to VISCOUS do work only on those steps).  The state advances exactly as
+ * with sph_step. */
+int sph_profile_stages(sph_ctx* ctx, int n, double* ms, long* rebuilds);
+
+/* Kernel launches one acoustic step queues (graph nodes of the step). */
+long sph_kernels_per_step(const sph_ctx* ctx);
 
 /* Sets an sph_option; takes effect at the next sph_step. */
 int sph_set_option(sph_ctx* ctx, int option, long value);

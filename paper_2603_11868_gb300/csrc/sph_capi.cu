@@ -377,29 +377,25 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
     configure_launch(c);
     DevBuffers& B = c->B;
     if (n > 0) {
-      std::vector<double> soa(n * 3, 0.0);
-      for (int k = 0; k < d; ++k) {
-        for (size_t i = 0; i < n; ++i) soa[k * n + i] = pos[i * d + k];
-        CK(cudaMemcpyAsync(B.x[0][k], &soa[k * n], n * 8, cudaMemcpyHostToDevice, c->stream));
+      // host AoS -> staging -> SoA on the device (no host-side loops)
+      CK(cudaMemcpyAsync(B.io, pos, n * d * 8, cudaMemcpyHostToDevice, c->stream));
+      launch_deinterleave(B.io, (int)n, d, B.x[0], c->stream);
+      if (vel) {
+        CK(cudaMemcpyAsync(B.io, vel, n * d * 8, cudaMemcpyHostToDevice, c->stream));
+        launch_deinterleave(B.io, (int)n, d, B.v[0], c->stream);
+      } else {
+        for (int k = 0; k < d; ++k) CK(cudaMemsetAsync(B.v[0][k], 0, n * 8, c->stream));
       }
-      CK(cudaStreamSynchronize(c->stream));
-      for (int k = 0; k < d; ++k) {
-        for (size_t i = 0; i < n; ++i) soa[k * n + i] = vel ? vel[i * d + k] : 0.0;
-        CK(cudaMemcpyAsync(B.v[0][k], &soa[k * n], n * 8, cudaMemcpyHostToDevice, c->stream));
-      }
-      CK(cudaStreamSynchronize(c->stream));
-      for (size_t i = 0; i < n; ++i) soa[i] = rho ? rho[i] : c->P.rho0;
-      CK(cudaMemcpyAsync(B.rho[0], soa.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
-      std::vector<uint32_t> iota(n);
-      for (size_t i = 0; i < n; ++i) iota[i] = (uint32_t)i;
-      CK(cudaMemcpyAsync(B.id[0], iota.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+      if (rho)
+        CK(cudaMemcpyAsync(B.rho[0], rho, n * 8, cudaMemcpyHostToDevice, c->stream));
+      launch_init_fluid(B.rho[0], rho ? 0 : 1, c->P.rho0, B.id[0], (int)n, c->stream);
       CK(cudaMemsetAsync(B.drho[0], 0, n * tsize(c), c->stream));
       for (int k = 0; k < d; ++k) {
         CK(cudaMemsetAsync(B.acc[k], 0, n * tsize(c), c->stream));
         CK(cudaMemsetAsync(B.aprior[k], 0, n * tsize(c), c->stream));
       }
       CK(cudaMemsetAsync(B.sigma, 0, n * tsize(c), c->stream));
-      CK(cudaStreamSynchronize(c->stream));
+      CK(cudaGetLastError());
     }
     DevScalars z{};
     CK(cudaMemcpyAsync(B.sc, &z, sizeof(z), cudaMemcpyHostToDevice, c->stream));
@@ -456,10 +452,11 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
       c->P.nw = 0;
       return set_err(c, SPH_E_OOM, "device allocation failed (wall buffers)");
     }
-    std::vector<double> soa(n * 3, 0.0);
-    for (int k = 0; k < d; ++k)
-      for (size_t i = 0; i < n; ++i) soa[k * n + i] = pos[i * d + k];
-    CK(cudaMemcpyAsync(W.io, soa.data(), n * 3 * 8, cudaMemcpyHostToDevice, c->stream));
+    // host AoS -> wall_xyz (scratch here) -> SoA [x | y | z] staging
+    CK(cudaMemcpyAsync(c->B.wall_xyz, pos, n * d * 8, cudaMemcpyHostToDevice, c->stream));
+    double* soa[3] = {W.io, W.io + n, W.io + 2 * n};
+    if (d == 2) CK(cudaMemsetAsync(W.io + 2 * n, 0, n * 8, c->stream));
+    launch_deinterleave(c->B.wall_xyz, (int)n, d, soa, c->stream);
     StageArgs a = args(c);
     a.B = W;
     if (c->precision == SPH_FP64)
@@ -652,6 +649,63 @@ int sph_debug_neighbour_stats(sph_ctx* c, uint32_t* cnt_fluid, uint32_t* cnt_wal
   rc = leave(c);
   if (rc) return rc;
   return sync_status(c);
+}
+
+int sph_profile_stages(sph_ctx* c, int n, double* ms, long* rebuilds) {
+  if (!c || !ms || n < 0) return SPH_E_INVALID;
+  if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
+  int rc = enter(c);
+  if (rc) return rc;
+  DevScalars before, after;
+  rc = read_scalars(c, &before);
+  if (rc) return rc;
+  cudaEvent_t ev[kStages + 1];
+  for (int k = 0; k <= kStages; ++k) CK(cudaEventCreate(&ev[k]));
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    if (c->precision == SPH_FP64)
+      enqueue_step_fp64(args(c), c->stream, ev);
+    else
+      enqueue_step_mixed(args(c), c->stream, ev);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[kStages]);
+    for (int k = 0; k < kStages && e == cudaSuccess; ++k) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      ms[k] += t;
+    }
+  }
+  for (int k = 0; k <= kStages; ++k) cudaEventDestroy(ev[k]);
+  if (e != cudaSuccess) return cuda_err(c, e, "sph_profile_stages");
+  rc = read_scalars(c, &after);
+  if (rc) return rc;
+  if (rebuilds) *rebuilds = (long)(after.n_adv - before.n_adv);
+  rc = leave(c);
+  if (rc) return rc;
+  return flags_status(c, after);
+}
+
+long sph_kernels_per_step(const sph_ctx* cc) {
+  if (!cc) return -1;
+  sph_ctx* c = const_cast<sph_ctx*>(cc);
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return -1;
+  enqueue_step(c, c->stream);
+  if (cudaStreamEndCapture(c->stream, &g) != cudaSuccess || !g) return -1;
+  size_t count = 0;
+  long kernels = -1;
+  if (cudaGraphGetNodes(g, nullptr, &count) == cudaSuccess) {
+    std::vector<cudaGraphNode_t> nodes(count);
+    if (cudaGraphGetNodes(g, nodes.data(), &count) == cudaSuccess) {
+      kernels = 0;
+      for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+      }
+    }
+  }
+  cudaGraphDestroy(g);
+  return kernels;
 }
 
 int sph_set_option(sph_ctx* c, int option, long value) {

@@ -3,11 +3,11 @@
 
 namespace sphgb {
 
-void enqueue_step_fp64(const StageArgs& a, cudaStream_t s) {
+void enqueue_step_fp64(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev) {
   if (a.P.dim == 2)
-    stages::enqueue_step_t<2, double>(a, s);
+    stages::enqueue_step_t<2, double>(a, s, ev);
   else
-    stages::enqueue_step_t<3, double>(a, s);
+    stages::enqueue_step_t<3, double>(a, s, ev);
 }
 
 void enqueue_initial_sort_fp64(const StageArgs& a, cudaStream_t s) {

@@ -13,8 +13,9 @@
 //   records, two buffers (written by one stage, read by the next neighbour loop):
 //     3D  P = (x, y, z, p)   S = (vx, vy, vz, rho)      T4 / T4
 //     2D  P = (x, y, vx, vy) S = (p, rho)               T4 / T2
-//   with positions absolute in FP64 mode and cell-local offsets
-//   x - (lo + c 2h) of the binned cell c in mixed mode.
+//   with positions absolute in FP64 mode and cell-centre offsets
+//   x - (lo + (c + 1/2) s) of the binned cell c in mixed mode (s = 2h
+//   rounded to float).
 //   keys (sorted cell keys), perm, cell_begin[ncell + 1]   uint32
 //   wall: positions (T4 / T2, same convention), cell_begin, ids
 #pragma once
@@ -32,6 +33,21 @@ constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;  // keys per thread per tile
 constexpr int kSortTile = kSortThreads * kSortItems;
 constexpr int kOffsetsChunk = 2048;  // cells per block of the offsets kernel
+
+// stages of one acoustic step (same numbering as enum sph_stage)
+enum {
+  kStageControl = 0,
+  kStageKeys,
+  kStageSort,
+  kStageReorder,
+  kStageOffsets,
+  kStageDensitySum,
+  kStageViscous,
+  kStageHalf1,
+  kStagePressure,
+  kStageDensityRelax,
+  kStages
+};
 
 // error flag bits (sticky, device)
 constexpr int kFlagOutOfDomain = 1;
@@ -138,9 +154,15 @@ struct StageArgs {
   LaunchCfg L;
 };
 
-// Queue one acoustic step (device-decided rebuild included).
-void enqueue_step_fp64(const StageArgs& a, cudaStream_t s);
-void enqueue_step_mixed(const StageArgs& a, cudaStream_t s);
+// Queue one acoustic step (device-decided rebuild included).  When ev is
+// given (kStages + 1 events), ev[k] is recorded before stage k and
+// ev[kStages] after the last stage.
+void enqueue_step_fp64(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev = nullptr);
+void enqueue_step_mixed(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev = nullptr);
+// rho = rho0 where fill_rho, id = 0..n-1
+void launch_init_fluid(double* rho, int fill_rho, double rho0, uint32_t* id, int n, cudaStream_t s);
+// AoS (n x dim) -> SoA copy on the device
+void launch_deinterleave(const double* aos, int n, int dim, double* const soa[3], cudaStream_t s);
 // Initial binning / sort after set_particles (forces a rebuild of the cell
 // list and builds the records without changing the schedule).
 void enqueue_initial_sort_fp64(const StageArgs& a, cudaStream_t s);

@@ -4,11 +4,11 @@
 
 namespace sphgb {
 
-void enqueue_step_mixed(const StageArgs& a, cudaStream_t s) {
+void enqueue_step_mixed(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev) {
   if (a.P.dim == 2)
-    stages::enqueue_step_t<2, float>(a, s);
+    stages::enqueue_step_t<2, float>(a, s, ev);
   else
-    stages::enqueue_step_t<3, float>(a, s);
+    stages::enqueue_step_t<3, float>(a, s, ev);
 }
 
 void enqueue_initial_sort_mixed(const StageArgs& a, cudaStream_t s) {

@@ -424,7 +424,37 @@ __global__ void k_neighbour_stats(Params P, DevBuffers B, const double* __restri
   }
 }
 
+__global__ void k_deinterleave(const double* __restrict__ aos, int n, int dim, double* s0,
+                               double* s1, double* s2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    s0[i] = aos[(size_t)i * dim];
+    s1[i] = aos[(size_t)i * dim + 1];
+    if (dim == 3) s2[i] = aos[(size_t)i * dim + 2];
+  }
+}
+
+__global__ void k_init_fluid(double* rho, int fill_rho, double rho0, uint32_t* id, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (fill_rho) rho[i] = rho0;
+    id[i] = (uint32_t)i;
+  }
+}
+
 }  // namespace
+
+void launch_init_fluid(double* rho, int fill_rho, double rho0, uint32_t* id, int n, cudaStream_t s) {
+  int blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_init_fluid<<<blocks, 256, 0, s>>>(rho, fill_rho, rho0, id, n);
+}
+
+void launch_deinterleave(const double* aos, int n, int dim, double* const soa[3], cudaStream_t s) {
+  int blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_deinterleave<<<blocks, 256, 0, s>>>(aos, n, dim, soa[0], soa[1], soa[2]);
+}
 
 int bits_for(uint32_t ncell) {
   int b = 1;

@@ -2,9 +2,10 @@
 // dimension D and the pair-arithmetic type T.
 //   T = double: FP64 path; records hold absolute positions.
 //   T = float : mixed path; records hold float cell-local offsets
-//               o = x - (lo + c 2h) of the binned cell c, so a pair distance is
-//               o_i - o_j - d 2h with d the cell offset (-1, 0, 1 per axis);
-//               state (x, v, rho) stays double.
+//               o = x - (lo + (c + 1/2) s) of the binned cell c, with s the cell
+//               edge 2h rounded to float, so a pair distance is o_i - o_j - d s
+//               with d the cell offset (-1, 0, 1 per axis) and d s exact in
+//               float; state (x, v, rho) stays double.
 //
 // Direct search (paper, section "Cell linked-list, direct search and
 // sorting"): each neighbour loop recomputes kernel values for every particle
@@ -212,11 +213,15 @@ struct Local<double> {
 template <>
 struct Local<float> {
   static constexpr bool kLocal = true;
+  // Offsets from the cell centre on a pitch that is exact in float, so that
+  // o_i - o_j - d * pitch reproduces x_i - x_j without a systematic error from
+  // rounding the pitch (the shift d * pitch is then exact in float).
   __device__ static void enc(const Params& P, Cell c, double x, double y, double z, float& ox,
                              float& oy, float& oz) {
-    ox = (float)(x - (P.lo[0] + (double)c.x * P.cs));
-    oy = (float)(y - (P.lo[1] + (double)c.y * P.cs));
-    oz = (float)(z - (P.lo[2] + (double)c.z * P.cs));
+    const double pf = (double)(float)P.cs;
+    ox = (float)(x - (P.lo[0] + ((double)c.x + 0.5) * pf));
+    oy = (float)(y - (P.lo[1] + ((double)c.y + 0.5) * pf));
+    oz = (float)(z - (P.lo[2] + ((double)c.z + 0.5) * pf));
   }
 };
 
@@ -673,40 +678,56 @@ inline int grid_for(int n, int block, int cap) {
   return b < 1 ? 1 : b;
 }
 
+// Records ev[k] before stage k (and ev[kStages] after the last) when given.
+inline void mark(cudaEvent_t* ev, int k, cudaStream_t s) {
+  if (ev) cudaEventRecord(ev[k], s);
+}
+
 template <int D, class T>
-void enqueue_rebuild(const StageArgs& a, cudaStream_t s, int gated) {
+void enqueue_rebuild(const StageArgs& a, cudaStream_t s, int gated, cudaEvent_t* ev) {
   const Params& P = a.P;
   const LaunchCfg& L = a.L;
   DevBuffers B = a.B;
   uint32_t* keys[2] = {B.keys[0], B.keys[1]};
   uint32_t* vals[2] = {B.vals[0], B.vals[1]};
+  mark(ev, kStageKeys, s);
   launch_cell_keys_par(P, L, B.x, keys[0], vals[0], P.n, B.sc, gated, B.digit_total, s);
+  mark(ev, kStageSort, s);
   B.sorted_buf = launch_radix_sort(L, keys, vals, P.n, B.tile_hist, B.digit_total, B.sc, gated, s);
+  mark(ev, kStageReorder, s);
   k_reorder<D, T><<<grid_for(P.n, L.block_stream, L.blocks_stream), L.block_stream, 0, s>>>(
       P, B, gated);
+  mark(ev, kStageOffsets, s);
   launch_cell_offsets(B.keys[B.sorted_buf], P.n, P.ncell, B.cell_begin, B.sc, gated, 1, s);
 }
 
 template <int D, class T>
-void enqueue_step_t(const StageArgs& a, cudaStream_t s) {
+void enqueue_step_t(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev) {
   const Params& P = a.P;
   const LaunchCfg& L = a.L;
   const DevBuffers& B = a.B;
   const KC<T> k = make_kc<T>(P);
+  mark(ev, kStageControl, s);
   launch_control(P, B.sc, s);
-  enqueue_rebuild<D, T>(a, s, 1);
+  enqueue_rebuild<D, T>(a, s, 1, ev);
   const int gl = grid_for(P.n, L.block_loop, L.blocks_loop);
   const int gs = grid_for(P.n, L.block_stream, L.blocks_stream);
+  mark(ev, kStageDensitySum, s);
   k_density_summation<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, 1);
+  mark(ev, kStageViscous, s);
   k_viscous<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, 1);
+  mark(ev, kStageHalf1, s);
   k_half1<D, T><<<gs, L.block_stream, 0, s>>>(P, B);
+  mark(ev, kStagePressure, s);
   k_pressure<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k);
+  mark(ev, kStageDensityRelax, s);
   k_density_relax<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k);
+  mark(ev, kStages, s);
 }
 
 template <int D, class T>
 void enqueue_initial_sort_t(const StageArgs& a, cudaStream_t s) {
-  enqueue_rebuild<D, T>(a, s, 0);
+  enqueue_rebuild<D, T>(a, s, 0, nullptr);
 }
 
 template <int D, class T>

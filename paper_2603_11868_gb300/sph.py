@@ -40,7 +40,9 @@ STATUS_NAMES = {0: "SPH_OK", 1: "SPH_E_INVALID", 2: "SPH_E_OOM", 3: "SPH_E_CUDA"
 EXPORTS = ("sph_create", "sph_set_particles", "sph_step", "sph_get_fields", "sph_get_scalars",
            "sph_count", "sph_cell_count", "sph_debug_neighbour_state",
            "sph_debug_neighbour_stats", "sph_set_option", "sph_synchronize", "sph_last_error",
-           "sph_destroy")
+           "sph_destroy", "sph_profile_stages", "sph_kernels_per_step")
+STAGE_NAMES = ("control", "keys", "sort", "reorder", "offsets", "density_sum", "viscous",
+               "half1", "pressure", "density_relax")
 
 
 class sph_domain(C.Structure):
@@ -109,6 +111,10 @@ def load(path: str | None = None):
         L.sph_last_error.argtypes = [vp]
         L.sph_destroy.restype = None
         L.sph_destroy.argtypes = [vp]
+        L.sph_profile_stages.restype = i
+        L.sph_profile_stages.argtypes = [vp, i, vp, vp]
+        L.sph_kernels_per_step.restype = C.c_long
+        L.sph_kernels_per_step.argtypes = [vp]
         _lib = L
         return L
 
@@ -213,6 +219,17 @@ def sph_destroy(ctx):
     load().sph_destroy(ctx)
 
 
+def sph_profile_stages(ctx, n):
+    ms = np.zeros(len(STAGE_NAMES), np.float64)
+    reb = C.c_long()
+    _check(ctx, load().sph_profile_stages(ctx, int(n), _ptr(ms), C.byref(reb)))
+    return dict(zip(STAGE_NAMES, ms)), reb.value
+
+
+def sph_kernels_per_step(ctx):
+    return load().sph_kernels_per_step(ctx)
+
+
 # --- PyTorch plumbing ------------------------------------------------------
 class TorchAllocator:
     """Allocator callbacks backed by torch's CUDA caching allocator."""
@@ -298,6 +315,12 @@ class Solver:
 
     def neighbour_stats(self):
         return sph_debug_neighbour_stats(self.ctx, self.n)
+
+    def profile_stages(self, n: int):
+        return sph_profile_stages(self.ctx, n)
+
+    def kernels_per_step(self):
+        return sph_kernels_per_step(self.ctx)
 
     def synchronize(self, timeout_s=0.0):
         sph_synchronize(self.ctx, timeout_s)

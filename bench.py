@@ -135,8 +135,10 @@ def dist_env():
     return ws, rank, local
 
 
-def make_workload(name: str):
+def make_workload(name: str, dp: float | None = None):
     from paper_2603_11868_gb300 import cases
+    if dp is not None:
+        return cases.dam_break_3d(dp=dp, seed=2), f"3D dam break, dp={dp}"
     if name == "dam_break_3d_5m":
         return cases.dam_break_3d(dp=0.0025, seed=2), "3D dam break, dp=0.0025"
     if name == "dam_break_3d_80k":
@@ -232,7 +234,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     sph.load()
-    case, wname = make_workload(args.workload)
+    case, wname = make_workload(args.workload, args.dp)
     solver = sph.Solver(case, precision=args.precision)
     n, nw = case.n, case.nw
     mean_nb = None
@@ -372,6 +374,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dam_break_3d_5m",
                     choices=["dam_break_3d_5m", "dam_break_3d_80k", "dam_break_2d"])
+    ap.add_argument("--dp", type=float, default=None,
+                    help="3D dam break at this spacing instead of the named workload")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--substeps", type=int, default=SUBSTEPS)
     ap.add_argument("--fp64-steps", type=int, default=2)

@@ -86,6 +86,8 @@ def lib():
             L.osph_front_ke.restype = None; L.osph_front_ke.argtypes = [vp, vp, vp]
             L.osph_sample_sigma.restype = None
             L.osph_sample_sigma.argtypes = [vp, l, vp, vp]
+            L.osph_sample_first_step_acc.restype = None
+            L.osph_sample_first_step_acc.argtypes = [vp, l, vp, vp]
             _lib = L
     return _lib
 
@@ -251,6 +253,12 @@ class Oracle:
         f, k = C.c_double(), C.c_double()
         lib().osph_front_ke(self._s, C.byref(f), C.byref(k))
         return f.value, k.value
+
+    def sample_first_step_acc(self, user_ids):
+        ids = np.ascontiguousarray(user_ids, dtype=np.uint32)
+        out = np.zeros((len(ids), self.dim), np.float64)
+        lib().osph_sample_first_step_acc(self._s, len(ids), _ptr(ids), _ptr(out))
+        return out
 
     def sample_sigma(self, user_ids):
         ids = np.ascontiguousarray(user_ids, dtype=np.uint32)

@@ -374,29 +374,35 @@ static double dist2(const double a[3], const double b[3]) {
  *   sigma_i = sum_{j in fluid and wall, r_ij < 2h} W(r_ij)   (self included),
  *   rho_i   = rho0 * max(sigma_i / sigma0, 1)    (reading: free-surface clamp),
  *   p_i     = c0^2 (rho_i - rho0).                                         */
-void osph_density_summation(osim* s) {
+static double sigma_of(const osim* s, long i) {
   const double r2max = 4.0 * s->h * s->h;
   long cells[27];
-  for (long i = 0; i < s->n; ++i) {
-    int nc = neighbour_cells(s, s->key[i], cells);
-    double sig = 0.0;
-    for (int q = 0; q < nc; ++q) {
-      for (long j = s->cb[cells[q]]; j < s->cb[cells[q] + 1]; ++j) {
-        double r2 = dist2(s->x[i], s->x[j]);
-        if (r2 >= r2max) continue;
-        sig += osph_W(s->dim, s->h, sqrt(r2));
-      }
-      for (long w = s->cbw[cells[q]]; w < s->cbw[cells[q] + 1]; ++w) {
-        double r2 = dist2(s->x[i], s->xw[w]);
-        if (r2 >= r2max) continue;
-        sig += osph_W(s->dim, s->h, sqrt(r2));
-      }
+  int nc = neighbour_cells(s, s->key[i], cells);
+  double sig = 0.0;
+  for (int q = 0; q < nc; ++q) {
+    for (long j = s->cb[cells[q]]; j < s->cb[cells[q] + 1]; ++j) {
+      double r2 = dist2(s->x[i], s->x[j]);
+      if (r2 >= r2max) continue;
+      sig += osph_W(s->dim, s->h, sqrt(r2));
     }
-    s->sigma[i] = sig;
+    for (long w = s->cbw[cells[q]]; w < s->cbw[cells[q] + 1]; ++w) {
+      double r2 = dist2(s->x[i], s->xw[w]);
+      if (r2 >= r2max) continue;
+      sig += osph_W(s->dim, s->h, sqrt(r2));
+    }
   }
+  return sig;
+}
+
+static double density_of_sigma(const osim* s, double sig) {
+  double ratio = sig / s->sigma0;
+  return s->rho0 * (ratio > 1.0 ? ratio : 1.0);
+}
+
+void osph_density_summation(osim* s) {
+  for (long i = 0; i < s->n; ++i) s->sigma[i] = sigma_of(s, i);
   for (long i = 0; i < s->n; ++i) {
-    double ratio = s->sigma[i] / s->sigma0;
-    s->rho[i] = s->rho0 * (ratio > 1.0 ? ratio : 1.0);
+    s->rho[i] = density_of_sigma(s, s->sigma[i]);
     s->p[i] = s->c0 * s->c0 * (s->rho[i] - s->rho0);
   }
 }
@@ -465,48 +471,64 @@ void osph_half1(osim* s, double dt) {
  *   p_w = p_i + rho_i (x_w - x_i).g,  rho_w = rho0 + p_w / c0^2,
  *   v_R = 2 v_w - v_i = -v_i,  V_w = m / rho_w.
  * Then v_i += dt (a_i + a_prior_i). */
-void osph_pressure_relaxation(osim* s, double dt) {
+/* Pressure acceleration of storage slot i with the given density and
+ * pressure arrays (indexed by storage slot). */
+static void pressure_acc_of(const osim* s, long i, const double* rho, const double* p,
+                            double out[3]) {
   const double r2max = 4.0 * s->h * s->h;
   const double c0 = s->c0;
   long cells[27];
-  for (long i = 0; i < s->n; ++i) {
-    int nc = neighbour_cells(s, s->key[i], cells);
-    double a[3] = {0.0, 0.0, 0.0};
-    for (int q = 0; q < nc; ++q) {
-      for (long j = s->cb[cells[q]]; j < s->cb[cells[q] + 1]; ++j) {
-        if (j == i) continue;
-        double r2 = dist2(s->x[i], s->x[j]);
-        if (r2 >= r2max) continue;
-        double r = sqrt(r2);
-        double e[3];
-        for (int k = 0; k < 3; ++k) e[k] = (s->x[i][k] - s->x[j][k]) / r;
-        double UL = -(s->v[i][0] * e[0] + s->v[i][1] * e[1] + s->v[i][2] * e[2]);
-        double UR = -(s->v[j][0] * e[0] + s->v[j][1] * e[1] + s->v[j][2] * e[2]);
-        double Ps, Us;
-        osph_riemann(s->p[i], s->p[j], s->rho[i], s->rho[j], UL, UR, c0, &Ps, &Us);
-        double f = Ps * (s->m / s->rho[j]) * osph_dW(s->dim, s->h, r);
-        for (int k = 0; k < 3; ++k) a[k] += f * e[k];
-      }
-      for (long w = s->cbw[cells[q]]; w < s->cbw[cells[q] + 1]; ++w) {
-        double r2 = dist2(s->x[i], s->xw[w]);
-        if (r2 >= r2max) continue;
-        double r = sqrt(r2);
-        double e[3];
-        for (int k = 0; k < 3; ++k) e[k] = (s->x[i][k] - s->xw[w][k]) / r;
-        double gdot = 0.0;
-        for (int k = 0; k < 3; ++k) gdot += (s->xw[w][k] - s->x[i][k]) * s->g[k];
-        double pw = s->p[i] + s->rho[i] * gdot;
-        double rhow = s->rho0 + pw / (c0 * c0);
-        double UL = -(s->v[i][0] * e[0] + s->v[i][1] * e[1] + s->v[i][2] * e[2]);
-        double UR = -UL;
-        double Ps, Us;
-        osph_riemann(s->p[i], pw, s->rho[i], rhow, UL, UR, c0, &Ps, &Us);
-        double f = Ps * (s->m / rhow) * osph_dW(s->dim, s->h, r);
-        for (int k = 0; k < 3; ++k) a[k] += f * e[k];
-      }
+  int nc = neighbour_cells(s, s->key[i], cells);
+  double a[3] = {0.0, 0.0, 0.0};
+  for (int q = 0; q < nc; ++q) {
+    for (long j = s->cb[cells[q]]; j < s->cb[cells[q] + 1]; ++j) {
+      if (j == i) continue;
+      double r2 = dist2(s->x[i], s->x[j]);
+      if (r2 >= r2max) continue;
+      double r = sqrt(r2);
+      double e[3];
+      for (int k = 0; k < 3; ++k) e[k] = (s->x[i][k] - s->x[j][k]) / r;
+      double UL = -(s->v[i][0] * e[0] + s->v[i][1] * e[1] + s->v[i][2] * e[2]);
+      double UR = -(s->v[j][0] * e[0] + s->v[j][1] * e[1] + s->v[j][2] * e[2]);
+      double Ps, Us;
+      osph_riemann(p[i], p[j], rho[i], rho[j], UL, UR, c0, &Ps, &Us);
+      double f = Ps * (s->m / rho[j]) * osph_dW(s->dim, s->h, r);
+      for (int k = 0; k < 3; ++k) a[k] += f * e[k];
     }
-    for (int k = 0; k < 3; ++k) s->acc[i][k] = -2.0 / s->rho[i] * a[k];
+    for (long w = s->cbw[cells[q]]; w < s->cbw[cells[q] + 1]; ++w) {
+      double r2 = dist2(s->x[i], s->xw[w]);
+      if (r2 >= r2max) continue;
+      double r = sqrt(r2);
+      double e[3];
+      for (int k = 0; k < 3; ++k) e[k] = (s->x[i][k] - s->xw[w][k]) / r;
+      double gdot = 0.0;
+      for (int k = 0; k < 3; ++k) gdot += (s->xw[w][k] - s->x[i][k]) * s->g[k];
+      double pw = p[i] + rho[i] * gdot;
+      double rhow = s->rho0 + pw / (c0 * c0);
+      double UL = -(s->v[i][0] * e[0] + s->v[i][1] * e[1] + s->v[i][2] * e[2]);
+      double UR = -UL;
+      double Ps, Us;
+      osph_riemann(p[i], pw, rho[i], rhow, UL, UR, c0, &Ps, &Us);
+      double f = Ps * (s->m / rhow) * osph_dW(s->dim, s->h, r);
+      for (int k = 0; k < 3; ++k) a[k] += f * e[k];
+    }
   }
+  for (int k = 0; k < 3; ++k) out[k] = -2.0 / rho[i] * a[k];
+}
+
+/* Riemann-based pressure relaxation [Z17], then the velocity kick.
+ * For the pair (i, j): e_ij = (x_i - x_j) / r_ij, U_L = -v_i.e_ij,
+ * U_R = -v_j.e_ij, and
+ *   a_i = -(2 / rho_i) sum_j P*_ij V_j W'(r_ij) e_ij,   V_j = m / rho_j.
+ * Wall particle w (static, v_w = 0) supplies a mirrored right state
+ * (reading: pressure extrapolated along gravity, density from the inverse
+ * equation of state and volume from that density, as in Adami, Hu & Adams,
+ * J. Comput. Phys. 231 (2012)):
+ *   p_w = p_i + rho_i (x_w - x_i).g,  rho_w = rho0 + p_w / c0^2,
+ *   v_R = 2 v_w - v_i = -v_i,  V_w = m / rho_w.
+ * Then v_i += dt (a_i + a_prior_i). */
+void osph_pressure_relaxation(osim* s, double dt) {
+  for (long i = 0; i < s->n; ++i) pressure_acc_of(s, i, s->rho, s->p, s->acc[i]);
   for (long i = 0; i < s->n; ++i)
     for (int k = 0; k < s->dim; ++k)
       s->v[i][k] += dt * (s->acc[i][k] + s->aprior[i][k]);
@@ -715,30 +737,53 @@ void osph_front_ke(const osim* s, double* front, double* ke) {
   *ke = e;
 }
 
-void osph_sample_sigma(const osim* s, long m, const uint32_t* user_ids,
-                       double* sigma) {
-  const double r2max = 4.0 * s->h * s->h;
-  long cells[27];
-  /* user id -> storage slot */
+static long* user_to_slot(const osim* s) {
   long* slot = (long*)xcalloc((size_t)s->n, sizeof(long));
   for (long k = 0; k < s->n; ++k) slot[s->id[k]] = k;
-  for (long q0 = 0; q0 < m; ++q0) {
-    long i = slot[user_ids[q0]];
+  return slot;
+}
+
+void osph_sample_sigma(const osim* s, long m, const uint32_t* user_ids,
+                       double* sigma) {
+  long* slot = user_to_slot(s);
+  for (long q = 0; q < m; ++q) sigma[q] = sigma_of(s, slot[user_ids[q]]);
+  free(slot);
+}
+
+/* First acoustic step from rest (v = 0, carried density rate 0, state as set):
+ * the step's density summation is evaluated for the sampled particles and
+ * all their neighbours, the first half-step leaves positions and densities
+ * unchanged and sets p = c0^2 (rho - rho0), and the pressure acceleration of
+ * each sampled particle follows (equal to osph_step(1) followed by OSPH_ACC,
+ * at the cost of the samples' neighbourhoods only). */
+void osph_sample_first_step_acc(const osim* s, long m, const uint32_t* user_ids,
+                                double* acc) {
+  const double r2max = 4.0 * s->h * s->h;
+  long cells[27];
+  long* slot = user_to_slot(s);
+  char* need = (char*)xcalloc((size_t)s->n, 1);
+  double* rho = (double*)xcalloc((size_t)s->n, sizeof(double));
+  double* p = (double*)xcalloc((size_t)s->n, sizeof(double));
+  for (long q = 0; q < m; ++q) {
+    long i = slot[user_ids[q]];
+    need[i] = 1;
     int nc = neighbour_cells(s, s->key[i], cells);
-    double sig = 0.0;
-    for (int q = 0; q < nc; ++q) {
-      for (long j = s->cb[cells[q]]; j < s->cb[cells[q] + 1]; ++j) {
-        double r2 = dist2(s->x[i], s->x[j]);
-        if (r2 >= r2max) continue;
-        sig += osph_W(s->dim, s->h, sqrt(r2));
-      }
-      for (long w = s->cbw[cells[q]]; w < s->cbw[cells[q] + 1]; ++w) {
-        double r2 = dist2(s->x[i], s->xw[w]);
-        if (r2 >= r2max) continue;
-        sig += osph_W(s->dim, s->h, sqrt(r2));
-      }
-    }
-    sigma[q0] = sig;
+    for (int c = 0; c < nc; ++c)
+      for (long j = s->cb[cells[c]]; j < s->cb[cells[c] + 1]; ++j)
+        if (dist2(s->x[i], s->x[j]) < r2max) need[j] = 1;
   }
+  for (long k = 0; k < s->n; ++k)
+    if (need[k]) {
+      rho[k] = density_of_sigma(s, sigma_of(s, k));
+      p[k] = s->c0 * s->c0 * (rho[k] - s->rho0);
+    }
+  for (long q = 0; q < m; ++q) {
+    double a[3];
+    pressure_acc_of(s, slot[user_ids[q]], rho, p, a);
+    for (int k = 0; k < s->dim; ++k) acc[q * s->dim + k] = a[k];
+  }
+  free(p);
+  free(rho);
+  free(need);
   free(slot);
 }

@@ -114,6 +114,11 @@ void osph_front_ke(const osim* s, double* front, double* ke);
  * the kernel sum (density summation) with the current cell list. */
 void osph_sample_sigma(const osim* s, long m, const uint32_t* user_ids,
                        double* sigma);
+/* For a state as set (at rest, no carried density rate, binned): the pressure
+ * acceleration the first acoustic step gives the m sampled fluid particles
+ * (acc: m * dim). */
+void osph_sample_first_step_acc(const osim* s, long m, const uint32_t* user_ids,
+                                double* acc);
 
 #ifdef __cplusplus
 }

@@ -146,15 +146,22 @@ def test_fp64_many_steps(sph, O):
     assert abs(sc["t"] - osc["t"]) <= 1e-12 * osc["t"]
 
 
-@pytest.mark.parametrize("name", ["dam_break_2d", "dam_break_3d_small"])
+def _acc_err(got, want, g):
+    return np.abs(got - want).max() / max(np.abs(want).max(), g)
+
+
+@pytest.mark.parametrize("name", ["dam_break_2d", "dam_break_3d_small", "dam_break_3d"])
 def test_mixed_one_step(sph, O, name):
-    case = SORT_CASES[name]()
+    case = SORT_CASES[name]() if name in SORT_CASES else cases.dam_break_3d()
     got, want, sc, osc = _run_pair(sph, O, case, "mixed", 1)
     g = np.abs(case.gravity).max()
+    errs = {k: _acc_err(got[k], want[k], g) for k in ("acc", "aprior")}
+    errs.update({k: rel(got[k], want[k]) for k in ("vel", "rho", "sigma", "drho", "p")})
+    errs["pos/dp"] = np.abs(got["pos"] - want["pos"]).max() / case.dp
+    print(f"\nmixed one-step errors {name}: " +
+          ", ".join(f"{k}={v:.2e}" for k, v in errs.items()))
     for k in ("acc", "aprior"):
-        den = max(np.abs(want[k]).max(), g)
-        err = np.abs(got[k] - want[k]).max() / den
-        assert err <= 1e-5, (k, err)
+        assert errs[k] <= 1e-5, (k, errs[k])
     assert np.abs(got["pos"] - want["pos"]).max() <= 1e-6 * case.dp
     assert rel(got["vel"], want["vel"]) <= 1e-5
     assert rel(got["rho"], want["rho"]) <= 1e-6
@@ -314,6 +321,12 @@ def test_full_size_sampled_density(sph, O):
     ids = rng.choice(case.n, 2000, replace=False).astype(np.uint32)
     want = o.sample_sigma(ids)
     assert rel(sig[ids], want) <= 1e-6
+    acc_ids = ids[:400]
+    a_ref = o.sample_first_step_acc(acc_ids)
+    a_got = s.field("acc")[acc_ids]
+    err = _acc_err(a_got, a_ref, 9.81)
+    print(f"\nfull-size mixed first-step acceleration error (400 samples): {err:.2e}")
+    assert err <= 1e-5
     del o
     st = s.neighbour_state()
     assert np.array_equal(np.sort(st["ids"]), np.arange(case.n, dtype=np.uint32))

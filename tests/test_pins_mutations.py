@@ -14,17 +14,17 @@ SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
 PIN_FILES = ["tests/test_oracle_kernel.py", "tests/test_oracle_neighbours.py",
              "tests/test_oracle_physics.py"]
 
-_WALL_P = ("double UR = -UL;\n        double Ps, Us;\n        osph_riemann(s->p[i], pw, s->rho[i], "
-           "rhow, UL, UR, c0, &Ps, &Us);\n        double f")
+_WALL_P = ("double UR = -UL;\n      double Ps, Us;\n      osph_riemann(p[i], pw, rho[i], "
+           "rhow, UL, UR, c0, &Ps, &Us);\n      double f")
 MUTATIONS = {
     "riemann_ustar_sign": ("*Ustar = 0.5 * (UL + UR) + (pL - pR)",
                            "*Ustar = 0.5 * (UL + UR) + (pR - pL)"),
     "riemann_limiter_direction": ("double jump = UL - UR;", "double jump = UR - UL;"),
     "riemann_rho_bar": ("double rho_bar = 0.5 * (rhoL + rhoR);", "double rho_bar = rhoL;"),
-    "pressure_volume_index": ("double f = Ps * (s->m / s->rho[j])",
-                              "double f = Ps * (s->m / s->rho[i])"),
-    "pressure_direction": ("for (int k = 0; k < 3; ++k) a[k] += f * e[k];",
-                           "for (int k = 0; k < 3; ++k) a[k] -= f * e[k];"),
+    "pressure_volume_index": ("double f = Ps * (s->m / rho[j])",
+                              "double f = Ps * (s->m / rho[i])"),
+    "pressure_direction": ("for (int k = 0; k < 3; ++k) out[k] = -2.0 / rho[i] * a[k];",
+                           "for (int k = 0; k < 3; ++k) out[k] = 2.0 / rho[i] * a[k];"),
     "wall_gravity_sign": ("gdot += (s->xw[w][k] - s->x[i][k]) * s->g[k];",
                           "gdot += (s->x[i][k] - s->xw[w][k]) * s->g[k];"),
     "wall_mirror_velocity": (_WALL_P, _WALL_P.replace("double UR = -UL;", "double UR = UL;")),
@@ -39,11 +39,11 @@ MUTATIONS = {
     "kick_prior_sign": ("s->v[i][k] += dt * (s->acc[i][k] + s->aprior[i][k]);",
                         "s->v[i][k] += dt * (s->acc[i][k] - s->aprior[i][k]);"),
     "summation_without_self": (
-        "        double r2 = dist2(s->x[i], s->x[j]);\n        if (r2 >= r2max) continue;\n        sig +=",
-        "        if (j == i) continue;\n        double r2 = dist2(s->x[i], s->x[j]);\n"
-        "        if (r2 >= r2max) continue;\n        sig +="),
-    "summation_no_clamp": ("s->rho[i] = s->rho0 * (ratio > 1.0 ? ratio : 1.0);",
-                           "s->rho[i] = s->rho0 * ratio;"),
+        "      double r2 = dist2(s->x[i], s->x[j]);\n      if (r2 >= r2max) continue;\n      sig +=",
+        "      if (j == i) continue;\n      double r2 = dist2(s->x[i], s->x[j]);\n"
+        "      if (r2 >= r2max) continue;\n      sig +="),
+    "summation_no_clamp": ("return s->rho0 * (ratio > 1.0 ? ratio : 1.0);",
+                           "return s->rho0 * ratio;"),
     "kernel_exponent": ("return osph_alpha(dim, h) * t * t * t * t * (2.0 * q + 1.0);",
                         "return osph_alpha(dim, h) * t * t * t * (2.0 * q + 1.0);"),
     "key_axis_swap": ("return (uint32_t)((c[2] * s->nc[1] + c[1]) * s->nc[0] + c[0]);",

@@ -248,6 +248,8 @@ int alloc_fluid(sph_ctx* c, size_t n) {
     B.vals[p] = (uint32_t*)A(nn * 4);
     ok &= B.recP[p] && B.recS[p] && B.keys[p] && B.vals[p];
   }
+  B.recI = c->precision == SPH_MIXED ? A(nn * (d == 3 ? 16 : 8)) : nullptr;
+  ok &= c->precision != SPH_MIXED || B.recI;
   const size_t tiles = (nn + kSortTile - 1) / kSortTile;
   B.tile_hist = (uint32_t*)A(tiles * ((size_t)1 << kMaxRadixBits) * 4);
   B.io = (double*)A(nn * 3 * 8);
@@ -426,6 +428,7 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
       c->B.wallP = nullptr;
       c->B.wall_id = nullptr;
       c->B.wall_xyz = nullptr;
+      c->B.wallI = nullptr;
       CK(cudaMemsetAsync(c->B.wall_cb, 0, ((size_t)c->P.ncell + 1) * 4, c->stream));
       CK(cudaStreamSynchronize(c->stream));
       return leave(c);
@@ -435,6 +438,7 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
     c->B.wallP = A(n * (d == 3 ? 4 : 2) * ts);
     c->B.wall_id = (uint32_t*)A(n * 4);
     c->B.wall_xyz = (double*)A(n * 3 * 8);
+    c->B.wallI = c->precision == SPH_MIXED ? A(n * (d == 3 ? 16 : 8)) : nullptr;
     std::vector<Block> tmp;
     DevBuffers W = c->B;
     W.io = (double*)dev_alloc(c, n * 3 * 8, tmp);
@@ -445,6 +449,7 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
     const size_t tiles = (n + kSortTile - 1) / kSortTile;
     W.tile_hist = (uint32_t*)dev_alloc(c, tiles * ((size_t)1 << kMaxRadixBits) * 4, tmp);
     bool ok = c->B.wallP && c->B.wall_id && c->B.wall_xyz && W.io && W.keys[0] && W.keys[1] &&
+              (c->precision != SPH_MIXED || c->B.wallI) &&
               W.vals[0] && W.vals[1] && W.tile_hist;
     if (!ok) {
       dev_free_list(c, tmp);

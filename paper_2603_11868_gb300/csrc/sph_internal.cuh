@@ -16,6 +16,8 @@
 //   with positions absolute in FP64 mode and cell-centre offsets
 //   x - (lo + (c + 1/2) s) of the binned cell c in mixed mode (s = 2h
 //   rounded to float).
+//   mixed mode also keeps fixed-point offsets (2^28 units per cell edge) of the
+//   positions at the last rebuild, for the exact density summation (int4 / int2)
 //   keys (sorted cell keys), perm, cell_begin[ncell + 1]   uint32
 //   wall: positions (T4 / T2, same convention), cell_begin, ids
 #pragma once
@@ -118,6 +120,7 @@ struct DevBuffers {
   void* sigma;      // T, diagnostics
   void* recP[2];    // T4
   void* recS[2];    // T4 (3D) or T2 (2D)
+  void* recI;       // mixed mode: int4 (3D) / int2 (2D) fixed-point offsets at the rebuild
   uint32_t* keys[2];  // sort ping-pong; keys[sorted_buf] holds the sorted keys
   uint32_t* vals[2];
   int sorted_buf;
@@ -129,6 +132,7 @@ struct DevBuffers {
   uint32_t* wall_cb;
   uint32_t* wall_id;
   double* wall_xyz;  // sorted wall positions, double SoA (3 nw)
+  void* wallI;       // mixed mode: wall fixed-point offsets (int4 / int2)
   DevScalars* sc;
   double* io;  // staging, n * dim doubles (also wall staging)
   uint32_t* u32_io;

@@ -225,6 +225,104 @@ struct Local<float> {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Fixed-point cell-centre offsets (mixed mode, density summation).  A position
+// is stored as round((x - centre of its binned cell) * 2^28 / cell edge) in
+// int32, so pair differences o_i - o_j - d 2^28 are exact integers and
+// r^2 in cell units is the exact integer sum of their squares times 2^-56.
+// Offsets are clamped to +-2^29 (only a particle outside the domain, which is
+// flagged, can reach that), which keeps every difference within int32.
+constexpr int kFxShift = 28;
+constexpr long long kFxOne = 1ll << kFxShift;
+
+template <int D>
+struct FxRec;
+template <>
+struct FxRec<3> {
+  using V = int4;
+};
+template <>
+struct FxRec<2> {
+  using V = int2;
+};
+
+__device__ __forceinline__ int fx_of(double x, double centre, double scale) {
+  double t = rint((x - centre) * scale);
+  t = fmin(fmax(t, -536870912.0), 536870912.0);
+  return (int)t;
+}
+
+template <int D>
+__device__ __forceinline__ typename FxRec<D>::V fx_encode(const Params& P, Cell c, double x,
+                                                          double y, double z) {
+  const double scale = (double)kFxOne / P.cs;
+  typename FxRec<D>::V r;
+  r.x = fx_of(x, P.lo[0] + ((double)c.x + 0.5) * P.cs, scale);
+  r.y = fx_of(y, P.lo[1] + ((double)c.y + 0.5) * P.cs, scale);
+  if constexpr (D == 3) {
+    r.z = fx_of(z, P.lo[2] + ((double)c.z + 0.5) * P.cs, scale);
+    r.w = 0;
+  }
+  return r;
+}
+
+// Double-float arithmetic on FP32 (value = hi + lo), built from the error-free
+// transformations TwoSum (Knuth) and TwoProduct with a fused multiply-add
+// (Dekker / Ogita-Rump-Oishi); additions carry no multiplications, so no
+// contraction can change them.
+struct dfl {
+  float hi, lo;
+};
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = a + b;
+  float e = b - (s - a);
+  return {s, e};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  dfl s = two_sum(a.hi, b.hi);
+  s.lo += a.lo + b.lo;
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e += a.hi * b.lo + a.lo * b.hi;
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dfl df_sqr(dfl a) {
+  float p = a.hi * a.hi;
+  float e = fmaf(a.hi, a.hi, -p);
+  e += 2.0f * a.hi * a.lo;
+  return fast_two_sum(p, e);
+}
+
+// Wendland C2 shape (1 - q/2)^4 (2q + 1) in double-float from the exact
+// integer r^2 in fixed-point units (R2 = r^2 2^56 / cell^2; the cell edge is
+// 2h, so q = 2 sqrt(R2) 2^-28 = sqrt(R2) 2^-27).
+__device__ __forceinline__ dfl wendland_shape_fx(unsigned long long R2) {
+  const float hi = __ull2float_rn(R2);
+  const long long rem = (long long)(R2 - (unsigned long long)hi);
+  const float lo = (float)rem;
+  const float s = sqrtf(hi);
+  const float e = fmaf(s, s, -hi);  // exact residual of the rounded root
+  const float s_lo = s > 0.0f ? __fdividef(lo - e, 2.0f * s) : 0.0f;
+  const float qh = s * 0x1p-27f, ql = s_lo * 0x1p-27f;
+  dfl u = two_sum(1.0f, -0.5f * qh);
+  u.lo -= 0.5f * ql;
+  u = fast_two_sum(u.hi, u.lo);
+  const dfl u4 = df_sqr(df_sqr(u));
+  dfl v = two_sum(1.0f, 2.0f * qh);
+  v.lo += 2.0f * ql;
+  v = fast_two_sum(v.hi, v.lo);
+  return df_mul(u4, v);
+}
+
 // Pointers of one state copy, chosen with selects (runtime indexing into the
 // kernel-parameter arrays would force them into local memory).
 template <class T>
@@ -284,10 +382,13 @@ __global__ void k_reorder(Params P, DevBuffers B, int gated) {
     Dd.drho[k] = S.drho[j];
     Dd.id[k] = S.id[j];
     T ox, oy, oz;
-    Local<T>::enc(P, decode(keys[k], P), x, y, z, ox, oy, oz);
+    const Cell ck = decode(keys[k], P);
+    Local<T>::enc(P, ck, x, y, z, ox, oy, oz);
     T p = (T)(P.c0sq * (rho - P.rho0));
     recP[k] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p);
     recS[k] = R::makeS((T)vx, (T)vy, (T)vz, (T)rho, p);
+    if constexpr (Local<T>::kLocal)
+      ((typename FxRec<D>::V*)B.recI)[k] = fx_encode<D>(P, ck, x, y, z);
   }
 }
 
@@ -339,6 +440,69 @@ __global__ void __launch_bounds__(256) k_density_summation(Params P, DevBuffers 
     R::set_rho(s, (T)rho);
     recS[i] = s;
     if (P.diag) ((T*)B.sigma)[i] = sig;
+  }
+}
+
+// Density summation of the mixed path: exact integer pair distances from the
+// fixed-point offsets of the rebuild and the kernel in double-float, so the
+// density (and through c0^2 the pressure) keeps double-precision accuracy
+// while every operation runs on the FP32 / integer pipes.
+template <int D>
+__global__ void __launch_bounds__(256) k_density_summation_fx(Params P, DevBuffers B,
+                                                              int gated) {
+  using R = Rec<D, float>;
+  using FV = typename FxRec<D>::V;
+  DevScalars* sc = B.sc;
+  if (gated && !sc->new_adv) return;
+  double* rho_live = sc->par ? B.rho[1] : B.rho[0];
+  const FV* __restrict__ rec = (const FV*)B.recI;
+  const FV* __restrict__ wrec = (const FV*)B.wallI;
+  typename R::SV* recS = (typename R::SV*)B.recS[0];
+  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  const uint32_t* __restrict__ cb = B.cell_begin;
+  const uint32_t* __restrict__ wcb = B.wall_cb;
+  const unsigned long long cut2 = 1ull << (2 * kFxShift);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    const Cell ci = decode(keys[i], P);
+    const FV oi = rec[i];
+    dfl sig = {0.0f, 0.0f};
+    for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
+      const int bx = oi.x - dx * (int)kFxOne, by = oi.y - dy * (int)kFxOne;
+      int bz = 0;
+      if constexpr (D == 3) bz = oi.z - dz * (int)kFxOne;
+      const uint32_t e = cb[c + 1];
+      for (uint32_t j = cb[c]; j < e; ++j) {
+        const FV oj = rec[j];
+        const long long ex = bx - oj.x, ey = by - oj.y;
+        unsigned long long R2 = (unsigned long long)(ex * ex) + (unsigned long long)(ey * ey);
+        if constexpr (D == 3) {
+          const long long ez = bz - oj.z;
+          R2 += (unsigned long long)(ez * ez);
+        }
+        if (R2 < cut2) sig = df_add(sig, wendland_shape_fx(R2));
+      }
+      if (P.nw > 0) {
+        const uint32_t we = wcb[c + 1];
+        for (uint32_t w = wcb[c]; w < we; ++w) {
+          const FV ow = wrec[w];
+          const long long ex = bx - ow.x, ey = by - ow.y;
+          unsigned long long R2 = (unsigned long long)(ex * ex) + (unsigned long long)(ey * ey);
+          if constexpr (D == 3) {
+            const long long ez = bz - ow.z;
+            R2 += (unsigned long long)(ez * ez);
+          }
+          if (R2 < cut2) sig = df_add(sig, wendland_shape_fx(R2));
+        }
+      }
+    });
+    const double sigma = P.walpha * ((double)sig.hi + (double)sig.lo);
+    const double ratio = sigma / P.sigma0;
+    const double rho = P.rho0 * (ratio > 1.0 ? ratio : 1.0);
+    rho_live[i] = rho;
+    typename R::SV s = recS[i];
+    R::set_rho(s, (float)rho);
+    recS[i] = s;
+    if (P.diag) ((float*)B.sigma)[i] = (float)sigma;
   }
 }
 
@@ -666,8 +830,11 @@ __global__ void k_wall_gather(Params P, DevBuffers B, const double* __restrict__
     if (D == 3) wz[k] = z;
     B.wall_id[k] = j;
     T ox, oy, oz;
-    Local<T>::enc(P, decode(keys[k], P), x, y, z, ox, oy, oz);
+    const Cell ck = decode(keys[k], P);
+    Local<T>::enc(P, ck, x, y, z, ox, oy, oz);
     out[k] = WR::make(ox, oy, oz);
+    if constexpr (Local<T>::kLocal)
+      ((typename FxRec<D>::V*)B.wallI)[k] = fx_encode<D>(P, ck, x, y, z);
   }
 }
 
@@ -713,7 +880,10 @@ void enqueue_step_t(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev) {
   const int gl = grid_for(P.n, L.block_loop, L.blocks_loop);
   const int gs = grid_for(P.n, L.block_stream, L.blocks_stream);
   mark(ev, kStageDensitySum, s);
-  k_density_summation<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, 1);
+  if constexpr (Local<T>::kLocal)
+    k_density_summation_fx<D><<<gl, L.block_loop, 0, s>>>(P, B, 1);
+  else
+    k_density_summation<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, 1);
   mark(ev, kStageViscous, s);
   k_viscous<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, 1);
   mark(ev, kStageHalf1, s);

@@ -205,6 +205,44 @@ int sph_profile_stages(sph_ctx* ctx, int n, double* ms, long* rebuilds);
 /* Kernel launches one acoustic step queues (graph nodes of the step). */
 long sph_kernels_per_step(const sph_ctx* ctx);
 
+/* Largest n accepted by sph_cell_sort_noalloc. */
+#define SPH_NOALLOC_MAX_PARTICLES (1u << 20)
+
+/* Cell sort that allocates no memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory at the
+ * moment they need a sort -- code that works inside a fixed memory budget
+ * handed out in advance, code that must not stall the device (cudaMalloc and
+ * cudaFree synchronise it), or code with no allocator at hand.
+ *
+ * It computes what sph_set_particles computes for the fluid: the cell key of
+ * every particle on the grid of `domain` with cells of edge `cell_size` (pass
+ * 2h to match a context), a stable sort of the particles by key (equal keys
+ * keep the input order), and the CSR offsets of the cells.  All pointers are
+ * device pointers:
+ *   x, y, z         positions, n doubles each (z ignored, may be NULL, in 2D)
+ *   keys_out[n]     sorted cell keys
+ *   perm_out[n]     input index of each sorted slot
+ *   cell_begin_out  ncell + 1 offsets, ncell = product of ceil((hi - lo) / cell_size)
+ * Work is queued on `stream` (NULL = legacy default stream) and the call
+ * returns without waiting.  Positions outside the domain are clamped into the
+ * edge cell without an error report.
+ *
+ * Scratch memory: a file-scope device array sized for
+ * SPH_NOALLOC_MAX_PARTICLES particles (about 8.3 MB), held on every GPU that
+ * loads the library until the process exits.  n above that limit fails with
+ * SPH_E_INVALID before any work is queued.  The first call on a device looks
+ * up the array's device address and sets kernel attributes for that device
+ * (the device must be current); make that first call before any stream
+ * capture.  No call allocates or frees memory.  All calls share the one
+ * array, which keeps the previous call's contents (what must start at zero is
+ * cleared by each call), so calls whose work overlaps on the GPU -- on
+ * different streams, or from different threads -- race and corrupt each
+ * other's results: order them on one stream or synchronise between them.
+ * Returns SPH_OK, SPH_E_INVALID (bad arguments or n too large) or SPH_E_CUDA. */
+int sph_cell_sort_noalloc(const sph_domain* domain, double cell_size, const double* x,
+                          const double* y, const double* z, size_t n, uint32_t* keys_out,
+                          uint32_t* perm_out, uint32_t* cell_begin_out, void* stream);
+
 /* Sets an sph_option; takes effect at the next sph_step. */
 int sph_set_option(sph_ctx* ctx, int option, long value);
 

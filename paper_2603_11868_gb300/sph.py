@@ -40,7 +40,9 @@ STATUS_NAMES = {0: "SPH_OK", 1: "SPH_E_INVALID", 2: "SPH_E_OOM", 3: "SPH_E_CUDA"
 EXPORTS = ("sph_create", "sph_set_particles", "sph_step", "sph_get_fields", "sph_get_scalars",
            "sph_count", "sph_cell_count", "sph_debug_neighbour_state",
            "sph_debug_neighbour_stats", "sph_set_option", "sph_synchronize", "sph_last_error",
-           "sph_destroy", "sph_profile_stages", "sph_kernels_per_step")
+           "sph_destroy", "sph_profile_stages", "sph_kernels_per_step",
+           "sph_cell_sort_noalloc")
+SPH_NOALLOC_MAX_PARTICLES = 1 << 20
 STAGE_NAMES = ("control", "keys", "sort", "reorder", "offsets", "density_sum", "viscous",
                "half1", "pressure", "density_relax")
 
@@ -115,6 +117,9 @@ def load(path: str | None = None):
         L.sph_profile_stages.argtypes = [vp, i, vp, vp]
         L.sph_kernels_per_step.restype = C.c_long
         L.sph_kernels_per_step.argtypes = [vp]
+        L.sph_cell_sort_noalloc.restype = i
+        L.sph_cell_sort_noalloc.argtypes = [C.POINTER(sph_domain), d, vp, vp, vp, sz, vp, vp, vp,
+                                            vp]
         _lib = L
         return L
 
@@ -228,6 +233,16 @@ def sph_profile_stages(ctx, n):
 
 def sph_kernels_per_step(ctx):
     return load().sph_kernels_per_step(ctx)
+
+
+def sph_cell_sort_noalloc(dim, lo, hi, cell_size, x, y, z, n, keys_out, perm_out,
+                          cell_begin_out, stream=0):
+    """Device-pointer arguments (ints); returns the status code (no raise)."""
+    dom = sph_domain(int(dim), (C.c_double * 3)(*list(lo) + [0.0] * (3 - len(lo))),
+                     (C.c_double * 3)(*list(hi) + [0.0] * (3 - len(hi))))
+    return load().sph_cell_sort_noalloc(C.byref(dom), float(cell_size), x, y, z, int(n),
+                                        keys_out, perm_out, cell_begin_out,
+                                        C.c_void_p(stream) if stream else None)
 
 
 # --- PyTorch plumbing ------------------------------------------------------

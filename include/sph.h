@@ -112,7 +112,12 @@ enum sph_option {
   SPH_OPT_USE_GRAPH = 2,          /* 0/1 (default 1): replay each step as a CUDA graph */
   SPH_OPT_BLOCK = 3,              /* threads per block of the neighbour loops: 64..256,
                                      multiple of 32 (default 128)                      */
-  SPH_OPT_RADIX_BITS = 4          /* digit width of the radix sort: 4..11 (default 8)  */
+  SPH_OPT_RADIX_BITS = 4,         /* digit width of the radix sort: 4..11 (default 8)  */
+  SPH_OPT_NEIGHBOUR_LIST = 5      /* 0/1 (default 1): loops after the density summation
+                                     walk per-particle neighbour lists (candidates within
+                                     2h + skin at the rebuild) instead of the cells while a
+                                     displacement bound shows them complete; results are
+                                     identical either way                               */
 };
 
 /* Creates a context.
@@ -136,7 +141,8 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
  *     time and step counters, the carried density rate and the schedule; the
  *     particles are binned and sorted once.  User order is the given order.
  *   SPH_WALL: static wall particles; vel and rho must be NULL.  Sorted once.
- * n may be 0.  Fails with SPH_E_INVALID on a NULL pos with n > 0. */
+ * n may be 0 and must be below 2^25.  Fails with SPH_E_INVALID on a NULL pos
+ * with n > 0 or on too many particles. */
 int sph_set_particles(sph_ctx* ctx, int kind, size_t n, const double* pos, const double* vel,
                       const double* rho);
 

@@ -250,6 +250,11 @@ int alloc_fluid(sph_ctx* c, size_t n) {
   }
   B.recI = c->precision == SPH_MIXED ? A(nn * (d == 3 ? 16 : 8)) : nullptr;
   ok &= c->precision != SPH_MIXED || B.recI;
+  // neighbour lists: capacity entries per particle, whole warps of 32
+  const size_t warps = (nn + 31) / 32;
+  B.nl = (uint32_t*)A(warps * (size_t)c->P.list_cap * 32 * 4);
+  B.nl_cnt = (uint32_t*)A(nn * 4);
+  ok &= B.nl && B.nl_cnt;
   const size_t tiles = (nn + kSortTile - 1) / kSortTile;
   B.tile_hist = (uint32_t*)A(tiles * ((size_t)1 << kMaxRadixBits) * 4);
   B.io = (double*)A(nn * 3 * 8);
@@ -323,6 +328,9 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
   P.sigma0 = lattice_sigma0(dim, dp, h, P.walpha);
   P.eps = 0.01 * h;
   P.diag = 0;
+  P.use_list = 1;
+  P.list_cap = dim == 3 ? 192 : 64;
+  P.skin_max = 0.6 * h;
 
   int rc = SPH_OK;
   cudaError_t e = cudaGetDevice(&c->device);
@@ -367,7 +375,7 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
                       const double* rho) {
   if (!c) return SPH_E_INVALID;
   if (n > 0 && !pos) return set_err(c, SPH_E_INVALID, "pos is NULL");
-  if (n > 0x7fffffffull) return set_err(c, SPH_E_INVALID, "too many particles");
+  if (n >= (1ull << 25)) return set_err(c, SPH_E_INVALID, "at most 2^25 - 1 particles per kind");
   const int d = c->P.dim;
   if (kind == SPH_FLUID) {
     int rc = enter(c);
@@ -727,6 +735,9 @@ int sph_set_option(sph_ctx* c, int option, long value) {
         return set_err(c, SPH_E_INVALID, "block size must be 64..256, a multiple of 32");
       c->L.block_loop = (int)value;
       configure_launch(c);
+      break;
+    case SPH_OPT_NEIGHBOUR_LIST:
+      c->P.use_list = value ? 1 : 0;
       break;
     case SPH_OPT_RADIX_BITS:
       if (value < 4 || value > kMaxRadixBits)

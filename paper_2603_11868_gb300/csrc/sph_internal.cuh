@@ -73,6 +73,9 @@ struct Params {
   double walpha;  // Wendland alpha_d
   double eps;     // 0.01 h viscous regulariser
   int diag;       // store acc / sigma
+  int use_list;   // neighbour lists enabled
+  int list_cap;   // list capacity (entries per particle)
+  double skin_max;
 };
 
 // Schedule scalars, resident on the device.
@@ -85,6 +88,13 @@ struct DevScalars {
   int started;
   int par;      // live state copy
   int flags;    // sticky error bits
+  // neighbour-list bookkeeping (see the list section of sph_stages.cuh)
+  double skin;     // list radius is 2h + skin for the current advection step
+  double disp;     // bound on any particle's displacement since the rebuild, at step start
+  double disp_p;   // the same bound after this step's first half-drift
+  double dt_prev;  // length of the previous acoustic step
+  int list_bad;    // a list overflowed its capacity in this advection step
+  int pad_;
 };
 
 template <class T>
@@ -121,6 +131,8 @@ struct DevBuffers {
   void* recP[2];    // T4
   void* recS[2];    // T4 (3D) or T2 (2D)
   void* recI;       // mixed mode: int4 (3D) / int2 (2D) fixed-point offsets at the rebuild
+  uint32_t* nl;     // neighbour lists: entry k of particle i at ((i/32) cap + k) 32 + i%32
+  uint32_t* nl_cnt; // list length per particle
   uint32_t* keys[2];  // sort ping-pong; keys[sorted_buf] holds the sorted keys
   uint32_t* vals[2];
   int sorted_buf;

@@ -321,22 +321,39 @@ __global__ void k_cell_offsets(const uint32_t* __restrict__ keys, int n, uint32_
 // ---------------------------------------------------------------------------
 // Dual-criteria schedule, one thread.  vmax2_cur holds max |v|^2 of the
 // current velocities.
+// Also keeps the neighbour-list displacement bound: every half-drift moves a
+// particle by at most dt/2 times the largest speed of the velocities it uses
+// (vmax2_cur holds the maximum after the last kick).
 __global__ void k_control(Params P, DevScalars* sc) {
   double vmax = sqrt(__longlong_as_double((long long)sc->vmax2_cur));
   int adv = (!sc->started || sc->tau >= sc->dt_ad) ? 1 : 0;
+  double disp = sc->started ? sc->disp_p + 0.5 * sc->dt_prev * vmax : 0.0;
+  double dt = 0.6 * P.h / (P.c0 + vmax);
   if (adv) {
     sc->dt_ad = 0.25 * P.h / (P.U_ref > vmax ? P.U_ref : vmax);
     sc->tau = 0.0;
     sc->n_adv += 1;
     sc->started = 1;
+    // skin for this advection step: twice the distance covered at the current
+    // top speed (plus what gravity can add) over the step and one overshooting
+    // acoustic step, with margin; the loops check the bound and fall back to
+    // direct search if it is ever exceeded
+    const double gmag = sqrt(P.g[0] * P.g[0] + P.g[1] * P.g[1] + P.g[2] * P.g[2]);
+    const double span = sc->dt_ad + 1.5 * dt;
+    double skin = 2.5 * (vmax + gmag * span) * span + 0.02 * P.h;
+    sc->skin = skin < P.skin_max ? skin : P.skin_max;
+    sc->list_bad = 0;
+    disp = 0.0;
   }
   sc->new_adv = adv;
-  double dt = 0.6 * P.h / (P.c0 + vmax);
   sc->dt_ac = dt;
   sc->tau += dt;
   sc->t += dt;
   sc->n_ac += 1;
   sc->vmax2_next = 0ull;
+  sc->disp = disp;
+  sc->disp_p = disp + 0.5 * dt * vmax;
+  sc->dt_prev = dt;
 }
 
 // |v|^2 without contraction, same rounding sequence as a plain serial sum

@@ -392,47 +392,145 @@ __global__ void k_reorder(Params P, DevBuffers B, int gated) {
   }
 }
 
-// Density summation: reads records P of buffer 0; writes rho (state) and the
-// rho slot of records S of buffer 0.
+// ---------------------------------------------------------------------------
+// Neighbour lists.  Direct search tests every particle of the 3^D cells
+// (about 475 in 3D) for about 81 accepted neighbours, and the pair arithmetic
+// then runs with few lanes of a warp active.  The density summation, which
+// runs right after each rebuild and walks all candidates anyway, also records
+// for every particle the candidates closer than 2h + skin, in candidate order
+// (cells dz, dy, dx; fluid then wall particles of each cell).  The other loops
+// of the advection step walk that list instead of the cells.
+//
+// Exactness: a candidate left out was at least 2h + skin away at the rebuild;
+// if no particle has moved more than D since then and 2D < skin, it is still
+// farther than 2h, so the accepted set -- and, since the list keeps candidate
+// order, every sum -- is the same as with direct search.  The schedule kernel
+// keeps D as the sum of dt/2 * (largest speed) over the half-drifts since the
+// rebuild; a loop uses the list only while 2D stays below the skin (with a
+// small margin) and no list overflowed, and falls back to direct search
+// otherwise.
+//
+// Entry: neighbour index in bits 0..24, dx+1 / dy+1 / dz+1 in bits 25..30,
+// wall flag in bit 31 (particle and wall counts below 2^25).  Entry k of
+// particle i lives at ((i / 32) cap + k) 32 + i % 32, so a warp's k-th entries
+// are one coalesced 128-byte line.
+constexpr uint32_t kIdxMask = (1u << 25) - 1u;
+
+__device__ __forceinline__ uint32_t nl_code(int dx, int dy, int dz, bool w) {
+  return ((uint32_t)(dx + 1) << 25) | ((uint32_t)(dy + 1) << 27) | ((uint32_t)(dz + 1) << 29) |
+         (w ? 0x80000000u : 0u);
+}
+__device__ __forceinline__ size_t nl_slot(int i, int k, int cap) {
+  return ((size_t)(i >> 5) * (size_t)cap + (size_t)k) * 32u + (size_t)(i & 31);
+}
+
+struct ListWriter {
+  uint32_t* nl;
+  int cap, i, cnt;
+  bool on;
+  __device__ __forceinline__ void add(uint32_t entry) {
+    if (on && cnt < cap) nl[nl_slot(i, cnt, cap)] = entry;
+    ++cnt;
+  }
+};
+
+// Visit the candidates of target i either through its list or through the
+// 3^D cells; v(j, dx, dy, dz, wall) does the test and the arithmetic.
+template <int D, class V>
+__device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffers& B, Cell ci,
+                                                 int i, bool use_list, V&& v) {
+  if (use_list) {
+    const int cnt = (int)B.nl_cnt[i];
+    const uint32_t* __restrict__ e = B.nl + nl_slot(i, 0, P.list_cap);
+    for (int k = 0; k < cnt; ++k) {
+      const uint32_t x = e[(size_t)k * 32u];
+      v((int)(x & kIdxMask), (int)((x >> 25) & 3u) - 1, (int)((x >> 27) & 3u) - 1,
+        (int)((x >> 29) & 3u) - 1, (x >> 31) != 0u);
+    }
+    return;
+  }
+  const uint32_t* __restrict__ cb = B.cell_begin;
+  const uint32_t* __restrict__ wcb = B.wall_cb;
+  for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
+    const uint32_t e = cb[c + 1];
+    for (uint32_t j = cb[c]; j < e; ++j) v((int)j, dx, dy, dz, false);
+    if (P.nw > 0) {
+      const uint32_t we = wcb[c + 1];
+      for (uint32_t w = wcb[c]; w < we; ++w) v((int)w, dx, dy, dz, true);
+    }
+  });
+}
+
+// shift of a neighbour cell in the record frame (zero for absolute positions)
+template <class T>
+__device__ __forceinline__ T cell_shift(int d, T cs) {
+  if constexpr (!Local<T>::kLocal) return T(0);
+  return d == 0 ? T(0) : (d < 0 ? -cs : cs);
+}
+
+// whether this launch may use the lists: disp is the displacement bound of the
+// positions the loop reads
+__device__ __forceinline__ bool list_ok(const Params& P, const DevScalars* sc, double disp) {
+  return P.use_list && !sc->list_bad && 2.0 * disp < 0.999 * sc->skin - 1e-6 * P.h;
+}
+
+// Pair geometry shared by the loops: r_ij = x_i - x_j of neighbour j.
+template <int D, class T>
+struct PairGeo {
+  using R = Rec<D, T>;
+  using WR = WallRec<D, T>;
+  const typename R::PV* __restrict__ recP;
+  const typename WR::WV* __restrict__ wall;
+  T xi, yi, zi;
+  T cs;
+  __device__ __forceinline__ void rel(int j, int dx, int dy, int dz, bool w, T& rx, T& ry,
+                                      T& rz) const {
+    const T bx = xi - cell_shift<T>(dx, cs);
+    const T by = yi - cell_shift<T>(dy, cs);
+    const T bz = zi - cell_shift<T>(dz, cs);
+    if (w) {
+      const typename WR::WV pw = wall[j];
+      rx = dsub(bx, pw.x); ry = dsub(by, pw.y); rz = dsub(bz, WR::z(pw));
+    } else {
+      const typename R::PV pj = recP[j];
+      rx = dsub(bx, R::px(pj)); ry = dsub(by, R::py(pj)); rz = dsub(bz, R::pz(pj));
+    }
+  }
+};
+
+// Density summation (FP64 path): reads records P of buffer 0; writes rho
+// (state), the rho slot of records S of buffer 0, and the neighbour lists.
 template <int D, class T>
 __global__ void __launch_bounds__(256) k_density_summation(Params P, DevBuffers B, KC<T> k,
                                                            int gated) {
   using R = Rec<D, T>;
-  using WR = WallRec<D, T>;
   DevScalars* sc = B.sc;
   if (gated && !sc->new_adv) return;
   double* rho_live = sc->par ? B.rho[1] : B.rho[0];
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
   typename R::SV* recS = (typename R::SV*)B.recS[0];
-  const typename WR::WV* __restrict__ wall = (const typename WR::WV*)B.wallP;
   const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
-  const uint32_t* __restrict__ cb = B.cell_begin;
-  const uint32_t* __restrict__ wcb = B.wall_cb;
+  const double rl = 2.0 * P.h + sc->skin;
+  const T rl2 = (T)(rl * rl);
+  int overflow = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
     const Cell ci = decode(keys[i], P);
     const typename R::PV pi = recP[i];
-    const T xi = R::px(pi), yi = R::py(pi), zi = R::pz(pi);
+    PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
+                    R::pz(pi), k.cs};
+    ListWriter L{B.nl, P.list_cap, i, 0, P.use_list != 0};
     T sig = T(0);
-    for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
-      const T sx = Local<T>::kLocal ? T(dx) * k.cs : T(0);
-      const T sy = Local<T>::kLocal ? T(dy) * k.cs : T(0);
-      const T sz = Local<T>::kLocal ? T(dz) * k.cs : T(0);
-      const T bx = xi - sx, by = yi - sy, bz = zi - sz;
-      const uint32_t e = cb[c + 1];
-      for (uint32_t j = cb[c]; j < e; ++j) {
-        const typename R::PV pj = recP[j];
-        const T r2 = r2_of(dsub(bx, R::px(pj)), dsub(by, R::py(pj)), dsub(bz, R::pz(pj)));
-        if (r2 < k.r2max) sig += wendland(k, sqrt(r2));
-      }
-      if (P.nw > 0) {
-        const uint32_t we = wcb[c + 1];
-        for (uint32_t w = wcb[c]; w < we; ++w) {
-          const typename WR::WV pw = wall[w];
-          const T r2 = r2_of(dsub(bx, pw.x), dsub(by, pw.y), dsub(bz, WR::z(pw)));
-          if (r2 < k.r2max) sig += wendland(k, sqrt(r2));
-        }
-      }
+    visit_neighbours<D>(P, B, ci, i, false, [&](int j, int dx, int dy, int dz, bool w) {
+      T rx, ry, rz;
+      G.rel(j, dx, dy, dz, w, rx, ry, rz);
+      const T r2 = r2_of(rx, ry, rz);
+      if (r2 < k.r2max) sig += wendland(k, sqrt(r2));
+      if (r2 < rl2 && (w || j != i)) L.add((uint32_t)j | nl_code(dx, dy, dz, w));
     });
+    if (P.use_list) {
+      B.nl_cnt[i] = (uint32_t)min(L.cnt, P.list_cap);
+      if (L.cnt > P.list_cap) overflow = 1;
+    }
     double ratio = (double)sig / P.sigma0;
     double rho = P.rho0 * (ratio > 1.0 ? ratio : 1.0);
     rho_live[i] = rho;
@@ -441,12 +539,28 @@ __global__ void __launch_bounds__(256) k_density_summation(Params P, DevBuffers 
     recS[i] = s;
     if (P.diag) ((T*)B.sigma)[i] = sig;
   }
+  if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(&sc->list_bad, 1);
 }
 
 // Density summation of the mixed path: exact integer pair distances from the
 // fixed-point offsets of the rebuild and the kernel in double-float, so the
 // density (and through c0^2 the pressure) keeps double-precision accuracy
-// while every operation runs on the FP32 / integer pipes.
+// while every operation runs on the FP32 / integer pipes.  Also writes the
+// neighbour lists (membership from the same exact integer distances).
+template <int D>
+__device__ __forceinline__ unsigned long long fx_r2(const typename FxRec<D>::V& a,
+                                                    const typename FxRec<D>::V& b, int dx, int dy,
+                                                    int dz) {
+  const long long ex = (a.x - dx * (int)kFxOne) - b.x;
+  const long long ey = (a.y - dy * (int)kFxOne) - b.y;
+  unsigned long long R2 = (unsigned long long)(ex * ex) + (unsigned long long)(ey * ey);
+  if constexpr (D == 3) {
+    const long long ez = (a.z - dz * (int)kFxOne) - b.z;
+    R2 += (unsigned long long)(ez * ez);
+  }
+  return R2;
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_density_summation_fx(Params P, DevBuffers B,
                                                               int gated) {
@@ -459,42 +573,26 @@ __global__ void __launch_bounds__(256) k_density_summation_fx(Params P, DevBuffe
   const FV* __restrict__ wrec = (const FV*)B.wallI;
   typename R::SV* recS = (typename R::SV*)B.recS[0];
   const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
-  const uint32_t* __restrict__ cb = B.cell_begin;
-  const uint32_t* __restrict__ wcb = B.wall_cb;
   const unsigned long long cut2 = 1ull << (2 * kFxShift);
+  // list radius in fixed-point units, rounded up (a superset is safe)
+  const double rl_cells = (2.0 * P.h + sc->skin) / P.cs;
+  const unsigned long long lim2 =
+      (unsigned long long)(rl_cells * rl_cells * 72057594037927936.0) + 1ull;  // * 2^56
+  int overflow = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
     const Cell ci = decode(keys[i], P);
     const FV oi = rec[i];
+    ListWriter L{B.nl, P.list_cap, i, 0, P.use_list != 0};
     dfl sig = {0.0f, 0.0f};
-    for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
-      const int bx = oi.x - dx * (int)kFxOne, by = oi.y - dy * (int)kFxOne;
-      int bz = 0;
-      if constexpr (D == 3) bz = oi.z - dz * (int)kFxOne;
-      const uint32_t e = cb[c + 1];
-      for (uint32_t j = cb[c]; j < e; ++j) {
-        const FV oj = rec[j];
-        const long long ex = bx - oj.x, ey = by - oj.y;
-        unsigned long long R2 = (unsigned long long)(ex * ex) + (unsigned long long)(ey * ey);
-        if constexpr (D == 3) {
-          const long long ez = bz - oj.z;
-          R2 += (unsigned long long)(ez * ez);
-        }
-        if (R2 < cut2) sig = df_add(sig, wendland_shape_fx(R2));
-      }
-      if (P.nw > 0) {
-        const uint32_t we = wcb[c + 1];
-        for (uint32_t w = wcb[c]; w < we; ++w) {
-          const FV ow = wrec[w];
-          const long long ex = bx - ow.x, ey = by - ow.y;
-          unsigned long long R2 = (unsigned long long)(ex * ex) + (unsigned long long)(ey * ey);
-          if constexpr (D == 3) {
-            const long long ez = bz - ow.z;
-            R2 += (unsigned long long)(ez * ez);
-          }
-          if (R2 < cut2) sig = df_add(sig, wendland_shape_fx(R2));
-        }
-      }
+    visit_neighbours<D>(P, B, ci, i, false, [&](int j, int dx, int dy, int dz, bool w) {
+      const unsigned long long R2 = fx_r2<D>(oi, w ? wrec[j] : rec[j], dx, dy, dz);
+      if (R2 < cut2) sig = df_add(sig, wendland_shape_fx(R2));
+      if (R2 < lim2 && (w || j != i)) L.add((uint32_t)j | nl_code(dx, dy, dz, w));
     });
+    if (P.use_list) {
+      B.nl_cnt[i] = (uint32_t)min(L.cnt, P.list_cap);
+      if (L.cnt > P.list_cap) overflow = 1;
+    }
     const double sigma = P.walpha * ((double)sig.hi + (double)sig.lo);
     const double ratio = sigma / P.sigma0;
     const double rho = P.rho0 * (ratio > 1.0 ? ratio : 1.0);
@@ -504,22 +602,21 @@ __global__ void __launch_bounds__(256) k_density_summation_fx(Params P, DevBuffe
     recS[i] = s;
     if (P.diag) ((float*)B.sigma)[i] = (float)sigma;
   }
+  if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(&sc->list_bad, 1);
 }
 
 // Viscous force: reads records P, S of buffer 0 (S carries the new rho);
-// writes a_prior = g + viscous acceleration.
+// writes a_prior = g + viscous acceleration.  Positions are those of the
+// rebuild, so the lists are always usable here (unless one overflowed).
 template <int D, class T>
 __global__ void __launch_bounds__(256) k_viscous(Params P, DevBuffers B, KC<T> k, int gated) {
   using R = Rec<D, T>;
-  using WR = WallRec<D, T>;
   DevScalars* sc = B.sc;
   if (gated && !sc->new_adv) return;
+  const bool use_list = list_ok(P, sc, 0.0);
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
   const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
-  const typename WR::WV* __restrict__ wall = (const typename WR::WV*)B.wallP;
   const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
-  const uint32_t* __restrict__ cb = B.cell_begin;
-  const uint32_t* __restrict__ wcb = B.wall_cb;
   T* ap0 = (T*)B.aprior[0];
   T* ap1 = (T*)B.aprior[1];
   T* ap2 = (T*)B.aprior[2];
@@ -528,41 +625,28 @@ __global__ void __launch_bounds__(256) k_viscous(Params P, DevBuffers B, KC<T> k
     const Cell ci = decode(keys[i], P);
     const typename R::PV pi = recP[i];
     const typename R::SV si = recS[i];
-    const T xi = R::px(pi), yi = R::py(pi), zi = R::pz(pi);
+    PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
+                    R::pz(pi), k.cs};
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     T ax = 0, ay = 0, az = 0;
-    for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
-      const T sx = Local<T>::kLocal ? T(dx) * k.cs : T(0);
-      const T sy = Local<T>::kLocal ? T(dy) * k.cs : T(0);
-      const T sz = Local<T>::kLocal ? T(dz) * k.cs : T(0);
-      const T bx = xi - sx, by = yi - sy, bz = zi - sz;
-      const uint32_t e = cb[c + 1];
-      for (uint32_t j = cb[c]; j < e; ++j) {
+    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
+      T rx, ry, rz;
+      G.rel(j, dx, dy, dz, w, rx, ry, rz);
+      const T r2 = r2_of(rx, ry, rz);
+      if (!(r2 < k.r2max) || (!w && j == i)) return;
+      const T r = sqrt(r2);
+      if (w) {
+        const T coef = wallV * wendland_dr(k, r) / (r + k.eps);
+        ax += coef * vxi;
+        ay += coef * vyi;
+        az += coef * vzi;
+      } else {
         const typename R::PV pj = recP[j];
-        const T rx = dsub(bx, R::px(pj)), ry = dsub(by, R::py(pj)), rz = dsub(bz, R::pz(pj));
-        const T r2 = r2_of(rx, ry, rz);
-        if (r2 < k.r2max && (int)j != i) {
-          const typename R::SV sj = recS[j];
-          const T r = sqrt(r2);
-          const T coef = div_t(k.m, R::rho(pj, sj)) * wendland_dr(k, r) / (r + k.eps);
-          ax += coef * (vxi - R::vx(pj, sj));
-          ay += coef * (vyi - R::vy(pj, sj));
-          az += coef * (vzi - R::vz(pj, sj));
-        }
-      }
-      if (P.nw > 0) {
-        const uint32_t we = wcb[c + 1];
-        for (uint32_t w = wcb[c]; w < we; ++w) {
-          const typename WR::WV pw = wall[w];
-          const T r2 = r2_of(dsub(bx, pw.x), dsub(by, pw.y), dsub(bz, WR::z(pw)));
-          if (r2 < k.r2max) {
-            const T r = sqrt(r2);
-            const T coef = wallV * wendland_dr(k, r) / (r + k.eps);
-            ax += coef * vxi;
-            ay += coef * vyi;
-            az += coef * vzi;
-          }
-        }
+        const typename R::SV sj = recS[j];
+        const T coef = div_t(k.m, R::rho(pj, sj)) * wendland_dr(k, r) / (r + k.eps);
+        ax += coef * (vxi - R::vx(pj, sj));
+        ay += coef * (vyi - R::vy(pj, sj));
+        az += coef * (vzi - R::vz(pj, sj));
       }
     });
     const T f = div_t(k.two_mu, R::rho(pi, si));
@@ -607,19 +691,16 @@ __global__ void k_half1(Params P, DevBuffers B) {
 template <int D, class T>
 __global__ void __launch_bounds__(256) k_pressure(Params P, DevBuffers B, KC<T> k) {
   using R = Rec<D, T>;
-  using WR = WallRec<D, T>;
   DevScalars* sc = B.sc;
   const int par = sc->par;
   const double dt = sc->dt_ac;
   const double hdt = 0.5 * dt;
+  const bool use_list = list_ok(P, sc, sc->disp_p);
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
   const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
   typename R::PV* outP = (typename R::PV*)B.recP[1];
   typename R::SV* outS = (typename R::SV*)B.recS[1];
-  const typename WR::WV* __restrict__ wall = (const typename WR::WV*)B.wallP;
   const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
-  const uint32_t* __restrict__ cb = B.cell_begin;
-  const uint32_t* __restrict__ wcb = B.wall_cb;
   const T* ap0 = (const T*)B.aprior[0];
   const T* ap1 = (const T*)B.aprior[1];
   const T* ap2 = (const T*)B.aprior[2];
@@ -630,66 +711,43 @@ __global__ void __launch_bounds__(256) k_pressure(Params P, DevBuffers B, KC<T> 
     const Cell ci = decode(keys[i], P);
     const typename R::PV pi = recP[i];
     const typename R::SV si = recS[i];
-    const T xi = R::px(pi), yi = R::py(pi), zi = R::pz(pi);
+    PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
+                    R::pz(pi), k.cs};
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     const T p_i = R::pres(pi, si), rho_i = R::rho(pi, si);
     T ax = 0, ay = 0, az = 0;
-    for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
-      const T sx = Local<T>::kLocal ? T(dx) * k.cs : T(0);
-      const T sy = Local<T>::kLocal ? T(dy) * k.cs : T(0);
-      const T sz = Local<T>::kLocal ? T(dz) * k.cs : T(0);
-      const T bx = xi - sx, by = yi - sy, bz = zi - sz;
-      const uint32_t e = cb[c + 1];
-      for (uint32_t j = cb[c]; j < e; ++j) {
+    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
+      T rx, ry, rz;
+      G.rel(j, dx, dy, dz, w, rx, ry, rz);
+      const T r2 = r2_of(rx, ry, rz);
+      if (!(r2 < k.r2max) || (!w && j == i)) return;
+      const T inv_r = inv_sqrt_t(r2);
+      const T r = r2 * inv_r;
+      const T ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
+      const T UL = -(vxi * ex + vyi * ey + vzi * ez);
+      T UR, p_j, rho_j;
+      if (w) {
+        // mirrored state: p_w = p_i + rho_i (x_w - x_i).g, x_w - x_i = -r_vec
+        const T gdot = -(rx * k.g[0] + ry * k.g[1] + rz * k.g[2]);
+        p_j = p_i + rho_i * gdot;
+        rho_j = k.rho0 + p_j * k.inv_c0sq;
+        UR = -UL;
+      } else {
         const typename R::PV pj = recP[j];
-        const T rx = dsub(bx, R::px(pj)), ry = dsub(by, R::py(pj)), rz = dsub(bz, R::pz(pj));
-        const T r2 = r2_of(rx, ry, rz);
-        if (r2 < k.r2max && (int)j != i) {
-          const typename R::SV sj = recS[j];
-          const T inv_r = inv_sqrt_t(r2);
-          const T r = r2 * inv_r;
-          const T ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
-          const T UL = -(vxi * ex + vyi * ey + vzi * ez);
-          const T UR = -(R::vx(pj, sj) * ex + R::vy(pj, sj) * ey + R::vz(pj, sj) * ez);
-          const T rho_j = R::rho(pj, sj);
-          const T rbar = k.half * (rho_i + rho_j);
-          const T jump = UL - UR;
-          T beta = T(3) * (jump > T(0) ? jump : T(0)) * k.inv_c0;
-          beta = beta < T(1) ? beta : T(1);
-          const T Ps = k.half * (p_i + R::pres(pj, sj)) + k.half * beta * rbar * k.c0 * jump;
-          const T f = Ps * div_t(k.m, rho_j) * wendland_dr(k, r);
-          ax += f * ex;
-          ay += f * ey;
-          az += f * ez;
-        }
+        const typename R::SV sj = recS[j];
+        UR = -(R::vx(pj, sj) * ex + R::vy(pj, sj) * ey + R::vz(pj, sj) * ez);
+        p_j = R::pres(pj, sj);
+        rho_j = R::rho(pj, sj);
       }
-      if (P.nw > 0) {
-        const uint32_t we = wcb[c + 1];
-        for (uint32_t w = wcb[c]; w < we; ++w) {
-          const typename WR::WV pw = wall[w];
-          const T rx = dsub(bx, pw.x), ry = dsub(by, pw.y), rz = dsub(bz, WR::z(pw));
-          const T r2 = r2_of(rx, ry, rz);
-          if (r2 < k.r2max) {
-            const T inv_r = inv_sqrt_t(r2);
-            const T r = r2 * inv_r;
-            const T ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
-            // mirrored state: p_w = p_i + rho_i (x_w - x_i).g, x_w - x_i = -r_vec
-            const T gdot = -(rx * k.g[0] + ry * k.g[1] + rz * k.g[2]);
-            const T pw_ = p_i + rho_i * gdot;
-            const T rho_w = k.rho0 + pw_ * k.inv_c0sq;
-            const T UL = -(vxi * ex + vyi * ey + vzi * ez);
-            const T jump = UL + UL;
-            const T rbar = k.half * (rho_i + rho_w);
-            T beta = T(3) * (jump > T(0) ? jump : T(0)) * k.inv_c0;
-            beta = beta < T(1) ? beta : T(1);
-            const T Ps = k.half * (p_i + pw_) + k.half * beta * rbar * k.c0 * jump;
-            const T f = Ps * div_t(k.m, rho_w) * wendland_dr(k, r);
-            ax += f * ex;
-            ay += f * ey;
-            az += f * ez;
-          }
-        }
-      }
+      const T rbar = k.half * (rho_i + rho_j);
+      const T jump = UL - UR;
+      T beta = T(3) * (jump > T(0) ? jump : T(0)) * k.inv_c0;
+      beta = beta < T(1) ? beta : T(1);
+      const T Ps = k.half * (p_i + p_j) + k.half * beta * rbar * k.c0 * jump;
+      const T f = Ps * div_t(k.m, rho_j) * wendland_dr(k, r);
+      ax += f * ex;
+      ay += f * ey;
+      az += f * ez;
     });
     const T s = div_t(T(-2), rho_i);
     ax *= s;
@@ -737,16 +795,16 @@ __global__ void __launch_bounds__(256) k_pressure(Params P, DevBuffers B, KC<T> 
 template <int D, class T>
 __global__ void __launch_bounds__(256) k_density_relax(Params P, DevBuffers B, KC<T> k) {
   using R = Rec<D, T>;
-  using WR = WallRec<D, T>;
   DevScalars* sc = B.sc;
   const int par = sc->par;
   const double hdt = 0.5 * sc->dt_ac;
+  // positions after the second half-drift: bound grows by dt/2 * top speed after the kick
+  const double disp2 =
+      sc->disp_p + hdt * sqrt(__longlong_as_double((long long)sc->vmax2_next));
+  const bool use_list = list_ok(P, sc, disp2);
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[1];
   const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[1];
-  const typename WR::WV* __restrict__ wall = (const typename WR::WV*)B.wallP;
   const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
-  const uint32_t* __restrict__ cb = B.cell_begin;
-  const uint32_t* __restrict__ wcb = B.wall_cb;
   const Live<T> S = live<T>(B, par);
   int bad = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) sc->vmax2_cur = sc->vmax2_next;
@@ -754,53 +812,36 @@ __global__ void __launch_bounds__(256) k_density_relax(Params P, DevBuffers B, K
     const Cell ci = decode(keys[i], P);
     const typename R::PV pi = recP[i];
     const typename R::SV si = recS[i];
-    const T xi = R::px(pi), yi = R::py(pi), zi = R::pz(pi);
+    PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
+                    R::pz(pi), k.cs};
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     const T p_i = R::pres(pi, si), rho_i = R::rho(pi, si);
     T sum = 0;
-    for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
-      const T sx = Local<T>::kLocal ? T(dx) * k.cs : T(0);
-      const T sy = Local<T>::kLocal ? T(dy) * k.cs : T(0);
-      const T sz = Local<T>::kLocal ? T(dz) * k.cs : T(0);
-      const T bx = xi - sx, by = yi - sy, bz = zi - sz;
-      const uint32_t e = cb[c + 1];
-      for (uint32_t j = cb[c]; j < e; ++j) {
+    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
+      T rx, ry, rz;
+      G.rel(j, dx, dy, dz, w, rx, ry, rz);
+      const T r2 = r2_of(rx, ry, rz);
+      if (!(r2 < k.r2max) || (!w && j == i)) return;
+      const T inv_r = inv_sqrt_t(r2);
+      const T r = r2 * inv_r;
+      const T ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
+      const T UL = -(vxi * ex + vyi * ey + vzi * ez);
+      if (w) {
+        const T gdot = -(rx * k.g[0] + ry * k.g[1] + rz * k.g[2]);
+        const T pw_ = p_i + rho_i * gdot;
+        const T rho_w = k.rho0 + pw_ * k.inv_c0sq;
+        const T rbar = k.half * (rho_i + rho_w);
+        // U_R = -U_L, so (U_L + U_R)/2 = 0
+        const T Us = div_t(p_i - pw_, T(2) * rbar * k.c0);
+        sum += div_t(k.m, rho_w) * wendland_dr(k, r) * (UL - Us);
+      } else {
         const typename R::PV pj = recP[j];
-        const T rx = dsub(bx, R::px(pj)), ry = dsub(by, R::py(pj)), rz = dsub(bz, R::pz(pj));
-        const T r2 = r2_of(rx, ry, rz);
-        if (r2 < k.r2max && (int)j != i) {
-          const typename R::SV sj = recS[j];
-          const T inv_r = inv_sqrt_t(r2);
-          const T r = r2 * inv_r;
-          const T ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
-          const T UL = -(vxi * ex + vyi * ey + vzi * ez);
-          const T UR = -(R::vx(pj, sj) * ex + R::vy(pj, sj) * ey + R::vz(pj, sj) * ez);
-          const T rho_j = R::rho(pj, sj);
-          const T rbar = k.half * (rho_i + rho_j);
-          const T Us = k.half * (UL + UR) + div_t(p_i - R::pres(pj, sj), T(2) * rbar * k.c0);
-          sum += div_t(k.m, rho_j) * wendland_dr(k, r) * (UL - Us);
-        }
-      }
-      if (P.nw > 0) {
-        const uint32_t we = wcb[c + 1];
-        for (uint32_t w = wcb[c]; w < we; ++w) {
-          const typename WR::WV pw = wall[w];
-          const T rx = dsub(bx, pw.x), ry = dsub(by, pw.y), rz = dsub(bz, WR::z(pw));
-          const T r2 = r2_of(rx, ry, rz);
-          if (r2 < k.r2max) {
-            const T inv_r = inv_sqrt_t(r2);
-            const T r = r2 * inv_r;
-            const T ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
-            const T gdot = -(rx * k.g[0] + ry * k.g[1] + rz * k.g[2]);
-            const T pw_ = p_i + rho_i * gdot;
-            const T rho_w = k.rho0 + pw_ * k.inv_c0sq;
-            const T UL = -(vxi * ex + vyi * ey + vzi * ez);
-            const T rbar = k.half * (rho_i + rho_w);
-            // U_R = -U_L, so (U_L + U_R)/2 = 0
-            const T Us = div_t(p_i - pw_, T(2) * rbar * k.c0);
-            sum += div_t(k.m, rho_w) * wendland_dr(k, r) * (UL - Us);
-          }
-        }
+        const typename R::SV sj = recS[j];
+        const T UR = -(R::vx(pj, sj) * ex + R::vy(pj, sj) * ey + R::vz(pj, sj) * ez);
+        const T rho_j = R::rho(pj, sj);
+        const T rbar = k.half * (rho_i + rho_j);
+        const T Us = k.half * (UL + UR) + div_t(p_i - R::pres(pj, sj), T(2) * rbar * k.c0);
+        sum += div_t(k.m, rho_j) * wendland_dr(k, r) * (UL - Us);
       }
     });
     const T dr = T(-2) * rho_i * sum;

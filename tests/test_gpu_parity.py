@@ -184,6 +184,24 @@ def test_graph_and_eager_identical(sph):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["dam_break_2d", "dam_break_3d_small"])
+def test_neighbour_list_identical_to_direct_search(sph, name, precision):
+    """Lists built at the rebuild (radius 2h + skin, candidate order) give the
+    same bits as direct search while the displacement bound holds, and the
+    loops fall back to direct search otherwise: 60 steps, 12 rebuilds."""
+    case = SORT_CASES[name]()
+    out = []
+    for use_list in (1, 0):
+        s = sph.Solver(case, precision=precision)
+        s.set_option(sph.SPH_OPT_NEIGHBOUR_LIST, use_list)
+        s.step(60)
+        out.append(s.fields("pos", "vel", "rho", "drho"))
+        s.close()
+    for k in out[0]:
+        assert np.array_equal(out[0][k], out[1][k]), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_deterministic(sph, precision):
     case = small_3d()
     out = []

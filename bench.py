@@ -220,6 +220,115 @@ def time_steps(solver, steps, substeps, torch):
     return e0.elapsed_time(e1) / 1e3
 
 
+def run_nsearch(args):
+    """Neighbour-search microbenchmark: 2^24 particles uniform in the unit cube
+    (seeded), h such that each particle has 57 others within 2h on average;
+    cell keys + radix sort + reorder + cell offsets + one density pass, with
+    float64 and float32 positions, timed per stage."""
+    import torch
+    from paper_2603_11868_gb300 import build, cases, sph
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    sph.load()
+    case = cases.uniform_cube(n=1 << 24, seed=3, neighbours=57.0)
+    res = {}
+    for label, dt, fp32 in (("f64", torch.float64, False), ("f32", torch.float32, True)):
+        dev = [torch.tensor(np.ascontiguousarray(case.fluid[:, k]), dtype=dt, device="cuda")
+               for k in range(3)]
+        ns = sph.NeighbourSearch(3, case.lo, case.hi, case.h, fp32=fp32)
+        for _ in range(args.warmup):
+            ns.run(*dev, timed=False)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(args.steps):
+            ns.run(*dev, timed=False)
+        e1.record(st)
+        e1.synchronize()
+        el = e0.elapsed_time(e1) / 1e3 / args.steps
+        stages = {k: 0.0 for k in ns.STAGES}
+        for _ in range(3):
+            for k, v in ns.run(*dev).items():
+                stages[k] += v / 3
+        res[label] = {"particles_per_s": case.n / el, "ms_per_run": el * 1e3,
+                      "stage_ms": {k: round(v, 4) for k, v in stages.items()}}
+        ns.close()
+        del dev
+    if rank == 0:
+        line = {"metric": "neighbour-search particles/s (keys + radix sort + reorder + offsets "
+                          "+ density pass), 16M uniform",
+                "value": res["f32"]["particles_per_s"], "unit": "particles/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": res["f32"]["ms_per_run"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 positions",
+                "data": "synthetic",
+                "config": {"workload": f"uniform cube, {case.n} particles, h={case.h:.6g}, "
+                                       f"{57} neighbours within 2h on average",
+                           "l2": "inputs larger than L2 (no flush)"},
+                "f32": res["f32"], "f64": res["f64"]}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def batched_cases(n_tanks: int = 256, dp: float = 0.01):
+    """256 independent 2D dam-break tanks, fluid counts log-uniform in
+    [1 000, 64 000] (seeded), dp = 0.01, 4 wall layers each."""
+    from paper_2603_11868_gb300 import cases
+    sizes = cases.batched_tank_sizes(n_tanks, seed=4)
+    return [cases.batched_tank(n, dp=dp, seed=100 + k) for k, n in enumerate(sizes)]
+
+
+def run_batched(args):
+    """Batched tanks: every tank advances one acoustic step (its own length)
+    per graph launch; value = total fluid particles x acoustic steps / time."""
+    import torch
+    from paper_2603_11868_gb300 import build, sph
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    sph.load()
+    cs = batched_cases()
+    b = sph.Batch(cs, precision=args.precision)
+    n, nw = b.n, b.nw
+    for _ in range(args.warmup):
+        b.step(args.substeps)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        el = time_steps(b, args.steps, args.substeps, torch)
+    sph.sph_batch_synchronize(b.b, 60.0)
+    value = n * args.steps * args.substeps / el
+    stages, rebuilds = b.profile(2 * args.substeps)
+    per_step = {k: v / (2 * args.substeps) for k, v in stages.items()}
+    kernels = sph.sph_batch_kernels_per_step(b.b)
+    sc = b.scalars()
+    b.close()
+    if rank == 0:
+        line = {"metric": "particle-steps/s, 256 batched 2D dam-break tanks (1k-64k particles "
+                          "each), FP32-mixed",
+                "value": value, "unit": "particle-steps/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 pair / f64 state" if args.precision == "mixed" else "f64",
+                "data": "synthetic",
+                "config": {"workload": f"{len(cs)} tanks, {n} fluid + {nw} wall particles, "
+                                       f"dp=0.01, {args.substeps} acoustic steps per bench step",
+                           "l2": "state larger than L2 (no flush)"},
+                "acoustic_steps_per_bench_step": args.substeps,
+                "stage_ms_per_acoustic_step": {k: round(v, 4) for k, v in per_step.items()},
+                "advection_steps_begun_per_acoustic_step": rebuilds / (2 * args.substeps),
+                "gpu_launches": kernels * args.substeps * args.steps,
+                "kernels_per_acoustic_step": kernels,
+                "tank_time_spread": [float(np.min(sc["t"])), float(np.max(sc["t"]))],
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_2603_11868_gb300 import build, sph
@@ -373,7 +482,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dam_break_3d_5m",
-                    choices=["dam_break_3d_5m", "dam_break_3d_80k", "dam_break_2d"])
+                    choices=["dam_break_3d_5m", "dam_break_3d_80k", "dam_break_2d",
+                             "nsearch_16m", "batched_256"])
     ap.add_argument("--dp", type=float, default=None,
                     help="3D dam break at this spacing instead of the named workload")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
@@ -386,6 +496,10 @@ def main():
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "nsearch_16m":
+        return run_nsearch(args)
+    if args.workload == "batched_256":
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -211,6 +211,39 @@ int sph_profile_stages(sph_ctx* ctx, int n, double* ms, long* rebuilds);
 /* Kernel launches one acoustic step queues (graph nodes of the step). */
 long sph_kernels_per_step(const sph_ctx* ctx);
 
+/* ---- Standalone neighbour search (the paper's cell-linked list build and one
+ * direct-search density pass, section "Cell linked-list, direct search and
+ * sorting"), for measuring the neighbour search on its own. ---------------- */
+typedef struct sph_nsearch sph_nsearch;
+
+/* Creates a neighbour search on the grid of `domain` with cells of edge 2h.
+ * pos_precision: SPH_FP64 for double positions, SPH_MIXED for float
+ * positions.  Device memory comes from `alloc` (or cudaMalloc); work is queued
+ * on `stream`.  SPH_E_INVALID on bad arguments. */
+int sph_nsearch_create(const sph_domain* domain, double h, int pos_precision,
+                       const sph_allocator* alloc, void* stream, sph_nsearch** out);
+
+/* Runs, for n particles given as device SoA coordinate arrays x, y, z (float
+ * or double as created; z ignored in 2D): cell keys, the stable radix sort,
+ * the reorder of the positions, the CSR cell offsets, and one density pass
+ * sigma_i = sum_{r_ij < 2h} W(r_ij) (self included) in the position type.
+ * stage_ms, if not NULL, receives the device time of the five stages (and the
+ * call then waits for them).  Buffers grow as needed. */
+int sph_nsearch_run(sph_nsearch* ns, size_t n, const void* x, const void* y, const void* z,
+                    double* stage_ms);
+
+/* Copies the last run's sorted keys[n], permutation perm[n] (input index of each
+ * sorted slot), cell_begin[ncell + 1] and sigma[n] (sorted order) to the host;
+ * any pointer may be NULL.  Waits for the run. */
+int sph_nsearch_results(sph_nsearch* ns, uint32_t* keys, uint32_t* perm, uint32_t* cell_begin,
+                        double* sigma);
+
+/* Cells of the grid (no synchronisation). */
+size_t sph_nsearch_cell_count(const sph_nsearch* ns);
+
+/* Frees everything (waits first). */
+void sph_nsearch_destroy(sph_nsearch* ns);
+
 /* Largest n accepted by sph_cell_sort_noalloc. */
 #define SPH_NOALLOC_MAX_PARTICLES (1u << 20)
 
@@ -248,6 +281,78 @@ long sph_kernels_per_step(const sph_ctx* ctx);
 int sph_cell_sort_noalloc(const sph_domain* domain, double cell_size, const double* x,
                           const double* y, const double* z, size_t n, uint32_t* keys_out,
                           uint32_t* perm_out, uint32_t* cell_begin_out, void* stream);
+
+/* ---- Batches of independent tanks.  The paper runs one problem at a time;
+ * a batch advances many small, independent problems together (each its own
+ * domain, particles, material, gravity and its own dual-criteria schedule, so
+ * its advection and acoustic steps have their own lengths).  Every stage of
+ * an acoustic step is one persistent launch over the tiles of all tanks (the
+ * rebuild stages over the tanks that begin an advection step in that step),
+ * and the step is replayed as one CUDA graph.  A tank of a batch computes
+ * exactly what an sph_ctx computes for it alone with the same options. */
+typedef struct sph_batch sph_batch;
+
+/* One tank: what sph_create takes for a single problem. */
+typedef struct {
+  sph_domain domain;
+  double dp, h;
+  sph_material material;
+  double gravity[3];
+} sph_tank;
+
+/* Largest number of tanks in a batch. */
+#define SPH_MAX_TANKS 1024
+
+/* Creates a batch of n_tanks (1..SPH_MAX_TANKS) tanks, all of the same
+ * dimension, computing in `precision`; allocator and stream as sph_create.
+ * SPH_E_INVALID for a bad tank (same rules as sph_create) or a total cell
+ * count of 2^31 or more. */
+int sph_create_batch(int n_tanks, const sph_tank* tanks, int precision,
+                     const sph_allocator* alloc, void* cuda_stream, sph_batch** out);
+
+/* Sets the particles of one kind for every tank: counts[t] particles for
+ * tank t (counts has n_tanks entries, a count may be 0), pos holds
+ * sum(counts) * dim doubles, tank 0's particles first (vel, rho as
+ * sph_set_particles: NULL = zero velocity / the tank's rho0; walls take
+ * positions only).  The total of each kind must stay below 2^25. */
+int sph_batch_set_particles(sph_batch* b, int kind, const size_t* counts, const double* pos,
+                            const double* vel, const double* rho);
+
+/* Queues n acoustic steps of every tank (each on its own schedule). */
+int sph_batch_step(sph_batch* b, int n);
+
+/* Fields as sph_get_fields, for all tanks: tank 0's particles first, each
+ * tank in its user order. */
+int sph_batch_get_fields(sph_batch* b, unsigned mask, double* out);
+
+/* Schedule scalars of every tank (arrays of n_tanks; any may be NULL). */
+int sph_batch_get_scalars(sph_batch* b, double* t, double* dt_ad, double* dt_ac, long* n_ac,
+                          long* n_adv);
+
+/* Neighbour structure of one tank after its last rebuild, in the tank's own
+ * numbering (as sph_debug_neighbour_state for that tank alone): keys[n] the
+ * binned cell of each storage slot, ids[n] the user index of each slot,
+ * cell_begin[ncell + 1] (ncell of that tank's grid); any may be NULL. */
+int sph_batch_debug_neighbour_state(sph_batch* b, int tank, uint32_t* keys, uint32_t* ids,
+                                    uint32_t* cell_begin);
+
+/* Totals over the tanks (kind = SPH_FLUID / SPH_WALL), the number of tanks,
+ * and one tank's cell count (no synchronisation; 0 for a bad argument). */
+size_t sph_batch_count(const sph_batch* b, int kind);
+int sph_batch_tank_count(const sph_batch* b);
+size_t sph_batch_cell_count(const sph_batch* b, int tank);
+
+/* As sph_profile_stages / sph_kernels_per_step for a batch; rebuilds counts
+ * the advection steps begun, summed over the tanks. */
+int sph_batch_profile_stages(sph_batch* b, int n, double* ms, long* rebuilds);
+long sph_batch_kernels_per_step(const sph_batch* b);
+
+/* Options as sph_set_option (SPH_OPT_BLOCK also sets the tile: slots per
+ * work unit of the persistent launches). */
+int sph_batch_set_option(sph_batch* b, int option, long value);
+int sph_batch_synchronize(sph_batch* b, double timeout_s);
+const char* sph_batch_last_error(const sph_batch* b);
+void sph_batch_destroy(sph_batch* b);
 
 /* Sets an sph_option; takes effect at the next sph_step. */
 int sph_set_option(sph_ctx* ctx, int option, long value);

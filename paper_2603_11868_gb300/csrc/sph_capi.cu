@@ -14,20 +14,10 @@
 #include <vector>
 
 #include "sph.h"
+#include "sph_host.cuh"
 #include "sph_internal.cuh"
 
 using namespace sphgb;
-
-namespace {
-
-constexpr double kPi = 3.14159265358979323846;
-
-struct Block {
-  void* p;
-  size_t bytes;
-};
-
-}  // namespace
 
 struct sph_ctx {
   Params P{};
@@ -102,29 +92,13 @@ void drop_graph(sph_ctx* c) {
   c->graph = nullptr;
 }
 
-// Reference number density of the unperturbed lattice (self included).
-double lattice_sigma0(int dim, double dp, double h, double walpha) {
-  const int K = (int)std::ceil(2.0 * h / dp) + 1;
-  const int kz = dim == 3 ? K : 0;
-  double s = 0.0;
-  for (int c = -kz; c <= kz; ++c)
-    for (int b = -K; b <= K; ++b)
-      for (int a = -K; a <= K; ++a) {
-        const double r = dp * std::sqrt((double)(a * a + b * b + c * c));
-        const double q = r / h;
-        if (q >= 2.0) continue;
-        const double t = 1.0 - 0.5 * q;
-        s += walpha * t * t * t * t * (2.0 * q + 1.0);
-      }
-  return s;
-}
-
 size_t tsize(const sph_ctx* c) { return c->precision == SPH_FP64 ? 8 : 4; }
 
 StageArgs args(const sph_ctx* c) {
   StageArgs a;
   a.P = c->P;
   a.B = c->B;
+  a.B.binned = a.B.keys[a.B.sorted_buf];
   a.L = c->L;
   return a;
 }
@@ -324,7 +298,7 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
   P.U_ref = mat->U_ref;
   P.V = dim == 2 ? dp * dp : dp * dp * dp;
   P.m = mat->rho0 * P.V;
-  P.walpha = dim == 2 ? 7.0 / (4.0 * kPi * h * h) : 21.0 / (16.0 * kPi * h * h * h);
+  P.walpha = wendland_alpha(dim, h);
   P.sigma0 = lattice_sigma0(dim, dp, h, P.walpha);
   P.eps = 0.01 * h;
   P.diag = 0;

@@ -76,6 +76,10 @@ struct Params {
   int use_list;   // neighbour lists enabled
   int list_cap;   // list capacity (entries per particle)
   double skin_max;
+  // position of this tank in the arrays of a batch (all zero for one tank):
+  // first fluid slot, first wall slot, first entry of its cell offsets
+  int foff, woff;
+  uint32_t cell_base;
 };
 
 // Schedule scalars, resident on the device.
@@ -136,6 +140,9 @@ struct DevBuffers {
   uint32_t* keys[2];  // sort ping-pong; keys[sorted_buf] holds the sorted keys
   uint32_t* vals[2];
   int sorted_buf;
+  // binned cell key of every storage slot (the cell of the last rebuild, in
+  // its tank's grid): keys[sorted_buf] for one tank, a separate array in a batch
+  const uint32_t* binned;
   uint32_t* tile_hist;  // bins x tiles
   uint32_t* digit_total;
   uint32_t* cell_begin;  // ncell + 1
@@ -162,6 +169,81 @@ struct LaunchCfg {
   int key_bits;
   int tiles;  // radix tiles
 };
+
+// ---------------------------------------------------------------------------
+// Batches of independent tanks.  Tank t owns the fluid slots
+// [foff, foff + n), the wall slots [woff, woff + nw) and the cell offsets
+// [cell_base, cell_base + ncell] of the shared arrays (its Params), and its
+// own schedule (DevScalars).  Every batched stage is one persistent launch
+// whose blocks walk a work list: the tiles of `tile` slots of the listed
+// tanks, or (cell offsets) their chunks of kOffsetsChunk cells.  A tank's
+// cell key in the batch-wide sort is cell_base + its cell index, so one
+// stable sort keeps every tank's particles inside its own range.
+constexpr int kMaxTanks = 1024;
+
+struct WorkList {
+  int count;   // listed tanks
+  int tiles;   // total tiles
+  int chunks;  // total offset chunks
+  int m;       // total slots of the listed tanks (length of the compacted sort)
+  int tile;    // slots per tile
+  int pad_[3];
+  int tank[kMaxTanks];
+  int tile_prefix[kMaxTanks + 1];
+  int chunk_prefix[kMaxTanks + 1];
+  int cbase[kMaxTanks];  // first compacted sort slot of each listed tank
+};
+
+// Device-side view of a batch, passed by value to the batched kernels.
+struct BatchArgs {
+  const Params* tP;    // per tank
+  const void* tK;      // per tank KC<T> of the pair type
+  DevScalars* tsc;     // per tank
+  WorkList* wl_all;    // every tank (static)
+  WorkList* wl_adv;    // tanks that begin an advection step (schedule kernel)
+  WorkList* wl_wall;   // every tank, wall tiles (static)
+  uint32_t* bkey;      // binned cell key of every fluid slot
+  int ntanks;
+  int n_total, nw_total;
+  int tiles_max;       // tiles of wl_all: bound of every fluid list (grid sizing)
+  int chunks_max;      // offset chunks of every tank
+};
+
+struct BatchStageArgs {
+  BatchArgs A;
+  DevBuffers B;  // shared arrays; B.sc unused, B.binned = A.bkey
+  LaunchCfg L;
+  int dim;
+};
+
+// batched schedule kernel: per-tank dual-criteria schedule, then the list of
+// tanks that begin an advection step (force: every tank with fluid, schedule
+// untouched -- the initial sort)
+void launch_batch_control(const BatchArgs& A, int tile, int force, cudaStream_t s);
+// batched cell keys of the listed tanks into compacted sort slots (walls: from
+// the staging SoA x[0]; fluid: from the live copy x[par] of each tank); block 0
+// clears the digit totals of the sort
+void launch_batch_cell_keys(const BatchArgs& A, const WorkList* wl, int walls,
+                            double* const x[2][3], uint32_t* keys, uint32_t* vals,
+                            uint32_t* digit_total, int bins, int grid, int block,
+                            cudaStream_t s);
+// batched CSR offsets of the listed tanks from the compacted sorted keys
+// (256 threads per block)
+void launch_batch_cell_offsets(const BatchArgs& A, const WorkList* wl, int walls, int grid,
+                               const uint32_t* keys, uint32_t* cb, int flip_par,
+                               cudaStream_t s);
+// fresh max |v|^2 per tank (live copy) into vmax2_cur (walks wl_all)
+void launch_batch_vmax(const BatchArgs& A, const DevBuffers& B, int grid, int block,
+                       cudaStream_t s);
+
+void enqueue_batch_step_fp64(const BatchStageArgs& a, cudaStream_t s, cudaEvent_t* ev = nullptr);
+void enqueue_batch_step_mixed(const BatchStageArgs& a, cudaStream_t s, cudaEvent_t* ev = nullptr);
+void enqueue_batch_initial_sort_fp64(const BatchStageArgs& a, cudaStream_t s);
+void enqueue_batch_initial_sort_mixed(const BatchStageArgs& a, cudaStream_t s);
+// walls of every tank from the staging SoA B.io ([x | y | z], nw_total each);
+// sort scratch in a.B.keys / vals / tile_hist
+void enqueue_batch_wall_setup_fp64(const BatchStageArgs& a, cudaStream_t s);
+void enqueue_batch_wall_setup_mixed(const BatchStageArgs& a, cudaStream_t s);
 
 // --- launch interface implemented per precision (sph_fp64.cu / sph_mixed.cu)
 struct StageArgs {
@@ -205,6 +287,11 @@ cudaError_t configure_sort_kernels();
 int launch_radix_sort(const LaunchCfg& L, uint32_t* keys[2], uint32_t* vals[2], int n,
                       uint32_t* tile_hist, uint32_t* digit_total, const DevScalars* sc,
                       int gated, cudaStream_t s);
+// the same sort over the first *n_dev entries (a count decided on the device,
+// at most n_max)
+int launch_radix_sort_dev(const LaunchCfg& L, uint32_t* keys[2], uint32_t* vals[2], int n_max,
+                          uint32_t* tile_hist, uint32_t* digit_total, const int* n_dev,
+                          cudaStream_t s);
 // CSR offsets from sorted keys; if flip_par, thread 0 flips sc->par afterwards
 void launch_cell_offsets(const uint32_t* keys, int n, uint32_t ncell, uint32_t* cell_begin,
                          DevScalars* sc, int gated, int flip_par, cudaStream_t s);
@@ -218,7 +305,68 @@ void launch_neighbour_stats(const Params& P, const LaunchCfg& L, const DevBuffer
                             const double* wall_xyz, uint32_t* cnt_f, uint32_t* cnt_w,
                             unsigned long long* hash, cudaStream_t s);
 
+// Work-list walkers: f(list position, first slot of the tile within the tank,
+// tile length) for every tile of the list, tiles dealt round-robin to blocks;
+// the tank of a tile is found by binary search in the prefix of tile counts
+// (tanks without tiles are skipped by taking the last position <= w).
+__device__ __forceinline__ int wl_find(const int* __restrict__ prefix, int count, int w) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= w)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+template <class F>
+__device__ __forceinline__ void for_each_tile(const WorkList* __restrict__ wl, F&& f) {
+  const int total = wl->tiles, cnt = wl->count, tile = wl->tile;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int a = wl_find(wl->tile_prefix, cnt, w);
+    f(a, (w - wl->tile_prefix[a]) * tile, tile);
+  }
+}
+template <class F>
+__device__ __forceinline__ void for_each_chunk(const WorkList* __restrict__ wl, F&& f) {
+  const int total = wl->chunks, cnt = wl->count;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const int a = wl_find(wl->chunk_prefix, cnt, w);
+    f(a, w - wl->chunk_prefix[a]);
+  }
+}
+
 int radix_passes_for(int key_bits, int radix_bits);
 int bits_for(uint32_t ncell);
+
+// Cell index along one axis: floor(fl((x - lo) / cs)) with a correctly rounded
+// subtraction and division, clamped into [0, nc - 1] (oob set when clamped or
+// not finite).  The quotient is first formed in float; when it lies farther
+// from the nearest integer than its worst-case error (three float roundings,
+// < 2e-7 relative), the double quotient has the same floor and the division
+// is skipped.  Only coordinates within that distance of a cell face take the
+// double division, so the result always equals the plain double formula.
+__device__ __forceinline__ int cell_coord_fast(double x, double lo, double cs, float inv_cs,
+                                               int nc, int& oob) {
+  const double d = __dsub_rn(x, lo);
+  const float qf = __fmul_rn((float)d, inv_cs);
+  const float fq = floorf(qf);
+  const float dist = fminf(qf - fq, fq + 1.0f - qf);
+  double f;
+  if (dist > 1e-6f * fabsf(qf) + 4e-6f)
+    f = (double)fq;
+  else
+    f = floor(__ddiv_rn(d, cs));
+  if (!(f >= 0.0)) {
+    oob = 1;
+    return 0;
+  }
+  if (f >= (double)nc) {
+    oob = 1;
+    return nc - 1;
+  }
+  return (int)f;
+}
 
 }  // namespace sphgb

@@ -23,21 +23,6 @@ __device__ __forceinline__ unsigned lanemask_lt() {
   return m;
 }
 
-// Cell of one coordinate: floor((x - lo) / cs) with a correctly rounded
-// subtraction and division (no contraction), clamped into [0, nc - 1].
-__device__ __forceinline__ int cell_coord(double x, double lo, double cs, int nc, int& oob) {
-  double f = floor(__ddiv_rn(__dsub_rn(x, lo), cs));
-  if (!(f >= 0.0)) {
-    oob = 1;
-    return 0;
-  }
-  if (f >= (double)nc) {
-    oob = 1;
-    return nc - 1;
-  }
-  return (int)f;
-}
-
 struct XSet {
   const double* x[2][3];
 };
@@ -53,10 +38,11 @@ __global__ void k_cell_keys(Params P, XSet xs, uint32_t* __restrict__ keys,
   const double* __restrict__ x1 = xs.x[par][1];
   const double* __restrict__ x2 = xs.x[par][2];
   int oob = 0;
+  const float inv_cs = (float)(1.0 / P.cs);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int cx = cell_coord(x0[i], P.lo[0], P.cs, P.nx, oob);
-    int cy = cell_coord(x1[i], P.lo[1], P.cs, P.ny, oob);
-    int cz = P.dim == 3 ? cell_coord(x2[i], P.lo[2], P.cs, P.nz, oob) : 0;
+    int cx = cell_coord_fast(x0[i], P.lo[0], P.cs, inv_cs, P.nx, oob);
+    int cy = cell_coord_fast(x1[i], P.lo[1], P.cs, inv_cs, P.ny, oob);
+    int cz = P.dim == 3 ? cell_coord_fast(x2[i], P.lo[2], P.cs, inv_cs, P.nz, oob) : 0;
     keys[i] = ((uint32_t)cz * (uint32_t)P.ny + (uint32_t)cy) * (uint32_t)P.nx + (uint32_t)cx;
     vals[i] = (uint32_t)i;
   }
@@ -70,10 +56,21 @@ __global__ void k_cell_keys(Params P, XSet xs, uint32_t* __restrict__ keys,
 // ranks are stable.  Histograms and ranks use __match_any_sync: the lanes that
 // share a digit count once per round through their leader.
 
+// The key count is n, or *n_dev when n_dev is given (a count decided on the
+// device; the grid is then sized for n, its upper bound).
+__device__ __forceinline__ void sort_count(int& n, int& tiles, const int* n_dev) {
+  if (n_dev) {
+    n = *n_dev;
+    tiles = (n + kSortTile - 1) / kSortTile;
+  }
+}
+
 __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int n, int shift, uint32_t mask,
                              uint32_t* __restrict__ tile_hist, uint32_t* digit_total, int tiles,
-                             const DevScalars* sc, int gated) {
+                             const DevScalars* sc, int gated, const int* n_dev) {
   if (gated && !sc->new_adv) return;
+  sort_count(n, tiles, n_dev);
+  if ((int)blockIdx.x >= tiles) return;
   extern __shared__ uint32_t smem[];
   const int bins = (int)mask + 1;
   const int warps = blockDim.x / 32;
@@ -131,8 +128,10 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
 
 // One block per digit: offsets[d][t] = sum of all digits < d + sum of tiles < t.
 __global__ void k_radix_scan(uint32_t* __restrict__ tile_hist, const uint32_t* digit_total,
-                             int tiles, const DevScalars* sc, int gated) {
+                             int tiles, const DevScalars* sc, int gated, const int* n_dev) {
   if (gated && !sc->new_adv) return;
+  int n = 0;
+  sort_count(n, tiles, n_dev);
   __shared__ uint32_t ws[33];
   const int d = blockIdx.x;
   uint32_t part = 0;
@@ -158,8 +157,9 @@ __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t
                                 uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, int n,
                                 int shift, uint32_t mask, const uint32_t* __restrict__ offsets,
                                 int tiles, const DevScalars* sc, int gated,
-                                uint32_t* digit_total) {
+                                uint32_t* digit_total, const int* n_dev) {
   if (gated && !sc->new_adv) return;
+  sort_count(n, tiles, n_dev);
   extern __shared__ uint32_t smem[];
   const int bins = (int)mask + 1;
   const int warps = blockDim.x / 32;
@@ -174,6 +174,7 @@ __global__ void k_radix_scatter(const uint32_t* __restrict__ kin, const uint32_t
     // the scan of this pass has consumed the totals: clear them for the next pass
     for (int t = threadIdx.x; t < bins; t += blockDim.x) digit_total[t] = 0;
   }
+  if ((int)blockIdx.x >= tiles) return;
   for (int t = threadIdx.x; t < warps * bins; t += blockDim.x) wcnt[t] = 0;
   __syncthreads();
   const int tile = blockIdx.x;
@@ -264,29 +265,29 @@ __device__ uint32_t warp_lower_bound(const uint32_t* __restrict__ keys, uint32_t
   return a + __popc(__ballot_sync(kFull, pred));
 }
 
-// cell_begin[c] = first sorted index with key >= c, for c in a chunk of
-// kOffsetsChunk cells per block; cell_begin[ncell] = n.
-__global__ void k_cell_offsets(const uint32_t* __restrict__ keys, int n, uint32_t ncell,
-                               uint32_t* __restrict__ cb, DevScalars* sc, int gated,
-                               int flip_par) {
-  if (gated && !sc->new_adv) return;
-  __shared__ uint32_t first[kOffsetsChunk];
+// Offsets of the local cells [c0, c1) of one grid whose sorted keys are
+// keys[0..n) (key = kbase + local cell): cb[c] = first + (first position with
+// key >= kbase + c); the chunk that ends at ncell also writes cb[ncell] =
+// first + n.  One block per chunk; blocks may call it for several chunks.
+__device__ __forceinline__ void offsets_chunk(const uint32_t* __restrict__ keys, uint32_t n,
+                                              uint32_t kbase, uint32_t c0, uint32_t c1,
+                                              uint32_t ncell, uint32_t first,
+                                              uint32_t* __restrict__ cb) {
+  __shared__ uint32_t sfirst[kOffsetsChunk];
   __shared__ uint32_t bounds[2];
   __shared__ uint32_t wmin[32];
-  const uint32_t c0 = blockIdx.x * kOffsetsChunk;
-  const uint32_t c1 = min(c0 + (uint32_t)kOffsetsChunk, ncell);
   const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (w < 2) {
-    uint32_t r = warp_lower_bound(keys, (uint32_t)n, w == 0 ? c0 : c1);
+    uint32_t r = warp_lower_bound(keys, n, kbase + (w == 0 ? c0 : c1));
     if (lane == 0) bounds[w] = r;
   }
   __syncthreads();
   const uint32_t lo = bounds[0], hi = bounds[1];
-  for (int t = threadIdx.x; t < kOffsetsChunk; t += blockDim.x) first[t] = hi;
+  for (int t = threadIdx.x; t < kOffsetsChunk; t += blockDim.x) sfirst[t] = hi;
   __syncthreads();
   for (uint32_t k = lo + threadIdx.x; k < hi; k += blockDim.x) {
     uint32_t kk = keys[k];
-    if (k == lo || keys[k - 1] != kk) first[kk - c0] = k;
+    if (k == lo || keys[k - 1] != kk) sfirst[kk - kbase - c0] = k;
   }
   __syncthreads();
   // suffix minimum: an empty cell starts where the next non-empty cell starts
@@ -294,7 +295,7 @@ __global__ void k_cell_offsets(const uint32_t* __restrict__ keys, int n, uint32_
   uint32_t v[PER];
   const int t0 = threadIdx.x * PER;
 #pragma unroll
-  for (int j = 0; j < PER; ++j) v[j] = first[t0 + j];
+  for (int j = 0; j < PER; ++j) v[j] = sfirst[t0 + j];
 #pragma unroll
   for (int j = PER - 2; j >= 0; --j) v[j] = min(v[j], v[j + 1]);
   uint32_t incl = v[0];
@@ -312,9 +313,20 @@ __global__ void k_cell_offsets(const uint32_t* __restrict__ keys, int n, uint32_
 #pragma unroll
   for (int j = 0; j < PER; ++j) {
     uint32_t c = c0 + t0 + j;
-    if (c < c1) cb[c] = min(v[j], excl);
+    if (c < c1) cb[c] = first + min(v[j], excl);
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) cb[ncell] = (uint32_t)n;
+  if (c1 == ncell && threadIdx.x == 0) cb[ncell] = first + n;
+  __syncthreads();  // the shared arrays are reused by the block's next chunk
+}
+
+// cell_begin of one grid, kOffsetsChunk cells per block (256 threads).
+__global__ void k_cell_offsets(const uint32_t* __restrict__ keys, int n, uint32_t ncell,
+                               uint32_t* __restrict__ cb, DevScalars* sc, int gated,
+                               int flip_par) {
+  if (gated && !sc->new_adv) return;
+  const uint32_t c0 = blockIdx.x * kOffsetsChunk;
+  const uint32_t c1 = min(c0 + (uint32_t)kOffsetsChunk, ncell);
+  offsets_chunk(keys, (uint32_t)n, 0u, c0, c1, ncell, 0u, cb);
   if (flip_par && blockIdx.x == 0 && threadIdx.x == 0) sc->par ^= 1;
 }
 
@@ -324,7 +336,7 @@ __global__ void k_cell_offsets(const uint32_t* __restrict__ keys, int n, uint32_
 // Also keeps the neighbour-list displacement bound: every half-drift moves a
 // particle by at most dt/2 times the largest speed of the velocities it uses
 // (vmax2_cur holds the maximum after the last kick).
-__global__ void k_control(Params P, DevScalars* sc) {
+__device__ __forceinline__ void control_one(const Params& P, DevScalars* sc) {
   double vmax = sqrt(__longlong_as_double((long long)sc->vmax2_cur));
   int adv = (!sc->started || sc->tau >= sc->dt_ad) ? 1 : 0;
   double disp = sc->started ? sc->disp_p + 0.5 * sc->dt_prev * vmax : 0.0;
@@ -356,6 +368,110 @@ __global__ void k_control(Params P, DevScalars* sc) {
   sc->dt_prev = dt;
 }
 
+__global__ void k_control(Params P, DevScalars* sc) { control_one(P, sc); }
+
+// ---------------------------------------------------------------------------
+// Batched schedule: one thread per tank (one block of up to kMaxTanks
+// threads).  The velocity maximum of the previous step's pressure stage
+// becomes the current one, the tank's schedule advances as for a single tank,
+// and the tanks that begin an advection step are listed (in tank order) with
+// their tile, chunk and compacted-slot prefixes.
+__global__ void kb_control(BatchArgs A, int tile, int force) {
+  __shared__ uint32_t ws[33];
+  WorkList* wl = A.wl_adv;
+  const int t = threadIdx.x;
+  uint32_t on = 0, tiles = 0, chunks = 0, n = 0;
+  if (t < A.ntanks) {
+    const Params& P = A.tP[t];
+    DevScalars* sc = A.tsc + t;
+    if (force) {
+      on = 1;
+    } else {
+      if (sc->started) sc->vmax2_cur = sc->vmax2_next;
+      control_one(P, sc);
+      on = sc->new_adv && P.n > 0;
+    }
+    if (on) {
+      n = (uint32_t)P.n;
+      tiles = (n + (uint32_t)tile - 1) / (uint32_t)tile;
+      chunks = (P.ncell + kOffsetsChunk - 1) / kOffsetsChunk;
+    }
+  }
+  uint32_t tot_on, tot_tiles, tot_chunks, tot_n;
+  const uint32_t pos = block_exclusive_scan(on, ws, tot_on);
+  const uint32_t tp = block_exclusive_scan(tiles, ws, tot_tiles);
+  const uint32_t cp = block_exclusive_scan(chunks, ws, tot_chunks);
+  const uint32_t np = block_exclusive_scan(n, ws, tot_n);
+  if (on) {
+    wl->tank[pos] = t;
+    wl->tile_prefix[pos] = (int)tp;
+    wl->chunk_prefix[pos] = (int)cp;
+    wl->cbase[pos] = (int)np;
+  }
+  if (t == 0) {
+    wl->count = (int)tot_on;
+    wl->tiles = (int)tot_tiles;
+    wl->chunks = (int)tot_chunks;
+    wl->m = (int)tot_n;
+    wl->tile = tile;
+    wl->tile_prefix[tot_on] = (int)tot_tiles;
+    wl->chunk_prefix[tot_on] = (int)tot_chunks;
+  }
+}
+
+// Batched cell keys: slot first + q of a listed tank goes to compacted slot
+// cbase + q with key cell_base + (its cell in the tank's grid), value = slot.
+__global__ void kb_cell_keys(BatchArgs A, const WorkList* wl, int walls, XSet xs,
+                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                             uint32_t* digit_total, int bins) {
+  if (blockIdx.x == 0)
+    for (int t = threadIdx.x; t < bins; t += blockDim.x) digit_total[t] = 0;
+  for_each_tile(wl, [&](int a, int off, int tile) {
+    const int t = wl->tank[a];
+    const Params& P = A.tP[t];
+    const int par = walls ? 0 : A.tsc[t].par;
+    const int first = walls ? P.woff : P.foff, cnt = walls ? P.nw : P.n;
+    const int base = wl->cbase[a];
+    const double* __restrict__ x0 = par ? xs.x[1][0] : xs.x[0][0];
+    const double* __restrict__ x1 = par ? xs.x[1][1] : xs.x[0][1];
+    const double* __restrict__ x2 = par ? xs.x[1][2] : xs.x[0][2];
+    const float inv_cs = (float)(1.0 / P.cs);
+    const double lo0 = P.lo[0], lo1 = P.lo[1], lo2 = P.lo[2], cs = P.cs;
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const uint32_t cbase = P.cell_base;
+    int oob = 0;
+    const int end = min(off + tile, cnt);
+    for (int q = off + (int)threadIdx.x; q < end; q += blockDim.x) {
+      const int i = first + q;
+      const int cx = cell_coord_fast(x0[i], lo0, cs, inv_cs, nx, oob);
+      const int cy = cell_coord_fast(x1[i], lo1, cs, inv_cs, ny, oob);
+      const int cz = P.dim == 3 ? cell_coord_fast(x2[i], lo2, cs, inv_cs, nz, oob) : 0;
+      keys[base + q] =
+          cbase + ((uint32_t)cz * (uint32_t)ny + (uint32_t)cy) * (uint32_t)nx + (uint32_t)cx;
+      vals[base + q] = (uint32_t)i;
+    }
+    if (__syncthreads_or(oob) && threadIdx.x == 0 && !walls)
+      atomicOr(&A.tsc[t].flags, kFlagOutOfDomain);
+  });
+}
+
+// Batched CSR offsets of the listed tanks (chunks of kOffsetsChunk cells);
+// flip_par: the tank's live copy flips once its reorder is done.
+__global__ void kb_cell_offsets(BatchArgs A, const WorkList* wl, int walls,
+                                const uint32_t* __restrict__ keys, uint32_t* cb, int flip_par) {
+  for_each_chunk(wl, [&](int a, int j) {
+    const int t = wl->tank[a];
+    const Params& P = A.tP[t];
+    const uint32_t n = (uint32_t)(walls ? P.nw : P.n);
+    const uint32_t first = (uint32_t)(walls ? P.woff : P.foff);
+    const uint32_t ncell = P.ncell, kbase = P.cell_base;
+    const uint32_t c0 = (uint32_t)j * kOffsetsChunk;
+    const uint32_t c1 = min(c0 + (uint32_t)kOffsetsChunk, ncell);
+    offsets_chunk(keys + wl->cbase[a], n, kbase, c0, c1, ncell, first, cb + kbase);
+    if (flip_par && j == 0 && threadIdx.x == 0) A.tsc[t].par ^= 1;
+  });
+}
+
 // |v|^2 without contraction, same rounding sequence as a plain serial sum
 __device__ __forceinline__ double speed2(double a, double b, double c) {
   return __dadd_rn(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)), __dmul_rn(c, c));
@@ -380,6 +496,34 @@ __global__ void k_vmax(Params P, DevBuffers B, int n) {
     for (int q = 1; q < (int)(blockDim.x / 32); ++q) m = fmax(m, wm[q]);
     atomicMax(&sc->vmax2_cur, (unsigned long long)__double_as_longlong(m));
   }
+}
+
+__global__ void kb_vmax(BatchArgs A, DevBuffers B) {
+  __shared__ double wm[32];
+  const WorkList* wl = A.wl_all;
+  for_each_tile(wl, [&](int a, int off, int tile) {
+    const int t = wl->tank[a];
+    const Params& P = A.tP[t];
+    const int par = A.tsc[t].par;
+    const double* v0 = par ? B.v[1][0] : B.v[0][0];
+    const double* v1 = par ? B.v[1][1] : B.v[0][1];
+    const double* v2 = par ? B.v[1][2] : B.v[0][2];
+    const int end = min(off + tile, P.n);
+    double m = 0.0;
+    for (int q = off + (int)threadIdx.x; q < end; q += blockDim.x) {
+      const int i = P.foff + q;
+      const double s = speed2(v0[i], v1[i], P.dim == 3 ? v2[i] : 0.0);
+      m = s > m ? s : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+    __syncthreads();
+    if (threadIdx.x % 32 == 0) wm[threadIdx.x / 32] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 1; q < (int)(blockDim.x / 32); ++q) m = fmax(m, wm[q]);
+      atomicMax(&A.tsc[t].vmax2_cur, (unsigned long long)__double_as_longlong(m));
+    }
+  });
 }
 
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
@@ -523,9 +667,10 @@ cudaError_t configure_sort_kernels() {
                               (int)scatter_smem(1 << kMaxRadixBits));
 }
 
-int launch_radix_sort(const LaunchCfg& L, uint32_t* keys[2], uint32_t* vals[2], int n,
-                      uint32_t* tile_hist, uint32_t* digit_total, const DevScalars* sc,
-                      int gated, cudaStream_t s) {
+namespace {
+int radix_sort_impl(const LaunchCfg& L, uint32_t* keys[2], uint32_t* vals[2], int n,
+                    uint32_t* tile_hist, uint32_t* digit_total, const DevScalars* sc, int gated,
+                    const int* n_dev, cudaStream_t s) {
   const int tiles = (n + kSortTile - 1) / kSortTile;
   int cur = 0;
   if (n <= 0) return 0;
@@ -537,14 +682,27 @@ int launch_radix_sort(const LaunchCfg& L, uint32_t* keys[2], uint32_t* vals[2], 
     const int bins = (int)mask + 1;
     k_radix_hist<<<tiles, kSortThreads, hist_smem(bins), s>>>(keys[cur], n, shift, mask,
                                                               tile_hist, digit_total, tiles, sc,
-                                                              gated);
-    k_radix_scan<<<bins, 256, 0, s>>>(tile_hist, digit_total, tiles, sc, gated);
+                                                              gated, n_dev);
+    k_radix_scan<<<bins, 256, 0, s>>>(tile_hist, digit_total, tiles, sc, gated, n_dev);
     k_radix_scatter<<<tiles, kSortThreads, scatter_smem(bins), s>>>(
         keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift, mask, tile_hist, tiles, sc,
-        gated, digit_total);
+        gated, digit_total, n_dev);
     cur ^= 1;
   }
   return cur;
+}
+}  // namespace
+
+int launch_radix_sort(const LaunchCfg& L, uint32_t* keys[2], uint32_t* vals[2], int n,
+                      uint32_t* tile_hist, uint32_t* digit_total, const DevScalars* sc,
+                      int gated, cudaStream_t s) {
+  return radix_sort_impl(L, keys, vals, n, tile_hist, digit_total, sc, gated, nullptr, s);
+}
+
+int launch_radix_sort_dev(const LaunchCfg& L, uint32_t* keys[2], uint32_t* vals[2], int n_max,
+                          uint32_t* tile_hist, uint32_t* digit_total, const int* n_dev,
+                          cudaStream_t s) {
+  return radix_sort_impl(L, keys, vals, n_max, tile_hist, digit_total, nullptr, 0, n_dev, s);
 }
 
 void launch_cell_offsets(const uint32_t* keys, int n, uint32_t ncell, uint32_t* cell_begin,
@@ -555,6 +713,33 @@ void launch_cell_offsets(const uint32_t* keys, int n, uint32_t ncell, uint32_t* 
 
 void launch_control(const Params& P, DevScalars* sc, cudaStream_t s) {
   k_control<<<1, 1, 0, s>>>(P, sc);
+}
+
+void launch_batch_control(const BatchArgs& A, int tile, int force, cudaStream_t s) {
+  const int threads = ((A.ntanks + 31) / 32) * 32;
+  kb_control<<<1, threads < 32 ? 32 : threads, 0, s>>>(A, tile, force);
+}
+
+void launch_batch_cell_keys(const BatchArgs& A, const WorkList* wl, int walls,
+                            double* const x[2][3], uint32_t* keys, uint32_t* vals,
+                            uint32_t* digit_total, int bins, int grid, int block,
+                            cudaStream_t s) {
+  XSet xs;
+  for (int p = 0; p < 2; ++p)
+    for (int k = 0; k < 3; ++k) xs.x[p][k] = x[p][k];
+  kb_cell_keys<<<grid < 1 ? 1 : grid, block, 0, s>>>(A, wl, walls, xs, keys, vals, digit_total,
+                                                     bins);
+}
+
+void launch_batch_cell_offsets(const BatchArgs& A, const WorkList* wl, int walls, int grid,
+                               const uint32_t* keys, uint32_t* cb, int flip_par,
+                               cudaStream_t s) {
+  kb_cell_offsets<<<grid < 1 ? 1 : grid, 256, 0, s>>>(A, wl, walls, keys, cb, flip_par);
+}
+
+void launch_batch_vmax(const BatchArgs& A, const DevBuffers& B, int grid, int block,
+                       cudaStream_t s) {
+  kb_vmax<<<grid < 1 ? 1 : grid, block, 0, s>>>(A, B);
 }
 
 void launch_vmax_reset(const Params& P, const LaunchCfg& L, const DevBuffers& B,

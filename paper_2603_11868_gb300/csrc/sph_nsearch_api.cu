@@ -1,0 +1,334 @@
+// Standalone neighbour search (sph_nsearch_*): the cell-linked-list build of
+// the paper (cell keys, device radix sort, reorder, cell offsets; section
+// "Cell linked-list, direct search and sorting") followed by one direct-search
+// density pass, over caller-provided device positions in float or double.
+// Each stage is timed with CUDA events on the object's stream.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "sph.h"
+#include "sph_internal.cuh"
+
+using namespace sphgb;
+
+struct sph_nsearch {
+  Params P{};
+  LaunchCfg L{};
+  int fp32 = 0;  // positions are float
+  sph_allocator alloc{};
+  bool has_alloc = false;
+  cudaStream_t user_stream = nullptr, stream = nullptr;
+  cudaEvent_t ev[6] = {};
+  size_t cap = 0;
+  struct Blk {
+    void* p;
+    size_t b;
+  };
+  std::vector<Blk> blocks, fixed;
+  uint32_t *keys[2] = {}, *vals[2] = {}, *tile_hist = nullptr, *digit_total = nullptr,
+           *cell_begin = nullptr;
+  void* xs[3] = {};  // sorted positions (float or double)
+  double* sigma = nullptr;
+  int sorted = 0;
+  size_t n = 0;
+};
+
+namespace {
+
+constexpr double kPiN = 3.14159265358979323846;
+
+void* ns_alloc(sph_nsearch* s, size_t bytes, std::vector<sph_nsearch::Blk>& list) {
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (!bytes) bytes = 256;
+  void* p = nullptr;
+  if (s->has_alloc) {
+    p = s->alloc.alloc(bytes, (void*)s->stream, s->alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) list.push_back({p, bytes});
+  return p;
+}
+
+void ns_free(sph_nsearch* s, std::vector<sph_nsearch::Blk>& list) {
+  for (auto& b : list) {
+    if (s->has_alloc)
+      s->alloc.free(b.p, b.b, (void*)s->stream, s->alloc.user);
+    else
+      cudaFree(b.p);
+  }
+  list.clear();
+}
+
+// Cell key from float or double coordinates: the coordinate is widened to
+// double (exact) and binned with the same formula as the simulation path
+// (clamped; this entry point reports no out-of-domain flag).
+template <class T>
+__global__ void k_ns_keys(Params P, const T* __restrict__ x, const T* __restrict__ y,
+                          const T* __restrict__ z, int n, uint32_t* keys, uint32_t* vals,
+                          uint32_t* digit_total, int bins) {
+  if (blockIdx.x == 0)
+    for (int t = threadIdx.x; t < bins; t += blockDim.x) digit_total[t] = 0;
+  const float inv_cs = (float)(1.0 / P.cs);
+  int oob = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int cx = cell_coord_fast((double)x[i], P.lo[0], P.cs, inv_cs, P.nx, oob);
+    const int cy = cell_coord_fast((double)y[i], P.lo[1], P.cs, inv_cs, P.ny, oob);
+    const int cz =
+        P.dim == 3 ? cell_coord_fast((double)z[i], P.lo[2], P.cs, inv_cs, P.nz, oob) : 0;
+    keys[i] = ((uint32_t)cz * (uint32_t)P.ny + (uint32_t)cy) * (uint32_t)P.nx + (uint32_t)cx;
+    vals[i] = (uint32_t)i;
+  }
+}
+
+template <class T>
+__global__ void k_ns_reorder(const uint32_t* __restrict__ perm, const T* __restrict__ x,
+                             const T* __restrict__ y, const T* __restrict__ z, int n, int dim,
+                             T* sx, T* sy, T* sz) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint32_t j = perm[k];
+    sx[k] = x[j];
+    sy[k] = y[j];
+    if (dim == 3) sz[k] = z[j];
+  }
+}
+
+// sigma_i = sum over the 3^d cells of W(r_ij), r < 2h, self included (the
+// density-summation pass), arithmetic in the position type.
+template <class T>
+__global__ void __launch_bounds__(256) k_ns_density(Params P, const uint32_t* __restrict__ keys,
+                                                    const uint32_t* __restrict__ cb,
+                                                    const T* __restrict__ x,
+                                                    const T* __restrict__ y,
+                                                    const T* __restrict__ z, int n,
+                                                    double* sigma) {
+  const T r2max = (T)P.r2max, inv_h = (T)(1.0 / P.h), cw = (T)P.walpha;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t key = keys[i];
+    const uint32_t r = key / (uint32_t)P.nx;
+    const int cx = (int)(key - r * (uint32_t)P.nx), cy = (int)(r % (uint32_t)P.ny),
+              cz = (int)(r / (uint32_t)P.ny);
+    const T xi = x[i], yi = y[i], zi = P.dim == 3 ? z[i] : T(0);
+    T sig = 0;
+    const int kz = P.dim == 3 ? 1 : 0;
+    for (int dz = -kz; dz <= kz; ++dz) {
+      const int zz = cz + dz;
+      if (zz < 0 || zz >= P.nz) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = cy + dy;
+        if (yy < 0 || yy >= P.ny) continue;
+        const uint32_t row = ((uint32_t)zz * (uint32_t)P.ny + (uint32_t)yy) * (uint32_t)P.nx;
+        const uint32_t c0 = row + (uint32_t)(cx > 0 ? cx - 1 : cx);
+        const uint32_t c1 = row + (uint32_t)(cx + 1 < P.nx ? cx + 1 : cx);
+        const uint32_t e = cb[c1 + 1];
+        for (uint32_t j = cb[c0]; j < e; ++j) {  // the row's 3 cells are contiguous
+          const T dx = xi - x[j], dyv = yi - y[j], dzv = P.dim == 3 ? zi - z[j] : T(0);
+          const T r2 = dx * dx + dyv * dyv + dzv * dzv;
+          if (r2 < r2max) {
+            const T q = sqrt(r2) * inv_h;
+            const T t = T(1) - T(0.5) * q;
+            const T t2 = t * t;
+            sig += cw * t2 * t2 * (T(2) * q + T(1));
+          }
+        }
+      }
+    }
+    sigma[i] = (double)sig;
+  }
+}
+
+int grid_of(int n, int block, int cap) {
+  int b = (n + block - 1) / block;
+  return b < 1 ? 1 : (b > cap ? cap : b);
+}
+
+}  // namespace
+
+extern "C" {
+
+int sph_nsearch_create(const sph_domain* domain, double h, int pos_precision,
+                       const sph_allocator* alloc, void* stream, sph_nsearch** out) {
+  if (!out || !domain || !(h > 0)) return SPH_E_INVALID;
+  *out = nullptr;
+  if (domain->dim != 2 && domain->dim != 3) return SPH_E_INVALID;
+  if (pos_precision != SPH_FP64 && pos_precision != SPH_MIXED) return SPH_E_INVALID;
+  if (alloc && (!alloc->alloc || !alloc->free)) return SPH_E_INVALID;
+  sph_nsearch* s = new sph_nsearch();
+  Params& P = s->P;
+  P.dim = domain->dim;
+  P.cs = 2.0 * h;
+  P.h = h;
+  P.r2max = 4.0 * h * h;
+  P.walpha = P.dim == 2 ? 7.0 / (4.0 * kPiN * h * h) : 21.0 / (16.0 * kPiN * h * h * h);
+  long long ncell = 1;
+  int nc[3] = {1, 1, 1};
+  for (int k = 0; k < P.dim; ++k) {
+    if (!(domain->hi[k] > domain->lo[k])) {
+      delete s;
+      return SPH_E_INVALID;
+    }
+    long long m = (long long)std::ceil((domain->hi[k] - domain->lo[k]) / P.cs);
+    nc[k] = (int)(m < 1 ? 1 : m);
+    ncell *= nc[k];
+    P.lo[k] = domain->lo[k];
+  }
+  if (ncell > 0xfffffffell) {
+    delete s;
+    return SPH_E_INVALID;
+  }
+  P.nx = nc[0];
+  P.ny = nc[1];
+  P.nz = nc[2];
+  P.ncell = (uint32_t)ncell;
+  s->fp32 = pos_precision == SPH_MIXED;
+  if (alloc) {
+    s->alloc = *alloc;
+    s->has_alloc = true;
+  }
+  s->user_stream = (cudaStream_t)stream;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->L.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+  for (int k = 0; k < 6 && e == cudaSuccess; ++k) e = cudaEventCreate(&s->ev[k]);
+  if (e == cudaSuccess) e = configure_sort_kernels();
+  if (e != cudaSuccess) {
+    sph_nsearch_destroy(s);
+    return SPH_E_CUDA;
+  }
+  s->L.block_stream = 256;
+  s->L.blocks_stream = s->L.sms * 8;
+  s->L.radix_bits = 8;
+  s->L.key_bits = bits_for(P.ncell);
+  s->L.radix_passes = radix_passes_for(s->L.key_bits, s->L.radix_bits);
+  s->cell_begin = (uint32_t*)ns_alloc(s, ((size_t)P.ncell + 1) * 4, s->fixed);
+  s->digit_total = (uint32_t*)ns_alloc(s, ((size_t)1 << kMaxRadixBits) * 4, s->fixed);
+  if (!s->cell_begin || !s->digit_total) {
+    sph_nsearch_destroy(s);
+    return SPH_E_OOM;
+  }
+  *out = s;
+  return SPH_OK;
+}
+
+int sph_nsearch_run(sph_nsearch* s, size_t n, const void* x, const void* y, const void* z,
+                    double* stage_ms) {
+  if (!s || n == 0 || n >= (1ull << 31) || !x || !y || (s->P.dim == 3 && !z))
+    return SPH_E_INVALID;
+  const size_t ts = s->fp32 ? 4 : 8;
+  if (n > s->cap) {
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return SPH_E_CUDA;
+    ns_free(s, s->blocks);
+    bool ok = true;
+    for (int p = 0; p < 2; ++p) {
+      s->keys[p] = (uint32_t*)ns_alloc(s, n * 4, s->blocks);
+      s->vals[p] = (uint32_t*)ns_alloc(s, n * 4, s->blocks);
+      ok &= s->keys[p] && s->vals[p];
+    }
+    for (int k = 0; k < 3; ++k) {
+      s->xs[k] = ns_alloc(s, n * ts, s->blocks);
+      ok &= s->xs[k] != nullptr;
+    }
+    s->sigma = (double*)ns_alloc(s, n * 8, s->blocks);
+    const size_t tiles = (n + kSortTile - 1) / kSortTile;
+    s->tile_hist = (uint32_t*)ns_alloc(s, tiles * ((size_t)1 << kMaxRadixBits) * 4, s->blocks);
+    ok &= s->sigma && s->tile_hist;
+    if (!ok) {
+      ns_free(s, s->blocks);
+      s->cap = 0;
+      return SPH_E_OOM;
+    }
+    s->cap = n;
+  }
+  s->n = n;
+  s->P.n = (int)n;
+  cudaStream_t st = s->stream;
+  if (cudaEventRecord(s->ev[0], s->user_stream) != cudaSuccess) return SPH_E_CUDA;
+  if (cudaStreamWaitEvent(st, s->ev[0], 0) != cudaSuccess) return SPH_E_CUDA;
+  const int ni = (int)n;
+  const int gs = grid_of(ni, 256, s->L.blocks_stream);
+  const int bins = 1 << s->L.radix_bits;
+  cudaEventRecord(s->ev[0], st);
+  if (s->fp32)
+    k_ns_keys<float><<<gs, 256, 0, st>>>(s->P, (const float*)x, (const float*)y, (const float*)z,
+                                         ni, s->keys[0], s->vals[0], s->digit_total, bins);
+  else
+    k_ns_keys<double><<<gs, 256, 0, st>>>(s->P, (const double*)x, (const double*)y,
+                                          (const double*)z, ni, s->keys[0], s->vals[0],
+                                          s->digit_total, bins);
+  cudaEventRecord(s->ev[1], st);
+  s->sorted = launch_radix_sort(s->L, s->keys, s->vals, ni, s->tile_hist, s->digit_total,
+                                nullptr, 0, st);
+  cudaEventRecord(s->ev[2], st);
+  const uint32_t* perm = s->vals[s->sorted];
+  const uint32_t* keys = s->keys[s->sorted];
+  if (s->fp32)
+    k_ns_reorder<float><<<gs, 256, 0, st>>>(perm, (const float*)x, (const float*)y,
+                                            (const float*)z, ni, s->P.dim, (float*)s->xs[0],
+                                            (float*)s->xs[1], (float*)s->xs[2]);
+  else
+    k_ns_reorder<double><<<gs, 256, 0, st>>>(perm, (const double*)x, (const double*)y,
+                                             (const double*)z, ni, s->P.dim, (double*)s->xs[0],
+                                             (double*)s->xs[1], (double*)s->xs[2]);
+  cudaEventRecord(s->ev[3], st);
+  launch_cell_offsets(keys, ni, s->P.ncell, s->cell_begin, nullptr, 0, 0, st);
+  cudaEventRecord(s->ev[4], st);
+  const int gd = grid_of(ni, 128, s->L.sms * 16);
+  if (s->fp32)
+    k_ns_density<float><<<gd, 128, 0, st>>>(s->P, keys, s->cell_begin, (const float*)s->xs[0],
+                                            (const float*)s->xs[1], (const float*)s->xs[2], ni,
+                                            s->sigma);
+  else
+    k_ns_density<double><<<gd, 128, 0, st>>>(s->P, keys, s->cell_begin,
+                                             (const double*)s->xs[0], (const double*)s->xs[1],
+                                             (const double*)s->xs[2], ni, s->sigma);
+  cudaEventRecord(s->ev[5], st);
+  if (cudaGetLastError() != cudaSuccess) return SPH_E_CUDA;
+  if (stage_ms) {
+    if (cudaEventSynchronize(s->ev[5]) != cudaSuccess) return SPH_E_CUDA;
+    for (int k = 0; k < 5; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, s->ev[k], s->ev[k + 1]);
+      stage_ms[k] = t;
+    }
+  }
+  if (cudaEventRecord(s->ev[0], st) != cudaSuccess) return SPH_E_CUDA;
+  return cudaStreamWaitEvent(s->user_stream, s->ev[0], 0) == cudaSuccess ? SPH_OK : SPH_E_CUDA;
+}
+
+int sph_nsearch_results(sph_nsearch* s, uint32_t* keys, uint32_t* perm, uint32_t* cell_begin,
+                        double* sigma) {
+  if (!s || !s->n) return SPH_E_STATE;
+  cudaStream_t st = s->stream;
+  const size_t n = s->n;
+  cudaError_t e = cudaSuccess;
+  if (keys) e = cudaMemcpyAsync(keys, s->keys[s->sorted], n * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && perm)
+    e = cudaMemcpyAsync(perm, s->vals[s->sorted], n * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && cell_begin)
+    e = cudaMemcpyAsync(cell_begin, s->cell_begin, ((size_t)s->P.ncell + 1) * 4,
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && sigma) e = cudaMemcpyAsync(sigma, s->sigma, n * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? SPH_OK : SPH_E_CUDA;
+}
+
+size_t sph_nsearch_cell_count(const sph_nsearch* s) { return s ? (size_t)s->P.ncell : 0; }
+
+void sph_nsearch_destroy(sph_nsearch* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  ns_free(s, s->blocks);
+  ns_free(s, s->fixed);
+  for (int k = 0; k < 6; ++k)
+    if (s->ev[k]) cudaEventDestroy(s->ev[k]);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+}  // extern "C"

@@ -357,21 +357,17 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// Reorder after the sort: gather the live state copy into the other copy and
-// write the loop records of buffer 0 (positions; velocity; old p; old rho).
+// Reorder after the sort: gather slot j of the live state copy into slot k of
+// the other copy and write the loop records of buffer 0 (positions; velocity;
+// old p; old rho) for binned cell key `key` (in the tank's grid).
 template <int D, class T>
-__global__ void k_reorder(Params P, DevBuffers B, int gated) {
+__device__ __forceinline__ void reorder_slot(const Params& P, const DevBuffers& B,
+                                             const Live<T>& S, const Live<T>& Dd, int k,
+                                             uint32_t j, uint32_t key) {
   using R = Rec<D, T>;
-  DevScalars* sc = B.sc;
-  if (gated && !sc->new_adv) return;
-  const int par = sc->par;
-  const Live<T> S = live<T>(B, par), Dd = live<T>(B, par ^ 1);
-  const uint32_t* __restrict__ perm = B.vals[B.sorted_buf];
-  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
   typename R::PV* recP = (typename R::PV*)B.recP[0];
   typename R::SV* recS = (typename R::SV*)B.recS[0];
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.n; k += gridDim.x * blockDim.x) {
-    const uint32_t j = perm[k];
+  {
     double x = S.x0[j], y = S.x1[j], z = D == 3 ? S.x2[j] : 0.0;
     double vx = S.v0[j], vy = S.v1[j], vz = D == 3 ? S.v2[j] : 0.0;
     double rho = S.rho[j];
@@ -387,7 +383,7 @@ __global__ void k_reorder(Params P, DevBuffers B, int gated) {
     Dd.drho[k] = S.drho[j];
     Dd.id[k] = S.id[j];
     T ox, oy, oz;
-    const Cell ck = decode(keys[k], P);
+    const Cell ck = decode(key, P);
     Local<T>::enc(P, ck, x, y, z, ox, oy, oz);
     T p = (T)(P.c0sq * (rho - P.rho0));
     recP[k] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p);
@@ -395,6 +391,18 @@ __global__ void k_reorder(Params P, DevBuffers B, int gated) {
     if constexpr (Local<T>::kLocal)
       ((typename FxRec<D>::V*)B.recI)[k] = fx_encode<D>(P, ck, x, y, z);
   }
+}
+
+template <int D, class T>
+__global__ void k_reorder(Params P, DevBuffers B, int gated) {
+  DevScalars* sc = B.sc;
+  if (gated && !sc->new_adv) return;
+  const int par = sc->par;
+  const Live<T> S = live<T>(B, par), Dd = live<T>(B, par ^ 1);
+  const uint32_t* __restrict__ perm = B.vals[B.sorted_buf];
+  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.n; k += gridDim.x * blockDim.x)
+    reorder_slot<D, T>(P, B, S, Dd, k, perm[k], keys[k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -460,8 +468,8 @@ __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffe
     }
     return;
   }
-  const uint32_t* __restrict__ cb = B.cell_begin;
-  const uint32_t* __restrict__ wcb = B.wall_cb;
+  const uint32_t* __restrict__ cb = B.cell_begin + P.cell_base;
+  const uint32_t* __restrict__ wcb = B.wall_cb + P.cell_base;
   for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
     const uint32_t e = cb[c + 1];
     for (uint32_t j = cb[c]; j < e; ++j) v((int)j, dx, dy, dz, false);
@@ -526,18 +534,21 @@ struct PairGeo {
 // 2h + skin.  The membership test runs in the pair type on the loop records;
 // its rounding is far below the skin, so the list is a superset of every
 // pair the later loops accept.
+//
+// Every loop below is a body over the slots i, i + stride, ... < end of one
+// tank (the whole fluid for one tank; one tile of a batch), ending with the
+// block-wide reductions; k_* are the one-tank kernels around them.
 template <int D, class T>
-__global__ void __launch_bounds__(256, kMinBlocks<T>) k_build_lists(Params P, DevBuffers B, KC<T> k,
-                                                     int gated) {
+__device__ __forceinline__ void build_lists_range(const Params& P, const DevBuffers& B,
+                                                  const KC<T>& k, DevScalars* sc, int i, int end,
+                                                  int stride) {
   using R = Rec<D, T>;
-  DevScalars* sc = B.sc;
-  if (!P.use_list || (gated && !sc->new_adv)) return;
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
-  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  const uint32_t* __restrict__ keys = B.binned;
   const double rl = (2.0 * P.h + sc->skin) * (1.0 + 1e-6);
   const T rl2 = (T)(rl * rl);
   int overflow = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+  for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
     const typename R::PV pi = recP[i];
     PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
@@ -552,6 +563,15 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_build_lists(Params P, De
     if (L.cnt > P.list_cap) overflow = 1;
   }
   if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(&sc->list_bad, 1);
+}
+
+template <int D, class T>
+__global__ void __launch_bounds__(256, kMinBlocks<T>) k_build_lists(Params P, DevBuffers B, KC<T> k,
+                                                                    int gated) {
+  DevScalars* sc = B.sc;
+  if (!P.use_list || (gated && !sc->new_adv)) return;
+  build_lists_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+                          gridDim.x * blockDim.x);
 }
 
 // Whether candidate (dx, dy, dz, wall, j) comes after particle i itself in the
@@ -569,17 +589,16 @@ __device__ __forceinline__ bool after_self(int dx, int dy, int dz, bool w, int j
 // sum (W(0)); the list holds the other particles in candidate order, so the
 // self term is added where direct search meets it.
 template <int D, class T>
-__global__ void __launch_bounds__(256, kMinBlocks<T>) k_density_summation(Params P, DevBuffers B, KC<T> k,
-                                                           int gated) {
+__device__ __forceinline__ void density_summation_range(const Params& P, const DevBuffers& B,
+                                                        const KC<T>& k, DevScalars* sc, int i,
+                                                        int end, int stride) {
   using R = Rec<D, T>;
-  DevScalars* sc = B.sc;
-  if (gated && !sc->new_adv) return;
   const bool use_list = list_ok(P, sc, 0.0);
   double* rho_live = sc->par ? B.rho[1] : B.rho[0];
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
   typename R::SV* recS = (typename R::SV*)B.recS[0];
-  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+  const uint32_t* __restrict__ keys = B.binned;
+  for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
     const typename R::PV pi = recP[i];
     PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
@@ -608,6 +627,15 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_density_summation(Params
   }
 }
 
+template <int D, class T>
+__global__ void __launch_bounds__(256, kMinBlocks<T>) k_density_summation(Params P, DevBuffers B,
+                                                                          KC<T> k, int gated) {
+  DevScalars* sc = B.sc;
+  if (gated && !sc->new_adv) return;
+  density_summation_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+                                gridDim.x * blockDim.x);
+}
+
 // Density summation of the mixed path: exact integer pair distances from the
 // fixed-point offsets of the rebuild and the kernel in double-float, so the
 // density (and through c0^2 the pressure) keeps double-precision accuracy
@@ -627,20 +655,19 @@ __device__ __forceinline__ unsigned long long fx_r2(const typename FxRec<D>::V& 
 }
 
 template <int D>
-__global__ void __launch_bounds__(256, 4) k_density_summation_fx(Params P, DevBuffers B,
-                                                              int gated) {
+__device__ __forceinline__ void density_summation_fx_range(const Params& P, const DevBuffers& B,
+                                                           DevScalars* sc, int i, int end,
+                                                           int stride) {
   using R = Rec<D, float>;
   using FV = typename FxRec<D>::V;
-  DevScalars* sc = B.sc;
-  if (gated && !sc->new_adv) return;
   const bool use_list = list_ok(P, sc, 0.0);
   double* rho_live = sc->par ? B.rho[1] : B.rho[0];
   const FV* __restrict__ rec = (const FV*)B.recI;
   const FV* __restrict__ wrec = (const FV*)B.wallI;
   typename R::SV* recS = (typename R::SV*)B.recS[0];
-  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  const uint32_t* __restrict__ keys = B.binned;
   const unsigned long long cut2 = 1ull << (2 * kFxShift);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+  for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
     const FV oi = rec[i];
     dfl sig = {0.0f, 0.0f};
@@ -666,23 +693,31 @@ __global__ void __launch_bounds__(256, 4) k_density_summation_fx(Params P, DevBu
   }
 }
 
+template <int D>
+__global__ void __launch_bounds__(256, 4) k_density_summation_fx(Params P, DevBuffers B,
+                                                                 int gated) {
+  DevScalars* sc = B.sc;
+  if (gated && !sc->new_adv) return;
+  density_summation_fx_range<D>(P, B, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+                                gridDim.x * blockDim.x);
+}
+
 // Viscous force: reads records P, S of buffer 0 (S carries the new rho);
 // writes a_prior = g + viscous acceleration.  Positions are those of the
 // rebuild, so the lists are always usable here (unless one overflowed).
 template <int D, class T>
-__global__ void __launch_bounds__(256, kMinBlocks<T>) k_viscous(Params P, DevBuffers B, KC<T> k, int gated) {
+__device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers& B, const KC<T>& k,
+                                              DevScalars* sc, int i, int end, int stride) {
   using R = Rec<D, T>;
-  DevScalars* sc = B.sc;
-  if (gated && !sc->new_adv) return;
   const bool use_list = list_ok(P, sc, 0.0);
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
   const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
-  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  const uint32_t* __restrict__ keys = B.binned;
   T* ap0 = (T*)B.aprior[0];
   T* ap1 = (T*)B.aprior[1];
   T* ap2 = (T*)B.aprior[2];
   const T wallV = (T)P.V;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+  for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
     const typename R::PV pi = recP[i];
     const typename R::SV si = recS[i];
@@ -717,19 +752,28 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_viscous(Params P, DevBuf
   }
 }
 
+template <int D, class T>
+__global__ void __launch_bounds__(256, kMinBlocks<T>) k_viscous(Params P, DevBuffers B, KC<T> k,
+                                                                int gated) {
+  DevScalars* sc = B.sc;
+  if (gated && !sc->new_adv) return;
+  viscous_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+                      gridDim.x * blockDim.x);
+}
+
 // First half of the acoustic step; writes records of buffer 0.
 template <int D, class T>
-__global__ void k_half1(Params P, DevBuffers B) {
+__device__ __forceinline__ void half1_range(const Params& P, const DevBuffers& B,
+                                            const DevScalars* sc, int i, int end, int stride) {
   using R = Rec<D, T>;
-  DevScalars* sc = B.sc;
   const int par = sc->par;
   const double dt = sc->dt_ac;
   const double hdt = 0.5 * dt;
-  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  const uint32_t* __restrict__ keys = B.binned;
   typename R::PV* recP = (typename R::PV*)B.recP[0];
   typename R::SV* recS = (typename R::SV*)B.recS[0];
   const Live<T> S = live<T>(B, par);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+  for (; i < end; i += stride) {
     double rho = S.rho[i] + hdt * (double)S.drho[i];
     double p = P.c0sq * (rho - P.rho0);
     double vx = S.v0[i], vy = S.v1[i], vz = D == 3 ? S.v2[i] : 0.0;
@@ -747,12 +791,18 @@ __global__ void k_half1(Params P, DevBuffers B) {
   }
 }
 
+template <int D, class T>
+__global__ void k_half1(Params P, DevBuffers B) {
+  half1_range<D, T>(P, B, B.sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+                    gridDim.x * blockDim.x);
+}
+
 // Riemann pressure relaxation + kick + the drift that opens the density stage.
 // Reads records of buffer 0, writes records of buffer 1.
 template <int D, class T>
-__global__ void __launch_bounds__(256, kMinBlocks<T>) k_pressure(Params P, DevBuffers B, KC<T> k) {
+__device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers& B, const KC<T>& k,
+                                               DevScalars* sc, int i, int end, int stride) {
   using R = Rec<D, T>;
-  DevScalars* sc = B.sc;
   const int par = sc->par;
   const double dt = sc->dt_ac;
   const double hdt = 0.5 * dt;
@@ -761,14 +811,14 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_pressure(Params P, DevBu
   const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
   typename R::PV* outP = (typename R::PV*)B.recP[1];
   typename R::SV* outS = (typename R::SV*)B.recS[1];
-  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  const uint32_t* __restrict__ keys = B.binned;
   const T* ap0 = (const T*)B.aprior[0];
   const T* ap1 = (const T*)B.aprior[1];
   const T* ap2 = (const T*)B.aprior[2];
   const Live<T> S = live<T>(B, par);
   double vmax2 = 0.0;
   int bad = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+  for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
     const typename R::PV pi = recP[i];
     const typename R::SV si = recS[i];
@@ -849,6 +899,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_pressure(Params P, DevBu
   }
   vmax2 = warp_max(vmax2);
   __shared__ double wm[32];
+  __syncthreads();  // the previous body call of this block has read wm
   if (threadIdx.x % 32 == 0) wm[threadIdx.x / 32] = vmax2;
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&sc->flags, kFlagNonFinite);
   if (threadIdx.x == 0) {
@@ -858,11 +909,18 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_pressure(Params P, DevBu
   }
 }
 
+template <int D, class T>
+__global__ void __launch_bounds__(256, kMinBlocks<T>) k_pressure(Params P, DevBuffers B, KC<T> k) {
+  pressure_range<D, T>(P, B, k, B.sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+                       gridDim.x * blockDim.x);
+}
+
 // Riemann density relaxation: reads records of buffer 1; drho and rho (state).
 template <int D, class T>
-__global__ void __launch_bounds__(256, kMinBlocks<T>) k_density_relax(Params P, DevBuffers B, KC<T> k) {
+__device__ __forceinline__ void density_relax_range(const Params& P, const DevBuffers& B,
+                                                    const KC<T>& k, DevScalars* sc, int i,
+                                                    int end, int stride) {
   using R = Rec<D, T>;
-  DevScalars* sc = B.sc;
   const int par = sc->par;
   const double hdt = 0.5 * sc->dt_ac;
   // positions after the second half-drift: bound grows by dt/2 * top speed after the kick
@@ -871,11 +929,10 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_density_relax(Params P, 
   const bool use_list = list_ok(P, sc, disp2);
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[1];
   const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[1];
-  const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  const uint32_t* __restrict__ keys = B.binned;
   const Live<T> S = live<T>(B, par);
   int bad = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) sc->vmax2_cur = sc->vmax2_next;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+  for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
     const typename R::PV pi = recP[i];
     const typename R::SV si = recS[i];
@@ -926,30 +983,49 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_density_relax(Params P, 
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&sc->flags, kFlagNonFinite);
 }
 
+// One tank: block 0 also publishes this step's velocity maximum for the next
+// step's schedule (a batch does that in its schedule kernel).
+template <int D, class T>
+__global__ void __launch_bounds__(256, kMinBlocks<T>) k_density_relax(Params P, DevBuffers B, KC<T> k) {
+  DevScalars* sc = B.sc;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc->vmax2_cur = sc->vmax2_next;
+  density_relax_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+                            gridDim.x * blockDim.x);
+}
+
 // Wall setup: gather sorted wall positions (double SoA for the parity kernel,
 // records for the loops) and ids from the unsorted staging copy.
+// Slot k of the sorted walls takes staging entry j, binned in cell `key` of
+// its tank's grid; (wx, wy, wz) is the double SoA of all sorted walls.
+template <int D, class T>
+__device__ __forceinline__ void wall_slot(const Params& P, const DevBuffers& B,
+                                          const double* __restrict__ ux,
+                                          const double* __restrict__ uy,
+                                          const double* __restrict__ uz, double* wx, double* wy,
+                                          double* wz, int k, uint32_t j, uint32_t key) {
+  using WR = WallRec<D, T>;
+  typename WR::WV* out = (typename WR::WV*)B.wallP;
+  double x = ux[j], y = uy[j], z = D == 3 ? uz[j] : 0.0;
+  wx[k] = x;
+  wy[k] = y;
+  if (D == 3) wz[k] = z;
+  B.wall_id[k] = j;
+  T ox, oy, oz;
+  const Cell ck = decode(key, P);
+  Local<T>::enc(P, ck, x, y, z, ox, oy, oz);
+  out[k] = WR::make(ox, oy, oz);
+  if constexpr (Local<T>::kLocal)
+    ((typename FxRec<D>::V*)B.wallI)[k] = fx_encode<D>(P, ck, x, y, z);
+}
+
 template <int D, class T>
 __global__ void k_wall_gather(Params P, DevBuffers B, const double* __restrict__ ux,
                               const double* __restrict__ uy, const double* __restrict__ uz,
                               double* wx, double* wy, double* wz) {
-  using WR = WallRec<D, T>;
   const uint32_t* perm = B.vals[B.sorted_buf];
   const uint32_t* keys = B.keys[B.sorted_buf];
-  typename WR::WV* out = (typename WR::WV*)B.wallP;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.nw; k += gridDim.x * blockDim.x) {
-    uint32_t j = perm[k];
-    double x = ux[j], y = uy[j], z = D == 3 ? uz[j] : 0.0;
-    wx[k] = x;
-    wy[k] = y;
-    if (D == 3) wz[k] = z;
-    B.wall_id[k] = j;
-    T ox, oy, oz;
-    const Cell ck = decode(keys[k], P);
-    Local<T>::enc(P, ck, x, y, z, ox, oy, oz);
-    out[k] = WR::make(ox, oy, oz);
-    if constexpr (Local<T>::kLocal)
-      ((typename FxRec<D>::V*)B.wallI)[k] = fx_encode<D>(P, ck, x, y, z);
-  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.nw; k += gridDim.x * blockDim.x)
+    wall_slot<D, T>(P, B, ux, uy, uz, wx, wy, wz, k, perm[k], keys[k]);
 }
 
 // ---------------------------------------------------------------------------

@@ -42,7 +42,14 @@ EXPORTS = ("sph_create", "sph_set_particles", "sph_step", "sph_get_fields", "sph
            "sph_count", "sph_cell_count", "sph_debug_neighbour_state",
            "sph_debug_neighbour_stats", "sph_set_option", "sph_synchronize", "sph_last_error",
            "sph_destroy", "sph_profile_stages", "sph_kernels_per_step",
-           "sph_cell_sort_noalloc")
+           "sph_cell_sort_noalloc", "sph_nsearch_create", "sph_nsearch_run",
+           "sph_nsearch_results", "sph_nsearch_cell_count", "sph_nsearch_destroy",
+           "sph_create_batch", "sph_batch_set_particles", "sph_batch_step",
+           "sph_batch_get_fields", "sph_batch_get_scalars", "sph_batch_debug_neighbour_state",
+           "sph_batch_count", "sph_batch_tank_count", "sph_batch_cell_count",
+           "sph_batch_profile_stages", "sph_batch_kernels_per_step", "sph_batch_set_option",
+           "sph_batch_synchronize", "sph_batch_last_error", "sph_batch_destroy")
+SPH_MAX_TANKS = 1024
 SPH_NOALLOC_MAX_PARTICLES = 1 << 20
 STAGE_NAMES = ("control", "keys", "sort", "reorder", "offsets", "density_sum", "viscous",
                "half1", "pressure", "density_relax")
@@ -55,6 +62,11 @@ class sph_domain(C.Structure):
 class sph_material(C.Structure):
     _fields_ = [("rho0", C.c_double), ("c0", C.c_double), ("mu", C.c_double),
                 ("U_ref", C.c_double)]
+
+
+class sph_tank(C.Structure):
+    _fields_ = [("domain", sph_domain), ("dp", C.c_double), ("h", C.c_double),
+                ("material", sph_material), ("gravity", C.c_double * 3)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -118,6 +130,48 @@ def load(path: str | None = None):
         L.sph_profile_stages.argtypes = [vp, i, vp, vp]
         L.sph_kernels_per_step.restype = C.c_long
         L.sph_kernels_per_step.argtypes = [vp]
+        L.sph_nsearch_create.restype = i
+        L.sph_nsearch_create.argtypes = [C.POINTER(sph_domain), d, i, C.POINTER(sph_allocator),
+                                         vp, C.POINTER(vp)]
+        L.sph_nsearch_run.restype = i
+        L.sph_nsearch_run.argtypes = [vp, sz, vp, vp, vp, vp]
+        L.sph_nsearch_results.restype = i
+        L.sph_nsearch_results.argtypes = [vp, vp, vp, vp, vp]
+        L.sph_nsearch_cell_count.restype = sz
+        L.sph_nsearch_cell_count.argtypes = [vp]
+        L.sph_nsearch_destroy.restype = None
+        L.sph_nsearch_destroy.argtypes = [vp]
+        L.sph_create_batch.restype = i
+        L.sph_create_batch.argtypes = [i, C.POINTER(sph_tank), i, C.POINTER(sph_allocator), vp,
+                                       C.POINTER(vp)]
+        L.sph_batch_set_particles.restype = i
+        L.sph_batch_set_particles.argtypes = [vp, i, vp, vp, vp, vp]
+        L.sph_batch_step.restype = i
+        L.sph_batch_step.argtypes = [vp, i]
+        L.sph_batch_get_fields.restype = i
+        L.sph_batch_get_fields.argtypes = [vp, C.c_uint, vp]
+        L.sph_batch_get_scalars.restype = i
+        L.sph_batch_get_scalars.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.sph_batch_debug_neighbour_state.restype = i
+        L.sph_batch_debug_neighbour_state.argtypes = [vp, i, vp, vp, vp]
+        L.sph_batch_count.restype = sz
+        L.sph_batch_count.argtypes = [vp, i]
+        L.sph_batch_tank_count.restype = i
+        L.sph_batch_tank_count.argtypes = [vp]
+        L.sph_batch_cell_count.restype = sz
+        L.sph_batch_cell_count.argtypes = [vp, i]
+        L.sph_batch_profile_stages.restype = i
+        L.sph_batch_profile_stages.argtypes = [vp, i, vp, vp]
+        L.sph_batch_kernels_per_step.restype = C.c_long
+        L.sph_batch_kernels_per_step.argtypes = [vp]
+        L.sph_batch_set_option.restype = i
+        L.sph_batch_set_option.argtypes = [vp, i, C.c_long]
+        L.sph_batch_synchronize.restype = i
+        L.sph_batch_synchronize.argtypes = [vp, d]
+        L.sph_batch_last_error.restype = C.c_char_p
+        L.sph_batch_last_error.argtypes = [vp]
+        L.sph_batch_destroy.restype = None
+        L.sph_batch_destroy.argtypes = [vp]
         L.sph_cell_sort_noalloc.restype = i
         L.sph_cell_sort_noalloc.argtypes = [C.POINTER(sph_domain), d, vp, vp, vp, sz, vp, vp, vp,
                                             vp]
@@ -132,6 +186,12 @@ def _ptr(a):
 def _check(ctx, rc):
     if rc != SPH_OK:
         msg = load().sph_last_error(ctx).decode() if ctx else ""
+        raise SphError(rc, msg)
+
+
+def _check_batch(b, rc):
+    if rc != SPH_OK:
+        msg = load().sph_batch_last_error(b).decode() if b else ""
         raise SphError(rc, msg)
 
 
@@ -234,6 +294,254 @@ def sph_profile_stages(ctx, n):
 
 def sph_kernels_per_step(ctx):
     return load().sph_kernels_per_step(ctx)
+
+
+class NeighbourSearch:
+    """sph_nsearch_*: keys, radix sort, reorder, offsets and one density pass
+    over device positions (torch tensors, float32 or float64)."""
+
+    STAGES = ("keys", "sort", "reorder", "offsets", "density")
+
+    def __init__(self, dim, lo, hi, h, fp32=False, torch_memory=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the SPH library has no CPU path")
+        L = load()
+        self._allocator = TorchAllocator() if torch_memory else None
+        dom = sph_domain(int(dim), (C.c_double * 3)(*list(lo) + [0.0] * (3 - len(lo))),
+                         (C.c_double * 3)(*list(hi) + [0.0] * (3 - len(hi))))
+        out = C.c_void_p()
+        rc = L.sph_nsearch_create(C.byref(dom), float(h), SPH_MIXED if fp32 else SPH_FP64,
+                                  C.byref(self._allocator.struct) if self._allocator else None,
+                                  C.c_void_p(torch.cuda.current_stream().cuda_stream) or None,
+                                  C.byref(out))
+        _check(None, rc)
+        self.ns = out.value
+        self.dim = int(dim)
+        self.n = 0
+
+    @property
+    def ncell(self):
+        return load().sph_nsearch_cell_count(self.ns)
+
+    def run(self, x, y, z=None, timed=True):
+        """x, y, z: contiguous device tensors of one dtype; returns the stage
+        times in ms (when timed)."""
+        ms = np.zeros(5, np.float64) if timed else None
+        self.n = int(x.numel())
+        zp = z.data_ptr() if z is not None else None
+        _check(None, load().sph_nsearch_run(self.ns, self.n, x.data_ptr(), y.data_ptr(), zp,
+                                             _ptr(ms)))
+        return dict(zip(self.STAGES, ms)) if timed else None
+
+    def results(self):
+        n = self.n
+        keys = np.empty(n, np.uint32); perm = np.empty(n, np.uint32)
+        cb = np.empty(self.ncell + 1, np.uint32); sig = np.empty(n, np.float64)
+        _check(None, load().sph_nsearch_results(self.ns, _ptr(keys), _ptr(perm), _ptr(cb),
+                                                 _ptr(sig)))
+        return dict(keys=keys, perm=perm, cell_begin=cb, sigma=sig)
+
+    def close(self):
+        if getattr(self, "ns", None):
+            load().sph_nsearch_destroy(self.ns)
+            self.ns = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- batches of independent tanks -----------------------------------------
+def _domain_of(dim, lo, hi):
+    return sph_domain(int(dim), (C.c_double * 3)(*list(lo) + [0.0] * (3 - len(lo))),
+                      (C.c_double * 3)(*list(hi) + [0.0] * (3 - len(hi))))
+
+
+def sph_create_batch(cases, precision=SPH_MIXED, allocator: sph_allocator | None = None,
+                     stream: int = 0):
+    """cases: sequence of objects with the attributes of ``cases.Case``."""
+    tanks = (sph_tank * len(cases))()
+    for t, c in enumerate(cases):
+        g = list(c.gravity) + [0.0] * (3 - len(c.gravity))
+        tanks[t] = sph_tank(_domain_of(c.dim, c.lo, c.hi), float(c.dp), float(c.h),
+                            sph_material(c.rho0, c.c0, c.mu, c.U_ref), (C.c_double * 3)(*g))
+    out = C.c_void_p()
+    rc = load().sph_create_batch(len(cases), tanks, int(precision),
+                                 C.byref(allocator) if allocator is not None else None,
+                                 C.c_void_p(stream) if stream else None, C.byref(out))
+    _check_batch(None, rc)
+    return out.value
+
+
+def sph_batch_set_particles(b, kind, counts, pos, vel=None, rho=None):
+    counts = np.ascontiguousarray(counts, dtype=np.uint64)
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    vel = None if vel is None else np.ascontiguousarray(vel, dtype=np.float64)
+    rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+    _check_batch(b, load().sph_batch_set_particles(b, int(kind), _ptr(counts), _ptr(pos),
+                                                   _ptr(vel), _ptr(rho)))
+
+
+def sph_batch_step(b, n):
+    _check_batch(b, load().sph_batch_step(b, int(n)))
+
+
+def sph_batch_get_fields(b, mask, n, dim):
+    comps = sum(dim if (mask & f) and f in _VECTOR_FIELDS else (1 if mask & f else 0)
+                for f in (1 << k for k in range(8)))
+    out = np.empty(n * comps, dtype=np.float64)
+    _check_batch(b, load().sph_batch_get_fields(b, int(mask), _ptr(out)))
+    res, off = {}, 0
+    for name, f in FIELD_NAMES.items():
+        if mask & f:
+            c = dim if f in _VECTOR_FIELDS else 1
+            a = out[off: off + n * c]
+            res[name] = a.reshape(n, dim) if c > 1 else a
+            off += n * c
+    return res
+
+
+def sph_batch_get_scalars(b, n_tanks):
+    t, dta, dtc = (np.empty(n_tanks, np.float64) for _ in range(3))
+    nac, nad = np.empty(n_tanks, np.int64), np.empty(n_tanks, np.int64)
+    _check_batch(b, load().sph_batch_get_scalars(b, _ptr(t), _ptr(dta), _ptr(dtc), _ptr(nac),
+                                                 _ptr(nad)))
+    return dict(t=t, dt_ad=dta, dt_ac=dtc, n_ac=nac, n_adv=nad)
+
+
+def sph_batch_debug_neighbour_state(b, tank, n, ncell):
+    keys = np.empty(n, np.uint32); ids = np.empty(n, np.uint32)
+    cb = np.empty(ncell + 1, np.uint32)
+    _check_batch(b, load().sph_batch_debug_neighbour_state(b, int(tank), _ptr(keys), _ptr(ids),
+                                                           _ptr(cb)))
+    return dict(keys=keys, ids=ids, cell_begin=cb)
+
+
+def sph_batch_count(b, kind=SPH_FLUID):
+    return load().sph_batch_count(b, int(kind))
+
+
+def sph_batch_tank_count(b):
+    return load().sph_batch_tank_count(b)
+
+
+def sph_batch_cell_count(b, tank):
+    return load().sph_batch_cell_count(b, int(tank))
+
+
+def sph_batch_profile_stages(b, n):
+    ms = np.zeros(len(STAGE_NAMES), np.float64)
+    reb = C.c_long()
+    _check_batch(b, load().sph_batch_profile_stages(b, int(n), _ptr(ms), C.byref(reb)))
+    return dict(zip(STAGE_NAMES, ms)), reb.value
+
+
+def sph_batch_kernels_per_step(b):
+    return load().sph_batch_kernels_per_step(b)
+
+
+def sph_batch_set_option(b, option, value):
+    _check_batch(b, load().sph_batch_set_option(b, int(option), int(value)))
+
+
+def sph_batch_synchronize(b, timeout_s=0.0):
+    _check_batch(b, load().sph_batch_synchronize(b, float(timeout_s)))
+
+
+def sph_batch_last_error(b):
+    return load().sph_batch_last_error(b).decode()
+
+
+def sph_batch_destroy(b):
+    load().sph_batch_destroy(b)
+
+
+class Batch:
+    """A batch of independent tanks (``cases``: a list of ``cases.Case``), each
+    with its own particles and schedule.  Fields come back tank-major."""
+
+    def __init__(self, cases, precision: str = "mixed", torch_memory: bool = True,
+                 stream: int | None = None):
+        self.cases = list(cases)
+        self.dim = self.cases[0].dim
+        self.precision = SPH_FP64 if precision == "fp64" else SPH_MIXED
+        self._allocator = None
+        if torch_memory:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("no CUDA device: the SPH library has no CPU path")
+            self._allocator = TorchAllocator()
+            if stream is None:
+                stream = torch.cuda.current_stream().cuda_stream
+        self.b = sph_create_batch(self.cases, self.precision,
+                                  self._allocator.struct if self._allocator else None,
+                                  stream or 0)
+        self.counts = np.array([c.n for c in self.cases], dtype=np.int64)
+        self.offsets = np.concatenate([[0], np.cumsum(self.counts)])
+        walls = [c.wall if c.wall is not None else np.zeros((0, self.dim)) for c in self.cases]
+        wcounts = [len(w) for w in walls]
+        if sum(wcounts):
+            sph_batch_set_particles(self.b, SPH_WALL, wcounts, np.concatenate(walls))
+        vel = None if all(c.vel is None for c in self.cases) else np.concatenate(
+            [c.vel if c.vel is not None else np.zeros_like(c.fluid) for c in self.cases])
+        rho = None if all(c.rho is None for c in self.cases) else np.concatenate(
+            [c.rho if c.rho is not None else np.full(c.n, c.rho0) for c in self.cases])
+        sph_batch_set_particles(self.b, SPH_FLUID, self.counts,
+                                np.concatenate([c.fluid for c in self.cases]), vel, rho)
+
+    @property
+    def tanks(self):
+        return len(self.cases)
+
+    @property
+    def n(self):
+        return sph_batch_count(self.b, SPH_FLUID)
+
+    @property
+    def nw(self):
+        return sph_batch_count(self.b, SPH_WALL)
+
+    def step(self, n: int = 1):
+        sph_batch_step(self.b, n)
+
+    def fields(self, *names):
+        mask = 0
+        for nm in names:
+            mask |= FIELD_NAMES[nm]
+        return sph_batch_get_fields(self.b, mask, self.n, self.dim)
+
+    def tank_fields(self, tank, *names):
+        f = self.fields(*names)
+        a, e = self.offsets[tank], self.offsets[tank + 1]
+        return {k: v[a:e] for k, v in f.items()}
+
+    def scalars(self):
+        return sph_batch_get_scalars(self.b, self.tanks)
+
+    def set_option(self, option, value):
+        sph_batch_set_option(self.b, option, value)
+
+    def neighbour_state(self, tank):
+        n = int(self.counts[tank]) if 0 <= tank < self.tanks else 0
+        return sph_batch_debug_neighbour_state(self.b, tank, n,
+                                               sph_batch_cell_count(self.b, tank))
+
+    def profile(self, n):
+        return sph_batch_profile_stages(self.b, n)
+
+    def close(self):
+        if getattr(self, "b", None):
+            sph_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sph_cell_sort_noalloc(dim, lo, hi, cell_size, x, y, z, n, keys_out, perm_out,

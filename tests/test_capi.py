@@ -82,3 +82,34 @@ def test_product_path_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "sph_oracle" not in text, f
+
+
+def test_batch_argument_validation_needs_no_device(lib):
+    """sph_create_batch rejects bad batches before any CUDA call."""
+    from paper_2603_11868_gb300 import sph
+
+    def tank(dim=2, dp=0.01, hi=1.0):
+        return sph.sph_tank(sph.sph_domain(dim, (C.c_double * 3)(0, 0, 0),
+                                           (C.c_double * 3)(hi, hi, hi)),
+                            dp, 1.3 * dp, sph.sph_material(1.0, 10.0, 0.0, 1.0),
+                            (C.c_double * 3)(0, -1, 0))
+
+    out = C.c_void_p()
+    two = (sph.sph_tank * 2)(tank(), tank())
+    assert lib.sph_create_batch(0, two, 1, None, None, C.byref(out)) == sph.SPH_E_INVALID
+    assert lib.sph_create_batch(sph.SPH_MAX_TANKS + 1, two, 1, None, None,
+                                C.byref(out)) == sph.SPH_E_INVALID
+    assert lib.sph_create_batch(2, None, 1, None, None, C.byref(out)) == sph.SPH_E_INVALID
+    assert lib.sph_create_batch(2, two, 5, None, None, C.byref(out)) == sph.SPH_E_INVALID
+    mixed_dims = (sph.sph_tank * 2)(tank(), tank(dim=3))
+    assert lib.sph_create_batch(2, mixed_dims, 1, None, None,
+                                C.byref(out)) == sph.SPH_E_INVALID
+    bad_dp = (sph.sph_tank * 2)(tank(), tank(dp=-0.01))
+    assert lib.sph_create_batch(2, bad_dp, 1, None, None, C.byref(out)) == sph.SPH_E_INVALID
+    # 2^31 or more cells over the batch (each tank alone is fine)
+    big = (sph.sph_tank * 40)(*[tank(dp=1e-4, hi=2.6) for _ in range(40)])  # 1e8 cells each
+    assert lib.sph_create_batch(40, big, 1, None, None, C.byref(out)) == sph.SPH_E_INVALID
+    assert out.value is None
+    assert lib.sph_batch_step(None, 1) == sph.SPH_E_INVALID
+    assert lib.sph_batch_tank_count(None) == 0
+    assert lib.sph_batch_destroy(None) is None

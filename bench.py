@@ -294,6 +294,7 @@ def run_batched(args):
     cs = batched_cases()
     b = sph.Batch(cs, precision=args.precision)
     n, nw = b.n, b.nw
+    tuning = None if args.no_autotune else b.autotune(args.substeps)
     for _ in range(args.warmup):
         b.step(args.substeps)
     torch.cuda.synchronize()
@@ -324,6 +325,7 @@ def run_batched(args):
                 "gpu_launches": kernels * args.substeps * args.steps,
                 "kernels_per_acoustic_step": kernels,
                 "tank_time_spread": [float(np.min(sc["t"])), float(np.max(sc["t"]))],
+                "tuning": tuning,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     return 0
@@ -346,6 +348,9 @@ def run_ours(args):
     case, wname = make_workload(args.workload, args.dp)
     solver = sph.Solver(case, precision=args.precision)
     n, nw = case.n, case.nw
+    # launch configuration picked by the library's autotuner (trials run from a
+    # snapshot that is restored afterwards, before the warm-up)
+    tuning = None if args.no_autotune else solver.autotune(args.substeps)
     mean_nb = None
     if rank == 0 and not args.quick:
         cf, cw, _ = solver.neighbour_stats()
@@ -467,7 +472,7 @@ def run_ours(args):
             "fp64_value": fp64,
             "speedup_vs_fp64": (value / ws / fp64) if fp64 else None,
             "gpips": (value * mean_nb * 2 / 1e9) if mean_nb else None,
-            "sim_time": sc["t"], "source_fingerprint": fp,
+            "sim_time": sc["t"], "source_fingerprint": fp, "tuning": tuning,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -491,6 +496,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="main number only")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch configuration")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

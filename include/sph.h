@@ -282,6 +282,27 @@ int sph_cell_sort_noalloc(const sph_domain* domain, double cell_size, const doub
                           const double* y, const double* z, size_t n, uint32_t* keys_out,
                           uint32_t* perm_out, uint32_t* cell_begin_out, void* stream);
 
+/* ---- Autotuner.  A launch configuration: threads per block of the
+ * neighbour loops (for a batch also the tile, the slots per work unit of its
+ * persistent launches), the digit width of the radix sort, and whether the
+ * loops walk neighbour lists.  None of them changes any result. */
+typedef struct {
+  int block;           /* SPH_OPT_BLOCK value */
+  int radix_bits;      /* SPH_OPT_RADIX_BITS value */
+  int neighbour_list;  /* SPH_OPT_NEIGHBOUR_LIST value */
+  int trials;          /* configurations timed by the search */
+  double ms_per_step;  /* measured device time per acoustic step */
+} sph_tuning;
+
+/* Picks the fastest configuration for this context as it stands: a
+ * coordinate search (block size, then radix width, then lists on / off) in
+ * which every candidate runs steps_per_trial acoustic steps (best of two
+ * runs, CUDA-graph replay) from a device snapshot of the whole context; the
+ * context is then restored to its state before the call and keeps the best
+ * configuration, which is written to *best.  Needs device memory for the
+ * snapshot (SPH_E_OOM otherwise); SPH_E_STATE before sph_set_particles. */
+int sph_autotune(sph_ctx* ctx, int steps_per_trial, sph_tuning* best);
+
 /* ---- Batches of independent tanks.  The paper runs one problem at a time;
  * a batch advances many small, independent problems together (each its own
  * domain, particles, material, gravity and its own dual-criteria schedule, so
@@ -352,6 +373,8 @@ long sph_batch_kernels_per_step(const sph_batch* b);
 int sph_batch_set_option(sph_batch* b, int option, long value);
 int sph_batch_synchronize(sph_batch* b, double timeout_s);
 const char* sph_batch_last_error(const sph_batch* b);
+/* The autotuner of sph_autotune for a batch. */
+int sph_batch_autotune(sph_batch* b, int steps_per_trial, sph_tuning* best);
 void sph_batch_destroy(sph_batch* b);
 
 /* Sets an sph_option; takes effect at the next sph_step. */

@@ -810,6 +810,7 @@ long sph_batch_kernels_per_step(const sph_batch* cb) {
 int sph_batch_set_option(sph_batch* b, int option, long value) {
   if (!b) return SPH_E_INVALID;
   int rc = SPH_OK;
+  const int old_list = b->P[0].use_list;
   switch (option) {
     case SPH_OPT_RECORD_DIAGNOSTICS:
       for (auto& p : b->P) p.diag = value ? 1 : 0;
@@ -841,6 +842,80 @@ int sph_batch_set_option(sph_batch* b, int option, long value) {
   drop_graph(b);
   rc = upload_tables(b);
   if (rc) return rc;
+  if (b->P[0].use_list && !old_list) {
+    // no list was built at the tanks' last rebuilds: direct search until the next ones
+    std::vector<DevScalars> hs;
+    rc = read_scalars(b, hs);
+    if (rc) return rc;
+    for (auto& h : hs) h.list_bad = 1;
+    CKB(cudaMemcpyAsync(b->A.tsc, hs.data(), sizeof(DevScalars) * b->T, cudaMemcpyHostToDevice,
+                        b->mem.stream));
+    CKB(cudaStreamSynchronize(b->mem.stream));
+  }
+  return leave(b);
+}
+
+int sph_batch_autotune(sph_batch* b, int steps_per_trial, sph_tuning* best) {
+  if (!b || !best || steps_per_trial < 1) return SPH_E_INVALID;
+  if (!b->fluid_set) return set_err(b, SPH_E_STATE, "no fluid particles set");
+  int rc = enter(b);
+  if (rc) return rc;
+  cudaStream_t s = b->mem.stream;
+  CKB(cudaStreamSynchronize(s));
+  Snapshot snap;
+  if (!snap.take(b->mem, {&b->fluid_blocks, &b->wall_blocks, &b->fixed_blocks}))
+    return set_err(b, SPH_E_OOM, "device allocation failed (autotuner snapshot)");
+  const LaunchCfg L0 = b->L;
+  const std::vector<Params> P0 = b->P;
+  const int sorted0 = b->B.sorted_buf;
+  const bool graph0 = b->use_graph;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  auto reset = [&]() -> int {
+    drop_graph(b);
+    if (snap.restore(s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+      return SPH_E_CUDA;
+    b->L = L0;
+    b->P = P0;
+    b->B.sorted_buf = sorted0;
+    b->use_graph = true;
+    return upload_tables(b);
+  };
+  auto apply = [&](const sph_tuning& t) -> int {
+    int r = sph_batch_set_option(b, SPH_OPT_BLOCK, t.block);
+    if (!r) r = sph_batch_set_option(b, SPH_OPT_RADIX_BITS, t.radix_bits);
+    if (!r) r = sph_batch_set_option(b, SPH_OPT_NEIGHBOUR_LIST, t.neighbour_list);
+    return r;
+  };
+  auto trial = [&](const sph_tuning& t) -> double {
+    double bestms = -1.0;
+    for (int rep = 0; rep < 2; ++rep) {
+      if (reset() || apply(t)) return -1.0;
+      if (cudaEventRecord(e0, b->user_stream) != cudaSuccess) return -1.0;
+      if (sph_batch_step(b, steps_per_trial)) return -1.0;
+      if (cudaEventRecord(e1, b->user_stream) != cudaSuccess) return -1.0;
+      if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.0;
+      const double per = ms / steps_per_trial;
+      if (bestms < 0 || per < bestms) bestms = per;
+    }
+    return bestms;
+  };
+  sph_tuning start{L0.block_loop, L0.radix_bits, P0[0].use_list, 0, 0.0};
+  sph_tuning found = start;
+  int search = e == cudaSuccess ? tune_search(start, trial, &found) : -1;
+  rc = reset();
+  if (!rc) rc = apply(search == 0 ? found : start);
+  b->use_graph = graph0;
+  snap.drop(b->mem);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (search != 0)
+    return rc ? rc : set_err(b, SPH_E_CUDA, "autotuner trial failed: " + b->err);
+  if (rc) return rc;
+  *best = found;
   return leave(b);
 }
 

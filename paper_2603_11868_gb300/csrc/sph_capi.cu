@@ -697,6 +697,8 @@ long sph_kernels_per_step(const sph_ctx* cc) {
 
 int sph_set_option(sph_ctx* c, int option, long value) {
   if (!c) return SPH_E_INVALID;
+  const int old_sorted = c->B.sorted_buf;
+  const int old_list = c->P.use_list;
   switch (option) {
     case SPH_OPT_RECORD_DIAGNOSTICS:
       c->P.diag = value ? 1 : 0;
@@ -723,7 +725,97 @@ int sph_set_option(sph_ctx* c, int option, long value) {
       return set_err(c, SPH_E_INVALID, "unknown option");
   }
   drop_graph(c);
+  if (c->fluid_set && (c->B.sorted_buf != old_sorted || (c->P.use_list && !old_list))) {
+    int rc = enter(c);
+    if (rc) return rc;
+    if (c->B.sorted_buf != old_sorted) {
+      // the binned keys (and the last permutation) move to the buffer the
+      // new pass count ends in
+      const size_t n = (size_t)c->P.n;
+      CK(cudaMemcpyAsync(c->B.keys[c->B.sorted_buf], c->B.keys[old_sorted], n * 4,
+                         cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaMemcpyAsync(c->B.vals[c->B.sorted_buf], c->B.vals[old_sorted], n * 4,
+                         cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (c->P.use_list && !old_list) {
+      // no list was built at the last rebuild: direct search until the next one
+      const int one = 1;
+      CK(cudaMemcpyAsync(&c->B.sc->list_bad, &one, sizeof(int), cudaMemcpyHostToDevice,
+                         c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
+    return leave(c);
+  }
   return SPH_OK;
+}
+
+int sph_autotune(sph_ctx* c, int steps_per_trial, sph_tuning* best) {
+  if (!c || !best || steps_per_trial < 1) return SPH_E_INVALID;
+  if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
+  int rc = enter(c);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  DevMem mem;
+  mem.alloc = c->alloc;
+  mem.has_alloc = c->has_alloc;
+  mem.stream = c->stream;
+  Snapshot snap;
+  if (!snap.take(mem, {&c->fluid_blocks, &c->wall_blocks, &c->fixed_blocks}))
+    return set_err(c, SPH_E_OOM, "device allocation failed (autotuner snapshot)");
+  const LaunchCfg L0 = c->L;
+  const Params P0 = c->P;
+  const int sorted0 = c->B.sorted_buf;
+  const bool graph0 = c->use_graph;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  // back to the state and configuration of the call
+  auto reset = [&]() -> int {
+    drop_graph(c);
+    if (snap.restore(c->stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return SPH_E_CUDA;
+    c->L = L0;
+    c->P = P0;
+    c->B.sorted_buf = sorted0;
+    c->use_graph = true;
+    return SPH_OK;
+  };
+  auto apply = [&](const sph_tuning& t) -> int {
+    int r = sph_set_option(c, SPH_OPT_BLOCK, t.block);
+    if (!r) r = sph_set_option(c, SPH_OPT_RADIX_BITS, t.radix_bits);
+    if (!r) r = sph_set_option(c, SPH_OPT_NEIGHBOUR_LIST, t.neighbour_list);
+    return r;
+  };
+  auto trial = [&](const sph_tuning& t) -> double {
+    double bestms = -1.0;
+    for (int rep = 0; rep < 2; ++rep) {
+      if (reset() || apply(t)) return -1.0;
+      if (cudaEventRecord(e0, c->user_stream) != cudaSuccess) return -1.0;
+      if (sph_step(c, steps_per_trial)) return -1.0;
+      if (cudaEventRecord(e1, c->user_stream) != cudaSuccess) return -1.0;
+      if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.0;
+      const double per = ms / steps_per_trial;
+      if (bestms < 0 || per < bestms) bestms = per;
+    }
+    return bestms;
+  };
+  sph_tuning start{L0.block_loop, L0.radix_bits, P0.use_list, 0, 0.0};
+  sph_tuning found = start;
+  int search = e == cudaSuccess ? tune_search(start, trial, &found) : -1;
+  // leave the context as it was, with the chosen configuration
+  rc = reset();
+  if (!rc) rc = apply(search == 0 ? found : start);
+  c->use_graph = graph0;
+  snap.drop(mem);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (search != 0)
+    return rc ? rc : set_err(c, SPH_E_CUDA, "autotuner trial failed: " + c->err);
+  if (rc) return rc;
+  *best = found;
+  return leave(c);
 }
 
 const char* sph_last_error(const sph_ctx* c) { return c ? c->err.c_str() : "null context"; }

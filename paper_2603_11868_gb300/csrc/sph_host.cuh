@@ -47,6 +47,95 @@ struct DevMem {
   }
 };
 
+// Device copy of every allocation of an object, so that trial runs (the
+// autotuner) leave the object exactly as they found it.
+struct Snapshot {
+  std::vector<Block> src, saved;
+
+  bool take(const DevMem& mem, const std::vector<const std::vector<Block>*>& lists) {
+    for (auto* l : lists)
+      for (auto& b : *l) src.push_back(b);
+    for (auto& b : src)
+      if (!mem.get(b.bytes, saved)) {
+        drop(mem);
+        return false;
+      }
+    return copy(true, mem.stream) == cudaSuccess;
+  }
+  cudaError_t copy(bool save, cudaStream_t s) const {
+    for (size_t k = 0; k < src.size(); ++k) {
+      cudaError_t e = save ? cudaMemcpyAsync(saved[k].p, src[k].p, src[k].bytes,
+                                             cudaMemcpyDeviceToDevice, s)
+                           : cudaMemcpyAsync(src[k].p, saved[k].p, src[k].bytes,
+                                             cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  cudaError_t restore(cudaStream_t s) const { return copy(false, s); }
+  void drop(const DevMem& mem) {
+    mem.release(saved);
+    src.clear();
+  }
+};
+
+// Coordinate search of the launch configuration: first the block size (the
+// tile of a batch), then the radix width of the sort, then neighbour lists on
+// or off, each time keeping the fastest.  trial(cfg) restores the object,
+// applies cfg and returns its time per acoustic step in ms (< 0: error, which
+// ends the search).  Every configuration computes the same results; only the
+// time differs.
+template <class Trial>
+int tune_search(sph_tuning start, Trial trial, sph_tuning* best) {
+  sph_tuning b = start;
+  int trials = 0;
+  double ms = trial(b);
+  ++trials;
+  if (ms < 0) return -1;
+  b.ms_per_step = ms;
+  const int blocks[] = {64, 96, 128, 192, 256};
+  const int block0 = b.block;
+  for (int v : blocks) {
+    if (v == block0) continue;
+    sph_tuning c = b;
+    c.block = v;
+    const double t = trial(c);
+    ++trials;
+    if (t < 0) return -1;
+    if (t < b.ms_per_step) {
+      b = c;
+      b.ms_per_step = t;
+    }
+  }
+  const int radix0 = b.radix_bits;
+  for (int v = 5; v <= 11; ++v) {
+    if (v == radix0) continue;
+    sph_tuning c = b;
+    c.radix_bits = v;
+    const double t = trial(c);
+    ++trials;
+    if (t < 0) return -1;
+    if (t < b.ms_per_step) {
+      b = c;
+      b.ms_per_step = t;
+    }
+  }
+  {
+    sph_tuning c = b;
+    c.neighbour_list = !b.neighbour_list;
+    const double t = trial(c);
+    ++trials;
+    if (t < 0) return -1;
+    if (t < b.ms_per_step) {
+      b = c;
+      b.ms_per_step = t;
+    }
+  }
+  b.trials = trials;
+  *best = b;
+  return 0;
+}
+
 constexpr double kPiHost = 3.14159265358979323846;
 
 inline double wendland_alpha(int dim, double h) {

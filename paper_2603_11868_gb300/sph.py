@@ -48,7 +48,8 @@ EXPORTS = ("sph_create", "sph_set_particles", "sph_step", "sph_get_fields", "sph
            "sph_batch_get_fields", "sph_batch_get_scalars", "sph_batch_debug_neighbour_state",
            "sph_batch_count", "sph_batch_tank_count", "sph_batch_cell_count",
            "sph_batch_profile_stages", "sph_batch_kernels_per_step", "sph_batch_set_option",
-           "sph_batch_synchronize", "sph_batch_last_error", "sph_batch_destroy")
+           "sph_batch_synchronize", "sph_batch_last_error", "sph_batch_destroy",
+           "sph_autotune", "sph_batch_autotune")
 SPH_MAX_TANKS = 1024
 SPH_NOALLOC_MAX_PARTICLES = 1 << 20
 STAGE_NAMES = ("control", "keys", "sort", "reorder", "offsets", "density_sum", "viscous",
@@ -67,6 +68,14 @@ class sph_material(C.Structure):
 class sph_tank(C.Structure):
     _fields_ = [("domain", sph_domain), ("dp", C.c_double), ("h", C.c_double),
                 ("material", sph_material), ("gravity", C.c_double * 3)]
+
+
+class sph_tuning(C.Structure):
+    _fields_ = [("block", C.c_int), ("radix_bits", C.c_int), ("neighbour_list", C.c_int),
+                ("trials", C.c_int), ("ms_per_step", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -172,6 +181,10 @@ def load(path: str | None = None):
         L.sph_batch_last_error.argtypes = [vp]
         L.sph_batch_destroy.restype = None
         L.sph_batch_destroy.argtypes = [vp]
+        L.sph_autotune.restype = i
+        L.sph_autotune.argtypes = [vp, i, C.POINTER(sph_tuning)]
+        L.sph_batch_autotune.restype = i
+        L.sph_batch_autotune.argtypes = [vp, i, C.POINTER(sph_tuning)]
         L.sph_cell_sort_noalloc.restype = i
         L.sph_cell_sort_noalloc.argtypes = [C.POINTER(sph_domain), d, vp, vp, vp, sz, vp, vp, vp,
                                             vp]
@@ -294,6 +307,12 @@ def sph_profile_stages(ctx, n):
 
 def sph_kernels_per_step(ctx):
     return load().sph_kernels_per_step(ctx)
+
+
+def sph_autotune(ctx, steps_per_trial=10):
+    t = sph_tuning()
+    _check(ctx, load().sph_autotune(ctx, int(steps_per_trial), C.byref(t)))
+    return t.as_dict()
 
 
 class NeighbourSearch:
@@ -459,6 +478,12 @@ def sph_batch_destroy(b):
     load().sph_batch_destroy(b)
 
 
+def sph_batch_autotune(b, steps_per_trial=10):
+    t = sph_tuning()
+    _check_batch(b, load().sph_batch_autotune(b, int(steps_per_trial), C.byref(t)))
+    return t.as_dict()
+
+
 class Batch:
     """A batch of independent tanks (``cases``: a list of ``cases.Case``), each
     with its own particles and schedule.  Fields come back tank-major."""
@@ -531,6 +556,9 @@ class Batch:
 
     def profile(self, n):
         return sph_batch_profile_stages(self.b, n)
+
+    def autotune(self, steps_per_trial=10):
+        return sph_batch_autotune(self.b, steps_per_trial)
 
     def close(self):
         if getattr(self, "b", None):
@@ -636,6 +664,9 @@ class Solver:
 
     def neighbour_state(self):
         return sph_debug_neighbour_state(self.ctx, self.n, self.ncell)
+
+    def autotune(self, steps_per_trial=10):
+        return sph_autotune(self.ctx, steps_per_trial)
 
     def neighbour_stats(self):
         return sph_debug_neighbour_stats(self.ctx, self.n)

@@ -66,10 +66,18 @@ def source_fingerprint() -> str:
     return h.hexdigest()[:12]
 
 
-# dram read + write bytes per launch from an ncu capture of the named kernel,
-# keyed by the fingerprint of the kernel sources it was taken on (see
-# profiles/); a stale fingerprint reports traffic as null.
-NCU_TRAFFIC = {}
+# dram read + write bytes of one launch of the named stage from an ncu capture,
+# per fluid particle (the capture ran a smaller case of the same geometry; its
+# traffic scales with the particle count), keyed by the fingerprint of the
+# kernel sources it was taken on (profiles/k_pressure_dam_break_3d_643k_mixed.md);
+# a stale fingerprint reports traffic as null.
+NCU_TRAFFIC = {
+    ("pressure", "c16176593f19"): (270899456 + 9280000) / 643200,
+}
+# neighbour-list bytes per list entry and launch of the stages that use the
+# lists: the loops read each entry once; the rebuild stage writes and then
+# reads them once (list build + density summation)
+LIST_ENTRY_BYTES = {"pressure": 4, "density_relax": 4, "viscous": 4, "density_sum": 8}
 
 
 def measured_peaks() -> dict:
@@ -133,6 +141,47 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def apply_tuning(obj, args):
+    """--tuning B,R,L sets block size, radix bits and lists directly (for
+    profiling runs); otherwise the autotuner picks them (unless disabled)."""
+    from paper_2603_11868_gb300 import sph
+    if args.tuning:
+        blk, radix, lists = (int(v) for v in args.tuning.split(","))
+        obj.set_option(sph.SPH_OPT_BLOCK, blk)
+        obj.set_option(sph.SPH_OPT_RADIX_BITS, radix)
+        obj.set_option(sph.SPH_OPT_NEIGHBOUR_LIST, lists)
+        return {"block": blk, "radix_bits": radix, "neighbour_list": lists, "trials": 0}
+    return None if args.no_autotune else obj.autotune(args.substeps)
+
+
+def replica_value(el: float, units: float, dist, device) -> tuple[float, float]:
+    """Whole-job throughput of independent replicas: the units every rank
+    processed, summed, over the slowest rank's time (no collective on the data
+    path; these two reductions only aggregate the measurement)."""
+    if dist is None:
+        return units / el, el
+    import torch
+    t = torch.tensor([el], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
+def shard_tanks(sizes, ranks: int) -> list[list[int]]:
+    """Tanks of a batch dealt to ranks, largest first, each to the rank with
+    the fewest particles so far; each rank's tanks in ascending order."""
+    sizes = np.asarray(sizes, dtype=np.float64)
+    order = np.argsort(-sizes, kind="stable")
+    load = np.zeros(ranks)
+    out: list[list[int]] = [[] for _ in range(ranks)]
+    for t in order:
+        r = int(np.argmin(load))
+        out[r].append(int(t))
+        load[r] += sizes[t]
+    return [sorted(o) for o in out]
 
 
 def make_workload(name: str, dp: float | None = None):
@@ -289,19 +338,28 @@ def run_batched(args):
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     sph.load()
     cs = batched_cases()
+    n_all = sum(c.n for c in cs)
+    if ws > 1:  # independent tanks: each rank advances its share, no collective
+        cs = [cs[t] for t in shard_tanks([c.n for c in cs], ws)[rank]]
     b = sph.Batch(cs, precision=args.precision)
     n, nw = b.n, b.nw
-    tuning = None if args.no_autotune else b.autotune(args.substeps)
+    tuning = apply_tuning(b, args)
     for _ in range(args.warmup):
         b.step(args.substeps)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     with ClockSampler(local) as clk:
         el = time_steps(b, args.steps, args.substeps, torch)
     sph.sph_batch_synchronize(b.b, 60.0)
-    value = n * args.steps * args.substeps / el
+    value, el = replica_value(el, n * args.steps * args.substeps, dist, "cuda")
     stages, rebuilds = b.profile(2 * args.substeps)
     per_step = {k: v / (2 * args.substeps) for k, v in stages.items()}
     kernels = sph.sph_batch_kernels_per_step(b.b)
@@ -316,8 +374,10 @@ def run_batched(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32 pair / f64 state" if args.precision == "mixed" else "f64",
                 "data": "synthetic",
-                "config": {"workload": f"{len(cs)} tanks, {n} fluid + {nw} wall particles, "
+                "config": {"workload": f"256 tanks, {n_all} fluid particles over {ws} rank(s) "
+                                       f"(rank 0: {len(cs)} tanks, {n} fluid + {nw} wall), "
                                        f"dp=0.01, {args.substeps} acoustic steps per bench step",
+                           "parallelism": f"tanks sharded over {ws} rank(s)",
                            "l2": "state larger than L2 (no flush)"},
                 "acoustic_steps_per_bench_step": args.substeps,
                 "stage_ms_per_acoustic_step": {k: round(v, 4) for k, v in per_step.items()},
@@ -328,6 +388,9 @@ def run_batched(args):
                 "tuning": tuning,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
     return 0
 
 
@@ -350,7 +413,7 @@ def run_ours(args):
     n, nw = case.n, case.nw
     # launch configuration picked by the library's autotuner (trials run from a
     # snapshot that is restored afterwards, before the warm-up)
-    tuning = None if args.no_autotune else solver.autotune(args.substeps)
+    tuning = apply_tuning(solver, args)
     mean_nb = None
     if rank == 0 and not args.quick:
         cf, cw, _ = solver.neighbour_stats()
@@ -362,13 +425,10 @@ def run_ours(args):
         dist.barrier()
     with ClockSampler(local) as clk:
         el = time_steps(solver, args.steps, args.substeps, torch)
-    if dist:
-        t = torch.tensor([el], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el = float(t.item())
-        dist.barrier()
     acoustic = args.steps * args.substeps
-    value = ws * n * acoustic / el
+    value, el = replica_value(el, n * acoustic, dist, "cuda")
+    if dist:
+        dist.barrier()
     clocks = clk.summary()
     kps = solver.kernels_per_step()
     sc = solver.scalars()
@@ -383,12 +443,15 @@ def run_ours(args):
     dom = max(ms, key=lambda k: ms[k])
     peaks = measured_peaks()
     fp = source_fingerprint()
+    list_entries = float(solver.list_lengths().astype(np.float64).sum())
     dom_bytes = BYTES_PER_PARTICLE_MIXED_3D.get(dom, 0) * n
     if dom in ("density_sum", "viscous", "pressure", "density_relax"):
         dom_bytes += WALL_RECORD_BYTES_3D * nw
+    dom_bytes += LIST_ENTRY_BYTES.get(dom, 0) * list_entries
     avg_s = ms[dom] / 1e3 / max(1, launches[dom])
     achieved = dom_bytes / avg_s / 1e9
-    traffic = NCU_TRAFFIC.get((dom, fp))
+    per_particle = NCU_TRAFFIC.get((dom, fp))
+    traffic = per_particle * n if per_particle is not None and args.precision == "mixed" else None
 
     # FP64 path on the same workload for the speed-up (fewer steps)
     fp64 = None
@@ -461,7 +524,8 @@ def run_ours(args):
                          "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                          "peak_source": peaks["source"],
-                         "bytes_per_launch": dom_bytes, "avg_launch_ms": avg_s * 1e3},
+                         "bytes_per_launch": dom_bytes, "avg_launch_ms": avg_s * 1e3,
+                         "list_entries_per_particle": list_entries / n},
             "stage_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
             "rebuilds_per_step": rebuilds / prof_steps,
             "clocks": clocks,
@@ -498,6 +562,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="main number only")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch configuration")
+    ap.add_argument("--tuning", default=None,
+                    help="block,radix_bits,lists: fixed launch configuration, no autotuner")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -185,6 +185,11 @@ int sph_debug_neighbour_state(sph_ctx* ctx, uint32_t* keys, uint32_t* perm, uint
 int sph_debug_neighbour_stats(sph_ctx* ctx, uint32_t* cnt_fluid, uint32_t* cnt_wall,
                               uint64_t* hash);
 
+/* Length of every fluid particle's neighbour list (storage order, n entries)
+ * as built at the last rebuild: the candidates closer than 2h + skin.  All 0
+ * when lists are off. */
+int sph_debug_list_lengths(sph_ctx* ctx, uint32_t* lengths);
+
 /* Stages of one acoustic step, in launch order (sph_profile_stages). */
 enum sph_stage {
   SPH_STAGE_CONTROL = 0,        /* schedule scalars (one thread)                   */

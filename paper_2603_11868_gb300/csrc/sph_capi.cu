@@ -638,6 +638,21 @@ int sph_debug_neighbour_stats(sph_ctx* c, uint32_t* cnt_fluid, uint32_t* cnt_wal
   return sync_status(c);
 }
 
+int sph_debug_list_lengths(sph_ctx* c, uint32_t* lengths) {
+  if (!c || !lengths) return SPH_E_INVALID;
+  if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
+  int rc = enter(c);
+  if (rc) return rc;
+  const size_t n = c->P.n;
+  if (c->P.use_list)
+    CK(cudaMemcpyAsync(lengths, c->B.nl_cnt, n * 4, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (!c->P.use_list) memset(lengths, 0, n * 4);
+  rc = leave(c);
+  if (rc) return rc;
+  return sync_status(c);
+}
+
 int sph_profile_stages(sph_ctx* c, int n, double* ms, long* rebuilds) {
   if (!c || !ms || n < 0) return SPH_E_INVALID;
   if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");

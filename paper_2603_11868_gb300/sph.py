@@ -49,7 +49,7 @@ EXPORTS = ("sph_create", "sph_set_particles", "sph_step", "sph_get_fields", "sph
            "sph_batch_count", "sph_batch_tank_count", "sph_batch_cell_count",
            "sph_batch_profile_stages", "sph_batch_kernels_per_step", "sph_batch_set_option",
            "sph_batch_synchronize", "sph_batch_last_error", "sph_batch_destroy",
-           "sph_autotune", "sph_batch_autotune")
+           "sph_autotune", "sph_batch_autotune", "sph_debug_list_lengths")
 SPH_MAX_TANKS = 1024
 SPH_NOALLOC_MAX_PARTICLES = 1 << 20
 STAGE_NAMES = ("control", "keys", "sort", "reorder", "offsets", "density_sum", "viscous",
@@ -181,6 +181,8 @@ def load(path: str | None = None):
         L.sph_batch_last_error.argtypes = [vp]
         L.sph_batch_destroy.restype = None
         L.sph_batch_destroy.argtypes = [vp]
+        L.sph_debug_list_lengths.restype = i
+        L.sph_debug_list_lengths.argtypes = [vp, vp]
         L.sph_autotune.restype = i
         L.sph_autotune.argtypes = [vp, i, C.POINTER(sph_tuning)]
         L.sph_batch_autotune.restype = i
@@ -280,6 +282,12 @@ def sph_debug_neighbour_stats(ctx, n):
     cf = np.empty(n, np.uint32); cw = np.empty(n, np.uint32); hs = np.empty(n, np.uint64)
     _check(ctx, load().sph_debug_neighbour_stats(ctx, _ptr(cf), _ptr(cw), _ptr(hs)))
     return cf, cw, hs
+
+
+def sph_debug_list_lengths(ctx, n):
+    out = np.empty(n, np.uint32)
+    _check(ctx, load().sph_debug_list_lengths(ctx, _ptr(out)))
+    return out
 
 
 def sph_set_option(ctx, option, value):
@@ -667,6 +675,9 @@ class Solver:
 
     def autotune(self, steps_per_trial=10):
         return sph_autotune(self.ctx, steps_per_trial)
+
+    def list_lengths(self):
+        return sph_debug_list_lengths(self.ctx, self.n)
 
     def neighbour_stats(self):
         return sph_debug_neighbour_stats(self.ctx, self.n)

@@ -19,6 +19,12 @@ Workloads:
   uniform_cube      N particles uniform in the unit cube, h chosen for a mean
                     of `neighbours` particles within 2h.
   batched_tanks     many independent 2D dam-break tanks of log-uniform size.
+  dam_break_obstacle_3d
+                    3D dam break whose surge hits a box obstacle on the floor
+                    (the kind of test the paper's second workload is): tank
+                    3.0 x 1.0 x 1.0, column 1.2 x 1.0 x 0.5 at the far end, a solid
+                    0.2 x 0.4 x 0.2 box of wall particles at x = 0.6..0.8,
+                    centred across the tank.
 """
 from __future__ import annotations
 
@@ -210,3 +216,30 @@ def batched_tank(n_target: float, dp: float = 0.01, seed: int = 0, layers: int =
                         column=(Wc, H), rho0=1.0, g=1.0, c0=c0)
     case.name = "batched_tank"
     return case
+
+
+def box_particles(dim: int, lo, size, dp: float) -> np.ndarray:
+    """Lattice points (i + 1/2) dp filling a solid box from corner `lo`."""
+    return fluid_block(dim, lo, size, dp, 0.0, None)
+
+
+def dam_break_obstacle_3d(dp: float = 0.02, seed: int = 7, jitter: float = 0.01,
+                          layers: int = 3, tank=(3.0, 1.0, 1.0), column=(1.2, 1.0, 0.5),
+                          box=(0.2, 0.4, 0.2), box_x: float = 0.6, rho0: float = 1000.0,
+                          g: float = 9.81, mu: float = 1.0e-3) -> Case:
+    """Open-top 3D tank; the column fills the far end (x from tank_x -
+    column_x), the surge runs towards x = 0 and meets a solid box of wall
+    particles standing on the floor.  c0 = 10 sqrt(2 g H)."""
+    rng = np.random.default_rng(seed)
+    x0 = tank[0] - column[0]
+    fluid = fluid_block(3, (x0, 0.0, 0.0), column, dp, jitter, rng)
+    walls = tank_walls(3, tank, dp, layers, open_top=True)
+    obstacle = box_particles(3, (box_x, 0.5 * (tank[1] - box[1]), 0.0), box, dp)
+    wall = np.ascontiguousarray(np.concatenate([walls, obstacle]))
+    lo, hi = _domain(3, tank, dp, layers, 0.25 * tank[2])
+    H = column[2]
+    c0 = 10.0 * math.sqrt(2.0 * g * H)
+    return Case("dam_break_obstacle_3d", 3, dp, 1.3 * dp, rho0, c0, mu, c0 / 10.0,
+                (0.0, 0.0, -g), lo, hi, fluid, wall,
+                meta=dict(tank=tank, column=column, box=box, box_x=box_x, layers=layers,
+                          seed=seed, n_obstacle=len(obstacle)))

@@ -229,7 +229,8 @@ int alloc_fluid(sph_batch* b, size_t n) {
   B.recI = b->precision == SPH_MIXED ? Al(nn * (d == 3 ? 16 : 8)) : nullptr;
   ok &= b->precision != SPH_MIXED || B.recI;
   const size_t warps = (nn + 31) / 32 + (size_t)b->T;  // per-warp list rows
-  B.nl = (uint32_t*)Al(warps * (size_t)b->P[0].list_cap * 32 * 4);
+  // two extra rows of 32 entries: the list walk prefetches two entries ahead
+  B.nl = (uint32_t*)Al((warps * (size_t)b->P[0].list_cap + 2) * 32 * 4);
   B.nl_cnt = (uint32_t*)Al(nn * 4);
   b->A.bkey = (uint32_t*)Al(nn * 4);
   ok &= B.nl && B.nl_cnt && b->A.bkey;

@@ -226,7 +226,9 @@ int alloc_fluid(sph_ctx* c, size_t n) {
   ok &= c->precision != SPH_MIXED || B.recI;
   // neighbour lists: capacity entries per particle, whole warps of 32
   const size_t warps = (nn + 31) / 32;
-  B.nl = (uint32_t*)A(warps * (size_t)c->P.list_cap * 32 * 4);
+  // two extra rows of 32 entries: the list walk reads up to two entries past
+  // a particle's last one (prefetch), which stays inside the allocation
+  B.nl = (uint32_t*)A((warps * (size_t)c->P.list_cap + 2) * 32 * 4);
   B.nl_cnt = (uint32_t*)A(nn * 4);
   ok &= B.nl && B.nl_cnt;
   const size_t tiles = (nn + kSortTile - 1) / kSortTile;

@@ -31,7 +31,7 @@ struct sph_nsearch {
   std::vector<Blk> blocks, fixed;
   uint32_t *keys[2] = {}, *vals[2] = {}, *tile_hist = nullptr, *digit_total = nullptr,
            *cell_begin = nullptr;
-  void* xs[3] = {};  // sorted positions (float or double)
+  void* sp = nullptr;  // sorted positions, packed (x, y, z, 0) of the position type
   double* sigma = nullptr;
   int sorted = 0;
   size_t n = 0;
@@ -86,15 +86,20 @@ __global__ void k_ns_keys(Params P, const T* __restrict__ x, const T* __restrict
   }
 }
 
+// Sorted positions packed as one vector per particle (x, y, z, 0): the density
+// pass then reads each candidate with a single load.
 template <class T>
 __global__ void k_ns_reorder(const uint32_t* __restrict__ perm, const T* __restrict__ x,
                              const T* __restrict__ y, const T* __restrict__ z, int n, int dim,
-                             T* sx, T* sy, T* sz) {
+                             typename Vec4<T>::type* sp) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const uint32_t j = perm[k];
-    sx[k] = x[j];
-    sy[k] = y[j];
-    if (dim == 3) sz[k] = z[j];
+    typename Vec4<T>::type v;
+    v.x = x[j];
+    v.y = y[j];
+    v.z = dim == 3 ? z[j] : T(0);
+    v.w = T(0);
+    sp[k] = v;
   }
 }
 
@@ -103,17 +108,16 @@ __global__ void k_ns_reorder(const uint32_t* __restrict__ perm, const T* __restr
 template <class T>
 __global__ void __launch_bounds__(256) k_ns_density(Params P, const uint32_t* __restrict__ keys,
                                                     const uint32_t* __restrict__ cb,
-                                                    const T* __restrict__ x,
-                                                    const T* __restrict__ y,
-                                                    const T* __restrict__ z, int n,
-                                                    double* sigma) {
+                                                    const typename Vec4<T>::type* __restrict__ sp,
+                                                    int n, double* sigma) {
   const T r2max = (T)P.r2max, inv_h = (T)(1.0 / P.h), cw = (T)P.walpha;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const uint32_t key = keys[i];
     const uint32_t r = key / (uint32_t)P.nx;
     const int cx = (int)(key - r * (uint32_t)P.nx), cy = (int)(r % (uint32_t)P.ny),
               cz = (int)(r / (uint32_t)P.ny);
-    const T xi = x[i], yi = y[i], zi = P.dim == 3 ? z[i] : T(0);
+    const typename Vec4<T>::type pi = sp[i];
+    const T xi = pi.x, yi = pi.y, zi = pi.z;
     T sig = 0;
     const int kz = P.dim == 3 ? 1 : 0;
     for (int dz = -kz; dz <= kz; ++dz) {
@@ -127,7 +131,8 @@ __global__ void __launch_bounds__(256) k_ns_density(Params P, const uint32_t* __
         const uint32_t c1 = row + (uint32_t)(cx + 1 < P.nx ? cx + 1 : cx);
         const uint32_t e = cb[c1 + 1];
         for (uint32_t j = cb[c0]; j < e; ++j) {  // the row's 3 cells are contiguous
-          const T dx = xi - x[j], dyv = yi - y[j], dzv = P.dim == 3 ? zi - z[j] : T(0);
+          const typename Vec4<T>::type pj = sp[j];
+          const T dx = xi - pj.x, dyv = yi - pj.y, dzv = zi - pj.z;
           const T r2 = dx * dx + dyv * dyv + dzv * dzv;
           if (r2 < r2max) {
             const T q = sqrt(r2) * inv_h;
@@ -230,10 +235,8 @@ int sph_nsearch_run(sph_nsearch* s, size_t n, const void* x, const void* y, cons
       s->vals[p] = (uint32_t*)ns_alloc(s, n * 4, s->blocks);
       ok &= s->keys[p] && s->vals[p];
     }
-    for (int k = 0; k < 3; ++k) {
-      s->xs[k] = ns_alloc(s, n * ts, s->blocks);
-      ok &= s->xs[k] != nullptr;
-    }
+    s->sp = ns_alloc(s, n * 4 * ts, s->blocks);
+    ok &= s->sp != nullptr;
     s->sigma = (double*)ns_alloc(s, n * 8, s->blocks);
     const size_t tiles = (n + kSortTile - 1) / kSortTile;
     s->tile_hist = (uint32_t*)ns_alloc(s, tiles * ((size_t)1 << kMaxRadixBits) * 4, s->blocks);
@@ -269,24 +272,21 @@ int sph_nsearch_run(sph_nsearch* s, size_t n, const void* x, const void* y, cons
   const uint32_t* keys = s->keys[s->sorted];
   if (s->fp32)
     k_ns_reorder<float><<<gs, 256, 0, st>>>(perm, (const float*)x, (const float*)y,
-                                            (const float*)z, ni, s->P.dim, (float*)s->xs[0],
-                                            (float*)s->xs[1], (float*)s->xs[2]);
+                                            (const float*)z, ni, s->P.dim, (float4*)s->sp);
   else
     k_ns_reorder<double><<<gs, 256, 0, st>>>(perm, (const double*)x, (const double*)y,
-                                             (const double*)z, ni, s->P.dim, (double*)s->xs[0],
-                                             (double*)s->xs[1], (double*)s->xs[2]);
+                                             (const double*)z, ni, s->P.dim,
+                                             (double4_32a*)s->sp);
   cudaEventRecord(s->ev[3], st);
   launch_cell_offsets(keys, ni, s->P.ncell, s->cell_begin, nullptr, 0, 0, st);
   cudaEventRecord(s->ev[4], st);
   const int gd = grid_of(ni, 128, s->L.sms * 16);
   if (s->fp32)
-    k_ns_density<float><<<gd, 128, 0, st>>>(s->P, keys, s->cell_begin, (const float*)s->xs[0],
-                                            (const float*)s->xs[1], (const float*)s->xs[2], ni,
+    k_ns_density<float><<<gd, 128, 0, st>>>(s->P, keys, s->cell_begin, (const float4*)s->sp, ni,
                                             s->sigma);
   else
     k_ns_density<double><<<gd, 128, 0, st>>>(s->P, keys, s->cell_begin,
-                                             (const double*)s->xs[0], (const double*)s->xs[1],
-                                             (const double*)s->xs[2], ni, s->sigma);
+                                             (const double4_32a*)s->sp, ni, s->sigma);
   cudaEventRecord(s->ev[5], st);
   if (cudaGetLastError() != cudaSuccess) return SPH_E_CUDA;
   if (stage_ms) {

@@ -166,9 +166,12 @@ __device__ __forceinline__ T wendland_dr(const KC<T>& k, T r) {
 }
 
 // Register budget of the neighbour-loop kernels (blocks of up to 256 threads):
-// 4 resident blocks -> at most 64 registers in float, 2 -> 128 in double.
+// 5 resident blocks -> at most 48 registers in float, 2 -> 128 in double.  The
+// 3D pressure loop keeps 4 blocks (64 registers): at 48 it spills.
 template <class T>
-constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 4;
+constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 5;
+template <int D, class T>
+constexpr int kMinBlocksP = D == 3 && sizeof(T) == 4 ? 4 : kMinBlocks<T>;
 
 // Binned cell of a storage slot from its sorted key.
 struct Cell {
@@ -910,7 +913,7 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
 }
 
 template <int D, class T>
-__global__ void __launch_bounds__(256, kMinBlocks<T>) k_pressure(Params P, DevBuffers B, KC<T> k) {
+__global__ void __launch_bounds__(256, kMinBlocksP<D, T>) k_pressure(Params P, DevBuffers B, KC<T> k) {
   pressure_range<D, T>(P, B, k, B.sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
                        gridDim.x * blockDim.x);
 }

@@ -62,6 +62,7 @@ def lib():
             L.osph_set_particles.restype = i
             L.osph_set_particles.argtypes = [vp, i, l, vp, vp, vp]
             L.osph_set_drho.restype = i; L.osph_set_drho.argtypes = [vp, vp]
+            L.osph_set_variant.restype = None; L.osph_set_variant.argtypes = [vp, i, i]
             L.osph_step.restype = i; L.osph_step.argtypes = [vp, l]
             for name in ("osph_rebuild", "osph_density_summation", "osph_viscous"):
                 getattr(L, name).restype = None
@@ -169,6 +170,11 @@ class Oracle:
     def set_drho(self, drho):
         drho = np.ascontiguousarray(drho, dtype=np.float64)
         lib().osph_set_drho(self._s, _ptr(drho))
+
+    def set_variant(self, density_riemann: bool = True, reinit_blended: bool = False):
+        """Method variants: Riemann or averaged U* in the density relaxation;
+        clamped or blended free-surface density reinitialisation."""
+        lib().osph_set_variant(self._s, int(bool(density_riemann)), int(bool(reinit_blended)))
 
     @property
     def n(self):

@@ -61,6 +61,10 @@ struct osim {
   double t, tau, dt_ad, dt_ac;
   long n_ac, n_adv;
   int started, flags;
+
+  /* method variants (osph_set_variant) */
+  int density_riemann; /* 1: Riemann U* in the density relaxation; 0: average */
+  int reinit_blended;  /* 0: free-surface clamp; 1: blended reinitialisation */
 };
 
 /* ------------------------------------------------------------------------ */
@@ -131,6 +135,7 @@ osim* osph_create(int dim, const double lo[3], const double hi[3], double dp,
                   const double g[3]) {
   if (dim != 2 && dim != 3) return NULL;
   osim* s = (osim*)xcalloc(1, sizeof(osim));
+  s->density_riemann = 1;
   s->dim = dim;
   s->dp = dp;
   s->h = h;
@@ -399,12 +404,30 @@ static double density_of_sigma(const osim* s, double sig) {
   return s->rho0 * (ratio > 1.0 ? ratio : 1.0);
 }
 
+/* Blended free-surface reinitialisation (variant; SPHinXsys free-surface
+ * density summation): with rho_sum = rho0 sigma / sigma0 and the density
+ * carried into the summation rho_prev,
+ *   rho = rho_sum + max(0, rho_prev - rho_sum) rho0 / rho_prev,
+ * so a particle with full kernel support (rho_sum >= rho_prev) takes the
+ * summed density and a particle near the surface keeps part of its own. */
+static double density_blended(const osim* s, double sig, double rho_prev) {
+  double rho_sum = s->rho0 * (sig / s->sigma0);
+  double excess = rho_prev - rho_sum;
+  return rho_sum + (excess > 0.0 ? excess : 0.0) * s->rho0 / rho_prev;
+}
+
 void osph_density_summation(osim* s) {
   for (long i = 0; i < s->n; ++i) s->sigma[i] = sigma_of(s, i);
   for (long i = 0; i < s->n; ++i) {
-    s->rho[i] = density_of_sigma(s, s->sigma[i]);
+    s->rho[i] = s->reinit_blended ? density_blended(s, s->sigma[i], s->rho[i])
+                                  : density_of_sigma(s, s->sigma[i]);
     s->p[i] = s->c0 * s->c0 * (s->rho[i] - s->rho0);
   }
+}
+
+void osph_set_variant(osim* s, int density_riemann, int reinit_blended) {
+  s->density_riemann = density_riemann ? 1 : 0;
+  s->reinit_blended = reinit_blended ? 1 : 0;
 }
 
 /* Viscous force (once per advection step), SPHinXsys form:
@@ -538,7 +561,10 @@ void osph_pressure_relaxation(osim* s, double dt) {
  * Riemann-based density relaxation
  *   drho_i = -2 rho_i sum_j V_j W'(r_ij) (U_L - U*_ij)
  * (fluid V_j = m / rho_j; wall: mirrored state and V_w = m / rho_w as in
- * the pressure stage), then rho_i += dt/2 drho_i. */
+ * the pressure stage), then rho_i += dt/2 drho_i.
+ * Variant without the Riemann solver (density_riemann = 0): U* is the plain
+ * average (U_L + U_R) / 2, which makes this the textbook SPH continuity
+ * equation drho_i = rho_i sum_j V_j W'(r_ij) (v_i - v_j).e_ij. */
 void osph_half2(osim* s, double dt) {
   const double r2max = 4.0 * s->h * s->h;
   const double c0 = s->c0;
@@ -560,6 +586,7 @@ void osph_half2(osim* s, double dt) {
         double UR = -(s->v[j][0] * e[0] + s->v[j][1] * e[1] + s->v[j][2] * e[2]);
         double Ps, Us;
         osph_riemann(s->p[i], s->p[j], s->rho[i], s->rho[j], UL, UR, c0, &Ps, &Us);
+        if (!s->density_riemann) Us = 0.5 * (UL + UR);
         sum += (s->m / s->rho[j]) * osph_dW(s->dim, s->h, r) * (UL - Us);
       }
       for (long w = s->cbw[cells[q]]; w < s->cbw[cells[q] + 1]; ++w) {
@@ -576,6 +603,7 @@ void osph_half2(osim* s, double dt) {
         double UR = -UL;
         double Ps, Us;
         osph_riemann(s->p[i], pw, s->rho[i], rhow, UL, UR, c0, &Ps, &Us);
+        if (!s->density_riemann) Us = 0.5 * (UL + UR);
         sum += (s->m / rhow) * osph_dW(s->dim, s->h, r) * (UL - Us);
       }
     }

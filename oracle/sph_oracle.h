@@ -55,6 +55,13 @@ void osph_destroy(osim* s);
  * and density are ignored (static wall).  Returns 0 on success. */
 int osph_set_particles(osim* s, int kind, long n, const double* pos,
                        const double* vel, const double* rho);
+/* method variants: density_riemann = 1 (default) takes the Riemann U* in the
+ * density relaxation, 0 the average of the two states; reinit_blended = 0
+ * (default) reinitialises the density with the free-surface clamp
+ * rho0 max(sigma / sigma0, 1), 1 with the blended form
+ * rho_sum + max(0, rho_prev - rho_sum) rho0 / rho_prev. */
+void osph_set_variant(osim* s, int density_riemann, int reinit_blended);
+
 /* set the carried density rate (user order, n values); default 0 */
 int osph_set_drho(osim* s, const double* drho);
 

@@ -12,7 +12,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
 PIN_FILES = ["tests/test_oracle_kernel.py", "tests/test_oracle_neighbours.py",
-             "tests/test_oracle_physics.py"]
+             "tests/test_oracle_physics.py", "tests/test_oracle_variants.py"]
 
 _WALL_P = ("double UR = -UL;\n      double Ps, Us;\n      osph_riemann(p[i], pw, rho[i], "
            "rhow, UL, UR, c0, &Ps, &Us);\n      double f")
@@ -49,6 +49,12 @@ MUTATIONS = {
     "key_axis_swap": ("return (uint32_t)((c[2] * s->nc[1] + c[1]) * s->nc[0] + c[0]);",
                       "return (uint32_t)((c[2] * s->nc[1] + c[0]) * s->nc[0] + c[1]);"),
     "advection_criterion": ("s->dt_ad = 0.25 * s->h /", "s->dt_ad = 0.35 * s->h /"),
+    "no_riemann_average": ("if (!s->density_riemann) Us = 0.5 * (UL + UR);\n        sum += (s->m / s->rho[j])",
+                           "if (!s->density_riemann) Us = 0.5 * UL;\n        sum += (s->m / s->rho[j])"),
+    "blended_weight": ("return rho_sum + (excess > 0.0 ? excess : 0.0) * s->rho0 / rho_prev;",
+                       "return rho_sum + (excess > 0.0 ? excess : 0.0) * rho_prev / s->rho0;"),
+    "blended_branch": ("double excess = rho_prev - rho_sum;",
+                       "double excess = rho_sum - rho_prev;"),
 }
 
 

@@ -113,11 +113,19 @@ enum sph_option {
   SPH_OPT_BLOCK = 3,              /* threads per block of the neighbour loops: 64..256,
                                      multiple of 32 (default 128)                      */
   SPH_OPT_RADIX_BITS = 4,         /* digit width of the radix sort: 4..11 (default 8)  */
-  SPH_OPT_NEIGHBOUR_LIST = 5      /* 0/1 (default 1): loops after the density summation
+  SPH_OPT_NEIGHBOUR_LIST = 5,     /* 0/1 (default 1): loops after the density summation
                                      walk per-particle neighbour lists (candidates within
                                      2h + skin at the rebuild) instead of the cells while a
                                      displacement bound shows them complete; results are
                                      identical either way                               */
+  SPH_OPT_DENSITY_RIEMANN = 6,    /* 1 (default): the density relaxation uses the
+                                     Riemann interface velocity U*; 0: the plain average
+                                     (U_L + U_R)/2, the dissipation-free variant, which is
+                                     the textbook SPH continuity equation                */
+  SPH_OPT_REINIT_BLENDED = 7      /* 0 (default): the density summation reinitialises
+                                     rho = rho0 max(sigma/sigma0, 1); 1: the blended
+                                     free-surface form rho_sum + max(0, rho_prev - rho_sum)
+                                     rho0 / rho_prev, rho_sum = rho0 sigma / sigma0      */
 };
 
 /* Creates a context.

@@ -365,6 +365,7 @@ int sph_create_batch(int n_tanks, const sph_tank* tanks, int precision,
     p.use_list = 1;
     p.list_cap = dim == 3 ? 192 : 64;
     p.skin_max = 0.6 * k.h;
+    p.variant = 0;
     p.cell_base = (uint32_t)total;
     total += ncell + 1;
     if (total >= (1ll << 31)) return SPH_E_INVALID;
@@ -834,6 +835,14 @@ int sph_batch_set_option(sph_batch* b, int option, long value) {
       b->L.radix_bits = (int)value;
       configure_launch(b);
       break;
+    case SPH_OPT_DENSITY_RIEMANN:
+      for (auto& p : b->P)
+        p.variant = value ? (p.variant & ~kVariantNoRiemann) : (p.variant | kVariantNoRiemann);
+      break;
+    case SPH_OPT_REINIT_BLENDED:
+      for (auto& p : b->P)
+        p.variant = value ? (p.variant | kVariantBlended) : (p.variant & ~kVariantBlended);
+      break;
     default:
       return set_err(b, SPH_E_INVALID, "unknown option");
   }
@@ -842,6 +851,8 @@ int sph_batch_set_option(sph_batch* b, int option, long value) {
   CKB(cudaStreamSynchronize(b->mem.stream));
   drop_graph(b);
   rc = upload_tables(b);
+  if (!rc)
+    rc = b->precision == SPH_FP64 ? upload_constants<double>(b) : upload_constants<float>(b);
   if (rc) return rc;
   if (b->P[0].use_list && !old_list) {
     // no list was built at the tanks' last rebuilds: direct search until the next ones

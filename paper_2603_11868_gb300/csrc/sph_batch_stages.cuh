@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) kb_pressure(BatchArgs 
 }
 
 template <int D, class T>
-__global__ void __launch_bounds__(256, kMinBlocks<T>) kb_density_relax(BatchArgs A, DevBuffers B,
+__global__ void __launch_bounds__(256, kMinBlocksP<D, T>) kb_density_relax(BatchArgs A, DevBuffers B,
                                                                        const WorkList* wl) {
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
     density_relax_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x);

@@ -307,6 +307,7 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
   P.use_list = 1;
   P.list_cap = dim == 3 ? 192 : 64;
   P.skin_max = 0.6 * h;
+  P.variant = 0;
 
   int rc = SPH_OK;
   cudaError_t e = cudaGetDevice(&c->device);
@@ -737,6 +738,12 @@ int sph_set_option(sph_ctx* c, int option, long value) {
         return set_err(c, SPH_E_INVALID, "radix bits must be 4..11");
       c->L.radix_bits = (int)value;
       configure_launch(c);
+      break;
+    case SPH_OPT_DENSITY_RIEMANN:
+      c->P.variant = value ? (c->P.variant & ~kVariantNoRiemann) : (c->P.variant | kVariantNoRiemann);
+      break;
+    case SPH_OPT_REINIT_BLENDED:
+      c->P.variant = value ? (c->P.variant | kVariantBlended) : (c->P.variant & ~kVariantBlended);
       break;
     default:
       return set_err(c, SPH_E_INVALID, "unknown option");

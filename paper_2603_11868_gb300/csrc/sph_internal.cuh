@@ -51,6 +51,9 @@ enum {
   kStages
 };
 
+constexpr int kVariantNoRiemann = 1;
+constexpr int kVariantBlended = 2;
+
 // error flag bits (sticky, device)
 constexpr int kFlagOutOfDomain = 1;
 constexpr int kFlagNonFinite = 2;
@@ -76,6 +79,10 @@ struct Params {
   int use_list;   // neighbour lists enabled
   int list_cap;   // list capacity (entries per particle)
   double skin_max;
+  // method variants: kVariantNoRiemann -> the density relaxation takes the
+  // average of the two states instead of the Riemann U*; kVariantBlended ->
+  // blended free-surface density reinitialisation instead of the clamp
+  int variant;
   // position of this tank in the arrays of a batch (all zero for one tank):
   // first fluid slot, first wall slot, first entry of its cell offsets
   int foff, woff;

@@ -112,6 +112,7 @@ template <class T>
 struct KC {
   T r2max, inv_h, cW, cdW, m, c0, inv_c0, rho0, inv_c0sq, eps, two_mu, cs, half;
   T g[3];
+  T riemann;  // 1: Riemann U* in the density relaxation; 0: the average of the states
 };
 
 template <class T>
@@ -130,6 +131,7 @@ __host__ KC<T> make_kc(const Params& P) {
   k.two_mu = (T)(2.0 * P.mu);
   k.cs = (T)P.cs;
   k.half = (T)0.5;
+  k.riemann = (P.variant & kVariantNoRiemann) ? (T)0 : (T)1;
   for (int d = 0; d < 3; ++d) k.g[d] = (T)P.g[d];
   return k;
 }
@@ -167,7 +169,8 @@ __device__ __forceinline__ T wendland_dr(const KC<T>& k, T r) {
 
 // Register budget of the neighbour-loop kernels (blocks of up to 256 threads):
 // 5 resident blocks -> at most 48 registers in float, 2 -> 128 in double.  The
-// 3D pressure loop keeps 4 blocks (64 registers): at 48 it spills.
+// 3D pressure and density-relaxation loops keep 4 blocks (64 registers): at
+// 48 they spill.
 template <class T>
 constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 5;
 template <int D, class T>
@@ -577,6 +580,18 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_build_lists(Params P, De
                           gridDim.x * blockDim.x);
 }
 
+// Density from the kernel sum: the free-surface clamp rho0 max(sigma/sigma0, 1),
+// or the blended reinitialisation rho_sum + max(0, rho_prev - rho_sum) rho0 /
+// rho_prev with rho_sum = rho0 sigma / sigma0 and rho_prev the density carried
+// into the summation.
+__device__ __forceinline__ double reinit_density(const Params& P, double sigma, double rho_prev) {
+  const double ratio = sigma / P.sigma0;
+  if (!(P.variant & kVariantBlended)) return P.rho0 * (ratio > 1.0 ? ratio : 1.0);
+  const double rho_sum = P.rho0 * ratio;
+  const double excess = rho_prev - rho_sum;
+  return rho_sum + (excess > 0.0 ? excess : 0.0) * P.rho0 / rho_prev;
+}
+
 // Whether candidate (dx, dy, dz, wall, j) comes after particle i itself in the
 // candidate order of direct search (cells dz, dy, dx; fluid before wall
 // particles of a cell; ascending index).
@@ -620,8 +635,7 @@ __device__ __forceinline__ void density_summation_range(const Params& P, const D
       if (!w && j == i) self_done = true;
     });
     if (!self_done) sig += wendland(k, T(0));
-    double ratio = (double)sig / P.sigma0;
-    double rho = P.rho0 * (ratio > 1.0 ? ratio : 1.0);
+    const double rho = reinit_density(P, (double)sig, rho_live[i]);
     rho_live[i] = rho;
     typename R::SV s = recS[i];
     R::set_rho(s, (T)rho);
@@ -686,8 +700,7 @@ __device__ __forceinline__ void density_summation_fx_range(const Params& P, cons
     });
     if (!self_done) sig = df_add(sig, dfl{1.0f, 0.0f});
     const double sigma = P.walpha * ((double)sig.hi + (double)sig.lo);
-    const double ratio = sigma / P.sigma0;
-    const double rho = P.rho0 * (ratio > 1.0 ? ratio : 1.0);
+    const double rho = reinit_density(P, sigma, rho_live[i]);
     rho_live[i] = rho;
     typename R::SV s = recS[i];
     R::set_rho(s, (float)rho);
@@ -967,13 +980,14 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
         const T rho_w = k.rho0 + pw_ * k.inv_c0sq;
         const T rbar = k.half * (rho_i + rho_w);
         // U_R = -U_L, so (U_L + U_R)/2 = 0
-        const T Us = div_t(p_i - pw_, T(2) * rbar * k.c0);
+        const T Us = k.riemann * div_t(p_i - pw_, T(2) * rbar * k.c0);
         sum += div_t(k.m, rho_w) * wendland_dr(k, r) * (UL - Us);
       } else {
         const T UR = -(R::vx(pj, sj) * ex + R::vy(pj, sj) * ey + R::vz(pj, sj) * ez);
         const T rho_j = R::rho(pj, sj);
         const T rbar = k.half * (rho_i + rho_j);
-        const T Us = k.half * (UL + UR) + div_t(p_i - R::pres(pj, sj), T(2) * rbar * k.c0);
+        const T Us =
+            k.half * (UL + UR) + k.riemann * div_t(p_i - R::pres(pj, sj), T(2) * rbar * k.c0);
         sum += div_t(k.m, rho_j) * wendland_dr(k, r) * (UL - Us);
       }
     });
@@ -989,7 +1003,7 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
 // One tank: block 0 also publishes this step's velocity maximum for the next
 // step's schedule (a batch does that in its schedule kernel).
 template <int D, class T>
-__global__ void __launch_bounds__(256, kMinBlocks<T>) k_density_relax(Params P, DevBuffers B, KC<T> k) {
+__global__ void __launch_bounds__(256, kMinBlocksP<D, T>) k_density_relax(Params P, DevBuffers B, KC<T> k) {
   DevScalars* sc = B.sc;
   if (blockIdx.x == 0 && threadIdx.x == 0) sc->vmax2_cur = sc->vmax2_next;
   density_relax_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,

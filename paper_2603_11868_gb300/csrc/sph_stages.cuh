@@ -486,11 +486,11 @@ __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffe
   });
 }
 
-// shift of a neighbour cell in the record frame (zero for absolute positions)
+// x - d * cs in the record frame (x itself for absolute positions)
 template <class T>
-__device__ __forceinline__ T cell_shift(int d, T cs) {
-  if constexpr (!Local<T>::kLocal) return T(0);
-  return d == 0 ? T(0) : (d < 0 ? -cs : cs);
+__device__ __forceinline__ T shifted(T x, int d, T cs) {
+  if constexpr (!Local<T>::kLocal) return x;
+  return fmaf(-(float)d, cs, x);
 }
 
 // whether this launch may use the lists: disp is the displacement bound of the
@@ -510,21 +510,21 @@ struct PairGeo {
   T cs;
   __device__ __forceinline__ void rel_rec(const typename R::PV& pj, int dx, int dy, int dz,
                                           T& rx, T& ry, T& rz) const {
-    rx = dsub(xi - cell_shift<T>(dx, cs), R::px(pj));
-    ry = dsub(yi - cell_shift<T>(dy, cs), R::py(pj));
-    rz = dsub(zi - cell_shift<T>(dz, cs), R::pz(pj));
+    rx = dsub(shifted<T>(xi, dx, cs), R::px(pj));
+    ry = dsub(shifted<T>(yi, dy, cs), R::py(pj));
+    rz = dsub(shifted<T>(zi, dz, cs), R::pz(pj));
   }
   __device__ __forceinline__ void rel_wall(const typename WR::WV& pw, int dx, int dy, int dz,
                                            T& rx, T& ry, T& rz) const {
-    rx = dsub(xi - cell_shift<T>(dx, cs), pw.x);
-    ry = dsub(yi - cell_shift<T>(dy, cs), pw.y);
-    rz = dsub(zi - cell_shift<T>(dz, cs), WR::z(pw));
+    rx = dsub(shifted<T>(xi, dx, cs), pw.x);
+    ry = dsub(shifted<T>(yi, dy, cs), pw.y);
+    rz = dsub(shifted<T>(zi, dz, cs), WR::z(pw));
   }
   __device__ __forceinline__ void rel(int j, int dx, int dy, int dz, bool w, T& rx, T& ry,
                                       T& rz) const {
-    const T bx = xi - cell_shift<T>(dx, cs);
-    const T by = yi - cell_shift<T>(dy, cs);
-    const T bz = zi - cell_shift<T>(dz, cs);
+    const T bx = shifted<T>(xi, dx, cs);
+    const T by = shifted<T>(yi, dy, cs);
+    const T bz = shifted<T>(zi, dz, cs);
     if (w) {
       const typename WR::WV pw = wall[j];
       rx = dsub(bx, pw.x); ry = dsub(by, pw.y); rz = dsub(bz, WR::z(pw));

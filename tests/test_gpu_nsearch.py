@@ -40,3 +40,49 @@ def test_nsearch_matches_oracle(n, fp32):
     err = np.abs(got["sigma"] - want_sig).max() / np.abs(want_sig).max()
     assert err <= (1e-5 if fp32 else 1e-12), err
     ns.close()
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_keys_on_and_next_to_cell_faces(fp32):
+    """Coordinates on cell faces lo + k cs and a few ulps to either side, with
+    a grid origin that makes x - lo inexact: the cell index must be the floor of
+    the correctly rounded double quotient (the key kernel's float shortcut
+    must hand every such coordinate to the exact division)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test needs a CUDA device")
+    from oracle import oracle as O
+    from paper_2603_11868_gb300 import build, sph
+    build.build()
+    h = 0.0123456789
+    cs = 2.0 * h
+    lo = np.array([-0.1037, 0.0513, 0.3001])
+    hi = lo + 37.3 * cs
+    rng = np.random.default_rng(5)
+    faces = lo[None, :] + np.arange(0, 37)[:, None] * cs
+    pts = []
+    for d in (-3, -2, -1, 0, 1, 2, 3):
+        f = faces.copy()
+        for _ in range(abs(d)):
+            f = np.nextafter(f, np.inf if d > 0 else -np.inf)
+        pts.append(f)
+    pts = np.concatenate(pts)
+    # mix the axes so that every point has face coordinates on all three
+    pts = np.stack([rng.permutation(pts[:, k]) for k in range(3)], 1)
+    pts = np.clip(pts, lo, hi - 1e-9)
+    if fp32:
+        pts = pts.astype(np.float32).astype(np.float64)
+    dt = torch.float32 if fp32 else torch.float64
+    dev = [torch.tensor(np.ascontiguousarray(pts[:, k]), dtype=dt, device="cuda")
+           for k in range(3)]
+    ns = sph.NeighbourSearch(3, lo, hi, h, fp32=fp32)
+    ns.run(*dev, timed=False)
+    got = ns.results()
+    o = O.Oracle(3, lo, hi, 0.01, h, 1.0, 10.0, 0.0, 1.0, (0, 0, 0))
+    o.set_fluid(pts)
+    want = o.neighbour_state()
+    for k in ("keys", "perm", "cell_begin"):
+        assert np.array_equal(got[k], want[k]), k
+    # the set really straddles faces: cells on both sides of many faces
+    assert len(np.unique(want["keys"])) > 100
+    ns.close()

@@ -344,7 +344,7 @@ def run_batched(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     sph.load()
-    cs = batched_cases()
+    cs = batched_cases(args.tanks)
     n_all = sum(c.n for c in cs)
     if ws > 1:  # independent tanks: each rank advances its share, no collective
         cs = [cs[t] for t in shard_tanks([c.n for c in cs], ws)[rank]]
@@ -374,7 +374,7 @@ def run_batched(args):
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32 pair / f64 state" if args.precision == "mixed" else "f64",
                 "data": "synthetic",
-                "config": {"workload": f"256 tanks, {n_all} fluid particles over {ws} rank(s) "
+                "config": {"workload": f"{args.tanks} tanks, {n_all} fluid particles over {ws} rank(s) "
                                        f"(rank 0: {len(cs)} tanks, {n} fluid + {nw} wall), "
                                        f"dp=0.01, {args.substeps} acoustic steps per bench step",
                            "parallelism": f"tanks sharded over {ws} rank(s)",
@@ -562,6 +562,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="main number only")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch configuration")
+    ap.add_argument("--tanks", type=int, default=256,
+                    help="tank count of the batched workload (the bench line is 256)")
     ap.add_argument("--tuning", default=None,
                     help="block,radix_bits,lists: fixed launch configuration, no autotuner")
     args = ap.parse_args()

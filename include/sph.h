@@ -221,7 +221,11 @@ enum sph_stage {
  * with sph_step. */
 int sph_profile_stages(sph_ctx* ctx, int n, double* ms, long* rebuilds);
 
-/* Kernel launches one acoustic step queues (graph nodes of the step). */
+/* Kernel launches of an acoustic step that begins an advection step (the
+ * rebuild stages included).  A step inside an advection step launches 4 of
+ * them (schedule, first half-step, pressure relaxation, density relaxation):
+ * the step's CUDA graph holds the rest in a conditional node that the
+ * schedule kernel opens or skips on the device. */
 long sph_kernels_per_step(const sph_ctx* ctx);
 
 /* ---- Standalone neighbour search (the paper's cell-linked list build and one

@@ -110,6 +110,65 @@ void enqueue_step(sph_ctx* c, cudaStream_t s) {
     enqueue_step_mixed(args(c), s);
 }
 
+// The acoustic step as a CUDA graph: the schedule kernel, then a conditional
+// node holding the stages of a step that begins an advection step (cell keys,
+// sort, reorder, offsets, lists, density summation, viscous force), then the
+// acoustic stages.  The schedule kernel sets the condition on the device, so a
+// step inside an advection step launches four kernels instead of the rebuild
+// chain of early-exiting ones.
+cudaError_t capture_step_graph(sph_ctx* c, cudaGraph_t* out) {
+  *out = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle cond;
+  // the condition starts every launch at 0 (skip) until the schedule sets it
+  e = cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault);
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(c->stream, g, nullptr, nullptr, 0, mode);
+  if (e == cudaSuccess) {
+    launch_control_cond(c->P, c->B.sc, cond, c->stream);
+    e = cudaStreamEndCapture(c->stream, &g);
+  }
+  cudaGraphNode_t control = nullptr;
+  size_t count = 1;
+  if (e == cudaSuccess) e = cudaGraphGetNodes(g, &control, &count);
+  if (e == cudaSuccess && count != 1) e = cudaErrorStreamCaptureInvalidated;
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeIf;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, g, &control, nullptr, 1, &cp);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0, mode);
+    if (e == cudaSuccess) {
+      if (c->precision == SPH_FP64)
+        enqueue_advection_fp64(args(c), c->stream);
+      else
+        enqueue_advection_mixed(args(c), c->stream);
+      e = cudaStreamEndCapture(c->stream, &body);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(c->stream, g, &cnode, nullptr, 1, mode);
+  if (e == cudaSuccess) {
+    if (c->precision == SPH_FP64)
+      enqueue_acoustic_fp64(args(c), c->stream);
+    else
+      enqueue_acoustic_mixed(args(c), c->stream);
+    e = cudaStreamEndCapture(c->stream, &g);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return e;
+  }
+  *out = g;
+  return cudaSuccess;
+}
+
 void configure_launch(sph_ctx* c) {
   LaunchCfg& L = c->L;
   if (L.block_loop <= 0) L.block_loop = 128;
@@ -471,9 +530,7 @@ int sph_step(sph_ctx* c, int n) {
   if (rc) return rc;
   if (c->use_graph) {
     if (!c->graph_exec) {
-      CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      enqueue_step(c, c->stream);
-      cudaError_t e = cudaStreamEndCapture(c->stream, &c->graph);
+      cudaError_t e = capture_step_graph(c, &c->graph);
       if (e != cudaSuccess) {
         c->graph = nullptr;
         return cuda_err(c, e, "graph capture");

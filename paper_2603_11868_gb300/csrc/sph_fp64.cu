@@ -10,6 +10,20 @@ void enqueue_step_fp64(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev) {
     stages::enqueue_step_t<3, double>(a, s, ev);
 }
 
+void enqueue_advection_fp64(const StageArgs& a, cudaStream_t s) {
+  if (a.P.dim == 2)
+    stages::enqueue_advection_t<2, double>(a, s);
+  else
+    stages::enqueue_advection_t<3, double>(a, s);
+}
+
+void enqueue_acoustic_fp64(const StageArgs& a, cudaStream_t s) {
+  if (a.P.dim == 2)
+    stages::enqueue_acoustic_t<2, double>(a, s);
+  else
+    stages::enqueue_acoustic_t<3, double>(a, s);
+}
+
 void enqueue_initial_sort_fp64(const StageArgs& a, cudaStream_t s) {
   if (a.P.dim == 2)
     stages::enqueue_initial_sort_t<2, double>(a, s);

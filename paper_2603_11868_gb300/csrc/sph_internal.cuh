@@ -264,6 +264,13 @@ struct StageArgs {
 // ev[kStages] after the last stage.
 void enqueue_step_fp64(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev = nullptr);
 void enqueue_step_mixed(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev = nullptr);
+// The two parts of a step for a graph with a conditional node: the stages of a
+// step that begins an advection step (rebuild, lists, density summation,
+// viscous force; launched ungated) and the acoustic stages of every step.
+void enqueue_advection_fp64(const StageArgs& a, cudaStream_t s);
+void enqueue_advection_mixed(const StageArgs& a, cudaStream_t s);
+void enqueue_acoustic_fp64(const StageArgs& a, cudaStream_t s);
+void enqueue_acoustic_mixed(const StageArgs& a, cudaStream_t s);
 // rho = rho0 where fill_rho, id = 0..n-1
 void launch_init_fluid(double* rho, int fill_rho, double rho0, uint32_t* id, int n, cudaStream_t s);
 // AoS (n x dim) -> SoA copy on the device
@@ -304,6 +311,10 @@ void launch_cell_offsets(const uint32_t* keys, int n, uint32_t ncell, uint32_t* 
                          DevScalars* sc, int gated, int flip_par, cudaStream_t s);
 // schedule control kernel (one thread)
 void launch_control(const Params& P, DevScalars* sc, cudaStream_t s);
+// the same, also setting the graph conditional `cond` to "this step begins an
+// advection step"
+void launch_control_cond(const Params& P, DevScalars* sc, cudaGraphConditionalHandle cond,
+                         cudaStream_t s);
 // fresh max |v|^2 of x[par] copy into vmax2_cur
 void launch_vmax_reset(const Params& P, const LaunchCfg& L, const DevBuffers& B,
                        cudaStream_t s);

@@ -11,6 +11,20 @@ void enqueue_step_mixed(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev) {
     stages::enqueue_step_t<3, float>(a, s, ev);
 }
 
+void enqueue_advection_mixed(const StageArgs& a, cudaStream_t s) {
+  if (a.P.dim == 2)
+    stages::enqueue_advection_t<2, float>(a, s);
+  else
+    stages::enqueue_advection_t<3, float>(a, s);
+}
+
+void enqueue_acoustic_mixed(const StageArgs& a, cudaStream_t s) {
+  if (a.P.dim == 2)
+    stages::enqueue_acoustic_t<2, float>(a, s);
+  else
+    stages::enqueue_acoustic_t<3, float>(a, s);
+}
+
 void enqueue_initial_sort_mixed(const StageArgs& a, cudaStream_t s) {
   if (a.P.dim == 2)
     stages::enqueue_initial_sort_t<2, float>(a, s);

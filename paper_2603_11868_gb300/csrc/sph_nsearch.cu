@@ -368,7 +368,13 @@ __device__ __forceinline__ void control_one(const Params& P, DevScalars* sc) {
   sc->dt_prev = dt;
 }
 
-__global__ void k_control(Params P, DevScalars* sc) { control_one(P, sc); }
+// use_cond: the step runs as a CUDA graph whose rebuild stages sit in a
+// conditional node; the schedule's decision opens or skips it on the device.
+__global__ void k_control(Params P, DevScalars* sc, cudaGraphConditionalHandle cond,
+                          int use_cond) {
+  control_one(P, sc);
+  if (use_cond) cudaGraphSetConditional(cond, sc->new_adv ? 1u : 0u);
+}
 
 // ---------------------------------------------------------------------------
 // Batched schedule: one thread per tank (one block of up to kMaxTanks
@@ -712,7 +718,12 @@ void launch_cell_offsets(const uint32_t* keys, int n, uint32_t ncell, uint32_t* 
 }
 
 void launch_control(const Params& P, DevScalars* sc, cudaStream_t s) {
-  k_control<<<1, 1, 0, s>>>(P, sc);
+  k_control<<<1, 1, 0, s>>>(P, sc, cudaGraphConditionalHandle{}, 0);
+}
+
+void launch_control_cond(const Params& P, DevScalars* sc, cudaGraphConditionalHandle cond,
+                         cudaStream_t s) {
+  k_control<<<1, 1, 0, s>>>(P, sc, cond, 1);
 }
 
 void launch_batch_control(const BatchArgs& A, int tile, int force, cudaStream_t s) {

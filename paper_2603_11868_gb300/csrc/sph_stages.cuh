@@ -1075,25 +1075,33 @@ void enqueue_rebuild(const StageArgs& a, cudaStream_t s, int gated, cudaEvent_t*
   launch_cell_offsets(B.keys[B.sorted_buf], P.n, P.ncell, B.cell_begin, B.sc, gated, 1, s);
 }
 
+// Stages after the rebuild of an advection step; gated: each kernel returns at
+// once unless the step begins an advection step.
 template <int D, class T>
-void enqueue_step_t(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev) {
+void enqueue_advection_loops(const StageArgs& a, cudaStream_t s, int gated, cudaEvent_t* ev) {
   const Params& P = a.P;
   const LaunchCfg& L = a.L;
   const DevBuffers& B = a.B;
   const KC<T> k = make_kc<T>(P);
-  mark(ev, kStageControl, s);
-  launch_control(P, B.sc, s);
-  enqueue_rebuild<D, T>(a, s, 1, ev);
+  const int gl = grid_for(P.n, L.block_loop, L.blocks_loop);
+  mark(ev, kStageDensitySum, s);
+  k_build_lists<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, gated);
+  if constexpr (Local<T>::kLocal)
+    k_density_summation_fx<D><<<gl, L.block_loop, 0, s>>>(P, B, gated);
+  else
+    k_density_summation<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, gated);
+  mark(ev, kStageViscous, s);
+  k_viscous<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, gated);
+}
+
+template <int D, class T>
+void enqueue_acoustic_t(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  const Params& P = a.P;
+  const LaunchCfg& L = a.L;
+  const DevBuffers& B = a.B;
+  const KC<T> k = make_kc<T>(P);
   const int gl = grid_for(P.n, L.block_loop, L.blocks_loop);
   const int gs = grid_for(P.n, L.block_stream, L.blocks_stream);
-  mark(ev, kStageDensitySum, s);
-  k_build_lists<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, 1);
-  if constexpr (Local<T>::kLocal)
-    k_density_summation_fx<D><<<gl, L.block_loop, 0, s>>>(P, B, 1);
-  else
-    k_density_summation<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, 1);
-  mark(ev, kStageViscous, s);
-  k_viscous<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, 1);
   mark(ev, kStageHalf1, s);
   k_half1<D, T><<<gs, L.block_stream, 0, s>>>(P, B);
   mark(ev, kStagePressure, s);
@@ -1101,6 +1109,23 @@ void enqueue_step_t(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev) {
   mark(ev, kStageDensityRelax, s);
   k_density_relax<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k);
   mark(ev, kStages, s);
+}
+
+// One acoustic step as a plain launch sequence (the rebuild stages gated).
+template <int D, class T>
+void enqueue_step_t(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev) {
+  mark(ev, kStageControl, s);
+  launch_control(a.P, a.B.sc, s);
+  enqueue_rebuild<D, T>(a, s, 1, ev);
+  enqueue_advection_loops<D, T>(a, s, 1, ev);
+  enqueue_acoustic_t<D, T>(a, s, ev);
+}
+
+// The body of the graph's conditional node: the same stages, ungated.
+template <int D, class T>
+void enqueue_advection_t(const StageArgs& a, cudaStream_t s) {
+  enqueue_rebuild<D, T>(a, s, 0, nullptr);
+  enqueue_advection_loops<D, T>(a, s, 0, nullptr);
 }
 
 template <int D, class T>

@@ -244,8 +244,13 @@ int sph_nsearch_create(const sph_domain* domain, double h, int pos_precision,
  * or double as created; z ignored in 2D): cell keys, the stable radix sort,
  * the reorder of the positions, the CSR cell offsets, and one density pass
  * sigma_i = sum_{r_ij < 2h} W(r_ij) (self included) in the position type.
- * stage_ms, if not NULL, receives the device time of the five stages (and the
- * call then waits for them).  Buffers grow as needed. */
+ * The coordinate arrays stay the caller's; they are read by work queued on the
+ * object's stream after the caller's stream, so they must stay valid until
+ * that work is done.  Positions outside the domain are clamped into the edge
+ * cell.  stage_ms, if not NULL, receives the device time of the five stages
+ * (and the call then waits for them).  Buffers grow as needed.  Returns
+ * SPH_E_INVALID for n = 0, n >= 2^31 or a missing array, SPH_E_OOM when the
+ * buffers cannot grow, SPH_E_CUDA for a launch or event failure. */
 int sph_nsearch_run(sph_nsearch* ns, size_t n, const void* x, const void* y, const void* z,
                     double* stage_ms);
 
@@ -299,7 +304,8 @@ int sph_cell_sort_noalloc(const sph_domain* domain, double cell_size, const doub
                           const double* y, const double* z, size_t n, uint32_t* keys_out,
                           uint32_t* perm_out, uint32_t* cell_begin_out, void* stream);
 
-/* ---- Autotuner.  A launch configuration: threads per block of the
+/* ---- Autotuner (the paper has no counterpart: it picks launch parameters
+ * of this implementation).  A launch configuration: threads per block of the
  * neighbour loops (for a batch also the tile, the slots per work unit of its
  * persistent launches), the digit width of the radix sort, and whether the
  * loops walk neighbour lists.  None of them changes any result. */

@@ -388,7 +388,12 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
   c->B.cell_begin = (uint32_t*)dev_alloc(c, ((size_t)P.ncell + 1) * 4, c->fixed_blocks);
   c->B.wall_cb = (uint32_t*)dev_alloc(c, ((size_t)P.ncell + 1) * 4, c->fixed_blocks);
   c->B.digit_total = (uint32_t*)dev_alloc(c, ((size_t)1 << kMaxRadixBits) * 4, c->fixed_blocks);
-  if (!c->B.sc || !c->B.cell_begin || !c->B.wall_cb || !c->B.digit_total) {
+  double* ctab = nullptr;
+  if (precision == SPH_MIXED)
+    ctab = (double*)dev_alloc(c, (size_t)(P.nx + P.ny + P.nz) * 8, c->fixed_blocks);
+  c->B.ctab = ctab;
+  if (!c->B.sc || !c->B.cell_begin || !c->B.wall_cb || !c->B.digit_total ||
+      (precision == SPH_MIXED && !ctab)) {
     sph_destroy(c);
     return SPH_E_OOM;
   }
@@ -397,6 +402,10 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
   if (e == cudaSuccess)
     e = cudaMemsetAsync(c->B.wall_cb, 0, ((size_t)P.ncell + 1) * 4, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->B.digit_total, 0, ((size_t)1 << kMaxRadixBits) * 4, c->stream);
+  if (e == cudaSuccess && ctab) {
+    launch_centre_table(P, ctab, c->stream);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     rc = cuda_err(c, e, "sph_create");

@@ -150,6 +150,9 @@ struct DevBuffers {
   // binned cell key of every storage slot (the cell of the last rebuild, in
   // its tank's grid): keys[sorted_buf] for one tank, a separate array in a batch
   const uint32_t* binned;
+  // mixed path: cell-centre coordinates per axis (nx | ny | nz doubles) of the
+  // record frame; null where the kernels compute them (FP64 path, batches)
+  const double* ctab;
   uint32_t* tile_hist;  // bins x tiles
   uint32_t* digit_total;
   uint32_t* cell_begin;  // ncell + 1
@@ -278,6 +281,8 @@ void launch_deinterleave(const double* aos, int n, int dim, double* const soa[3]
 // Initial binning / sort after set_particles (forces a rebuild of the cell
 // list and builds the records without changing the schedule).
 void enqueue_initial_sort_fp64(const StageArgs& a, cudaStream_t s);
+// the cell-centre table of the mixed path's record frame (nx + ny + nz doubles)
+void launch_centre_table(const Params& P, double* tab, cudaStream_t s);
 void enqueue_initial_sort_mixed(const StageArgs& a, cudaStream_t s);
 // Wall setup: keys, sort, wall records and wall cell offsets from the
 // staging buffer io (double SoA [x | y | z], nw each, user order).  The sort

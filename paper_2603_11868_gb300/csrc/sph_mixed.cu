@@ -4,6 +4,22 @@
 
 namespace sphgb {
 
+namespace {
+__global__ void k_centre_table(Params P, double* tab) {
+  const int total = P.nx + P.ny + P.nz;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int k = t < P.nx ? 0 : (t < P.nx + P.ny ? 1 : 2);
+    const int c = k == 0 ? t : (k == 1 ? t - P.nx : t - P.nx - P.ny);
+    tab[t] = stages::Local<float>::centre(P, k, c);
+  }
+}
+}  // namespace
+
+void launch_centre_table(const Params& P, double* tab, cudaStream_t s) {
+  const int total = P.nx + P.ny + P.nz;
+  k_centre_table<<<(total + 255) / 256, 256, 0, s>>>(P, tab);
+}
+
 void enqueue_step_mixed(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev) {
   if (a.P.dim == 2)
     stages::enqueue_step_t<2, float>(a, s, ev);

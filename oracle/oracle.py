@@ -63,6 +63,10 @@ def lib():
             L.osph_set_particles.argtypes = [vp, i, l, vp, vp, vp]
             L.osph_set_drho.restype = i; L.osph_set_drho.argtypes = [vp, vp]
             L.osph_set_variant.restype = None; L.osph_set_variant.argtypes = [vp, i, i]
+            L.osph_set_transport_correction.restype = None
+            L.osph_set_transport_correction.argtypes = [vp, i]
+            L.osph_transport_correction.restype = None
+            L.osph_transport_correction.argtypes = [vp]
             L.osph_step.restype = i; L.osph_step.argtypes = [vp, l]
             for name in ("osph_rebuild", "osph_density_summation", "osph_viscous"):
                 getattr(L, name).restype = None
@@ -170,6 +174,13 @@ class Oracle:
     def set_drho(self, drho):
         drho = np.ascontiguousarray(drho, dtype=np.float64)
         lib().osph_set_drho(self._s, _ptr(drho))
+
+    def set_transport_correction(self, on: bool = True):
+        """Transport-velocity correction once per advection step."""
+        lib().osph_set_transport_correction(self._s, int(bool(on)))
+
+    def transport_correction(self):
+        lib().osph_transport_correction(self._s)
 
     def set_variant(self, density_riemann: bool = True, reinit_blended: bool = False):
         """Method variants: Riemann or averaged U* in the density relaxation;

@@ -65,6 +65,7 @@ struct osim {
   /* method variants (osph_set_variant) */
   int density_riemann; /* 1: Riemann U* in the density relaxation; 0: average */
   int reinit_blended;  /* 0: free-surface clamp; 1: blended reinitialisation */
+  int transport;       /* 1: transport-velocity correction each advection step */
 };
 
 /* ------------------------------------------------------------------------ */
@@ -463,6 +464,50 @@ void osph_viscous(osim* s) {
   }
 }
 
+/* Transport-velocity (particle-shifting) correction (variant, a reading of
+ * SPHinXsys's transport velocity correction): once per advection step,
+ * right after the density summation, every fluid particle whose kernel sum
+ * shows full support (sigma_i >= 0.95 sigma0) moves by
+ *   dr_i = -C h^2 sum_j V_j W'(r_ij) e_ij,   C = 0.2,
+ * over its fluid (V_j = m / rho_j) and wall (V_w = dp^d) neighbours, self
+ * excluded.  All shifts come from the positions before any is applied.  The
+ * sum is the SPH gradient of the particle concentration, so the shift moves a
+ * particle from crowded towards sparse neighbourhoods. */
+void osph_transport_correction(osim* s) {
+  const double r2max = 4.0 * s->h * s->h;
+  const double coef = -0.2 * s->h * s->h;
+  double (*d)[3] = (double (*)[3])xcalloc((size_t)(s->n > 0 ? s->n : 1), sizeof *d);
+  long cells[27];
+  for (long i = 0; i < s->n; ++i) {
+    if (s->sigma[i] < 0.95 * s->sigma0) continue;
+    int nc = neighbour_cells(s, s->key[i], cells);
+    double g[3] = {0.0, 0.0, 0.0};
+    for (int q = 0; q < nc; ++q) {
+      for (long j = s->cb[cells[q]]; j < s->cb[cells[q] + 1]; ++j) {
+        if (j == i) continue;
+        double r2 = dist2(s->x[i], s->x[j]);
+        if (r2 >= r2max) continue;
+        double r = sqrt(r2);
+        double f = (s->m / s->rho[j]) * osph_dW(s->dim, s->h, r) / r;
+        for (int k = 0; k < 3; ++k) g[k] += f * (s->x[i][k] - s->x[j][k]);
+      }
+      for (long w = s->cbw[cells[q]]; w < s->cbw[cells[q] + 1]; ++w) {
+        double r2 = dist2(s->x[i], s->xw[w]);
+        if (r2 >= r2max) continue;
+        double r = sqrt(r2);
+        double f = s->V * osph_dW(s->dim, s->h, r) / r;
+        for (int k = 0; k < 3; ++k) g[k] += f * (s->x[i][k] - s->xw[w][k]);
+      }
+    }
+    for (int k = 0; k < 3; ++k) d[i][k] = coef * g[k];
+  }
+  for (long i = 0; i < s->n; ++i)
+    for (int k = 0; k < s->dim; ++k) s->x[i][k] += d[i][k];
+  free(d);
+}
+
+void osph_set_transport_correction(osim* s, int on) { s->transport = on ? 1 : 0; }
+
 double osph_vmax2(const osim* s) {
   double m = 0.0;
   for (long i = 0; i < s->n; ++i) {
@@ -627,6 +672,7 @@ int osph_step(osim* s, long nsteps) {
       s->dt_ad = 0.25 * s->h / (s->U_ref > vmax ? s->U_ref : vmax);
       osph_rebuild(s);
       osph_density_summation(s);
+      if (s->transport) osph_transport_correction(s);
       osph_viscous(s);
       s->tau = 0.0;
       s->n_adv += 1;

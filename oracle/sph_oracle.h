@@ -62,6 +62,12 @@ int osph_set_particles(osim* s, int kind, long n, const double* pos,
  * rho_sum + max(0, rho_prev - rho_sum) rho0 / rho_prev. */
 void osph_set_variant(osim* s, int density_riemann, int reinit_blended);
 
+/* transport-velocity correction (default off): once per advection step,
+ * after the density summation, fluid particles with sigma >= 0.95 sigma0 move
+ * by -0.2 h^2 sum_j V_j grad_i W_ij (fluid V_j = m / rho_j, wall dp^dim) */
+void osph_set_transport_correction(osim* s, int on);
+void osph_transport_correction(osim* s);
+
 /* set the carried density rate (user order, n values); default 0 */
 int osph_set_drho(osim* s, const double* drho);
 

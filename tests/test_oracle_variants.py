@@ -130,3 +130,73 @@ def test_variants_change_a_dam_break_run(oracle_mod):
         out.append(o.field(oracle_mod.RHO))
         assert np.isfinite(out[-1]).all()
     assert not np.array_equal(out[0], out[1]) and not np.array_equal(out[0], out[2])
+
+
+# --------------------------------------------------------------------------
+# transport-velocity (particle-shifting) correction
+def _lattice_block(n=14, dp=0.05, dim=2):
+    axes = [(np.arange(n) + 0.5) * dp for _ in range(dim)]
+    grid = np.meshgrid(*axes[::-1], indexing="ij")
+    return np.stack([g.ravel() for g in grid[::-1]], 1)
+
+
+def _shifted(oracle_mod, pos, dim=2, dp=0.05, wall=None):
+    c = cases.Case("tv", dim, dp, 1.3 * dp, 1.0, 10.0, 0.0, 1.0, tuple([0.0] * dim),
+                   tuple([-1.0] * dim), tuple([2.0] * dim), pos,
+                   np.zeros((0, dim)) if wall is None else wall)
+    o = oracle_mod.Oracle.from_case(c)
+    o.rebuild()
+    o.density_summation()
+    before = o.field(oracle_mod.POS)
+    o.transport_correction()
+    return o.field(oracle_mod.POS) - before, o.field(oracle_mod.SIGMA) / oracle_mod.sigma0(
+        dim, dp, 1.3 * dp)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_transport_correction_vanishes_on_a_perfect_lattice(oracle_mod, dim):
+    pos = _lattice_block(n=14 if dim == 2 else 9, dim=dim)
+    d, s = _shifted(oracle_mod, pos, dim=dim)
+    inner = s >= 0.95
+    assert inner.any() and (~inner).any()
+    # interior particles: the concentration gradient of a lattice is zero
+    deep = np.all((pos > 0.05 * 3) & (pos < pos.max(0) - 0.05 * 2.5), axis=1)
+    assert deep.any()
+    assert np.abs(d[deep]).max() < 1e-14
+    # particles without full support (the surface) never move
+    assert np.abs(d[~inner]).max() == 0.0
+
+
+def test_transport_correction_restores_a_displaced_particle(oracle_mod):
+    """One interior particle nudged off its lattice site moves back towards it
+    (away from the neighbours it crowded), by less than the nudge."""
+    pos = _lattice_block(n=14)
+    k = 7 * 14 + 7
+    nudge = np.array([0.004, -0.0025])
+    pos[k] += nudge
+    d, s = _shifted(oracle_mod, pos)
+    assert s[k] >= 0.95
+    assert np.dot(d[k], nudge) < 0
+    assert np.linalg.norm(d[k]) < np.linalg.norm(nudge)
+    # the lattice neighbours it moved closer to are pushed away from it, those it
+    # moved away from are drawn after it (beyond q = 0.5 the kernel slope grows
+    # as particles approach)
+    site = pos[k] - nudge
+    r = pos - pos[k]
+    near = (np.linalg.norm(pos - site, axis=1) < 1.5 * 0.05) & (np.arange(len(pos)) != k)
+    closer = np.linalg.norm(r, axis=1) < np.linalg.norm(pos - site, axis=1)
+    assert (near & closer).any() and (near & ~closer).any()
+    for q in np.nonzero(near)[0]:
+        assert (np.dot(d[q], r[q]) > 0) == closer[q], q
+
+
+def test_transport_correction_runs_in_the_schedule(oracle_mod):
+    c = cases.dam_break_2d(dp=0.05)
+    a = oracle_mod.Oracle.from_case(c)
+    a.step(12)
+    b = oracle_mod.Oracle.from_case(c)
+    b.set_transport_correction(True)
+    b.step(12)
+    pa, pb = a.field(oracle_mod.POS), b.field(oracle_mod.POS)
+    assert np.isfinite(pb).all()
+    assert 0 < np.abs(pa - pb).max() < 0.05 * c.dp

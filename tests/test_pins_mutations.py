@@ -55,6 +55,10 @@ MUTATIONS = {
                        "return rho_sum + (excess > 0.0 ? excess : 0.0) * rho_prev / s->rho0;"),
     "blended_branch": ("double excess = rho_prev - rho_sum;",
                        "double excess = rho_sum - rho_prev;"),
+    "transport_sign": ("const double coef = -0.2 * s->h * s->h;",
+                       "const double coef = 0.2 * s->h * s->h;"),
+    "transport_support": ("if (s->sigma[i] < 0.95 * s->sigma0) continue;",
+                          "if (s->sigma[i] < 0.5 * s->sigma0) continue;"),
 }
 
 

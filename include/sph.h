@@ -122,10 +122,14 @@ enum sph_option {
                                      Riemann interface velocity U*; 0: the plain average
                                      (U_L + U_R)/2, the dissipation-free variant, which is
                                      the textbook SPH continuity equation                */
-  SPH_OPT_REINIT_BLENDED = 7      /* 0 (default): the density summation reinitialises
+  SPH_OPT_REINIT_BLENDED = 7,     /* 0 (default): the density summation reinitialises
                                      rho = rho0 max(sigma/sigma0, 1); 1: the blended
                                      free-surface form rho_sum + max(0, rho_prev - rho_sum)
                                      rho0 / rho_prev, rho_sum = rho0 sigma / sigma0      */
+  SPH_OPT_TRANSPORT_CORRECTION = 8 /* 0 (default) / 1: transport-velocity (particle
+                                     shifting) correction once per advection step, after
+                                     the density summation: particles with sigma >= 0.95
+                                     sigma0 move by -0.2 h^2 sum_j V_j grad_i W_ij     */
 };
 
 /* Creates a context.

@@ -97,6 +97,8 @@ BatchStageArgs args(const sph_batch* b) {
   a.B.binned = b->A.bkey;
   a.L = b->L;
   a.dim = b->dim;
+  a.variants = 0;
+  for (const auto& p : b->P) a.variants |= p.variant;
   return a;
 }
 
@@ -217,6 +219,8 @@ int alloc_fluid(sph_batch* b, size_t n) {
     ok &= k >= d || (B.aprior[k] && B.acc[k]);
   }
   B.sigma = Al(nn * ts);
+  B.sigma64 = (double*)Al(nn * 8);
+  ok &= B.sigma64 != nullptr;
   const size_t pbytes = 4 * ts;
   const size_t sbytes = (d == 3 ? 4 : 2) * ts;
   for (int p = 0; p < 2; ++p) {
@@ -842,6 +846,10 @@ int sph_batch_set_option(sph_batch* b, int option, long value) {
     case SPH_OPT_REINIT_BLENDED:
       for (auto& p : b->P)
         p.variant = value ? (p.variant | kVariantBlended) : (p.variant & ~kVariantBlended);
+      break;
+    case SPH_OPT_TRANSPORT_CORRECTION:
+      for (auto& p : b->P)
+        p.variant = value ? (p.variant | kVariantTransport) : (p.variant & ~kVariantTransport);
       break;
     default:
       return set_err(b, SPH_E_INVALID, "unknown option");

@@ -93,6 +93,23 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) kb_density_summation(Batch
 }
 
 template <int D, class T>
+__global__ void __launch_bounds__(256, kMinBlocks<T>) kb_transport(BatchArgs A, DevBuffers B,
+                                                                   const WorkList* wl) {
+  for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
+    if (P.variant & kVariantTransport)
+      transport_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x);
+  });
+}
+
+template <int D, class T>
+__global__ void kb_transport_apply(BatchArgs A, DevBuffers B, const WorkList* wl) {
+  for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
+    if (P.variant & kVariantTransport)
+      transport_apply_range<D, T>(P, B, A.tsc + t, i, end, blockDim.x);
+  });
+}
+
+template <int D, class T>
 __global__ void __launch_bounds__(256, kMinBlocks<T>) kb_viscous(BatchArgs A, DevBuffers B,
                                                                  const WorkList* wl) {
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
@@ -167,6 +184,10 @@ void enqueue_batch_step_t(const BatchStageArgs& a, cudaStream_t s, cudaEvent_t* 
   mark(ev, kStageDensitySum, s);
   kb_build_lists<D, T><<<grid, blk, 0, s>>>(A, B, A.wl_adv);
   kb_density_summation<D, T><<<grid, blk, 0, s>>>(A, B, A.wl_adv);
+  if (a.variants & kVariantTransport) {
+    kb_transport<D, T><<<grid, blk, 0, s>>>(A, B, A.wl_adv);
+    kb_transport_apply<D, T><<<grid, blk, 0, s>>>(A, B, A.wl_adv);
+  }
   mark(ev, kStageViscous, s);
   kb_viscous<D, T><<<grid, blk, 0, s>>>(A, B, A.wl_adv);
   mark(ev, kStageHalf1, s);

@@ -272,6 +272,8 @@ int alloc_fluid(sph_ctx* c, size_t n) {
     ok &= k >= d || (B.aprior[k] && B.acc[k]);
   }
   B.sigma = A(nn * ts);
+  B.sigma64 = (double*)A(nn * 8);
+  ok &= B.sigma64 != nullptr;
   const size_t pbytes = 4 * ts;
   const size_t sbytes = (d == 3 ? 4 : 2) * ts;
   for (int p = 0; p < 2; ++p) {
@@ -810,6 +812,10 @@ int sph_set_option(sph_ctx* c, int option, long value) {
       break;
     case SPH_OPT_REINIT_BLENDED:
       c->P.variant = value ? (c->P.variant | kVariantBlended) : (c->P.variant & ~kVariantBlended);
+      break;
+    case SPH_OPT_TRANSPORT_CORRECTION:
+      c->P.variant =
+          value ? (c->P.variant | kVariantTransport) : (c->P.variant & ~kVariantTransport);
       break;
     default:
       return set_err(c, SPH_E_INVALID, "unknown option");

@@ -53,6 +53,7 @@ enum {
 
 constexpr int kVariantNoRiemann = 1;
 constexpr int kVariantBlended = 2;
+constexpr int kVariantTransport = 4;  // transport-velocity correction each advection step
 
 // error flag bits (sticky, device)
 constexpr int kFlagOutOfDomain = 1;
@@ -81,7 +82,8 @@ struct Params {
   double skin_max;
   // method variants: kVariantNoRiemann -> the density relaxation takes the
   // average of the two states instead of the Riemann U*; kVariantBlended ->
-  // blended free-surface density reinitialisation instead of the clamp
+  // blended free-surface density reinitialisation instead of the clamp;
+  // kVariantTransport -> transport-velocity correction after the summation
   int variant;
   // position of this tank in the arrays of a batch (all zero for one tank):
   // first fluid slot, first wall slot, first entry of its cell offsets
@@ -106,6 +108,9 @@ struct DevScalars {
   double dt_prev;  // length of the previous acoustic step
   int list_bad;    // a list overflowed its capacity in this advection step
   int pad_;
+  // bit pattern of the largest transport-velocity shift of this advection step
+  // (part of every particle's displacement since the rebuild)
+  unsigned long long shift_bits;
 };
 
 template <class T>
@@ -139,6 +144,7 @@ struct DevBuffers {
   void* aprior[3];  // T
   void* acc[3];     // T, diagnostics
   void* sigma;      // T, diagnostics
+  double* sigma64;  // kernel sum of the last summation (transport correction's support test)
   void* recP[2];    // T4
   void* recS[2];    // T4 (3D) or T2 (2D)
   void* recI;       // mixed mode: int4 (3D) / int2 (2D) fixed-point offsets at the rebuild
@@ -224,6 +230,7 @@ struct BatchStageArgs {
   DevBuffers B;  // shared arrays; B.sc unused, B.binned = A.bkey
   LaunchCfg L;
   int dim;
+  int variants;  // union of the tanks' method variants (which stages to launch)
 };
 
 // batched schedule kernel: per-tank dual-criteria schedule, then the list of

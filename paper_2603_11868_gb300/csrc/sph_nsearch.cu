@@ -355,6 +355,7 @@ __device__ __forceinline__ void control_one(const Params& P, DevScalars* sc) {
     double skin = 2.5 * (vmax + gmag * span) * span + 0.02 * P.h;
     sc->skin = skin < P.skin_max ? skin : P.skin_max;
     sc->list_bad = 0;
+    sc->shift_bits = 0ull;
     disp = 0.0;
   }
   sc->new_adv = adv;

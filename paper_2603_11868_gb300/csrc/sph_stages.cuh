@@ -56,6 +56,9 @@ struct Rec<3, T> {
   __device__ static T pres(const PV& a, const SV&) { return a.w; }
   __device__ static T rho(const PV&, const SV& b) { return b.w; }
   __device__ static void set_rho(SV& b, T r) { b.w = r; }
+  __device__ static void set_pos(PV& a, T x, T y, T z) {
+    a.x = x; a.y = y; a.z = z;
+  }
 };
 
 template <class T>
@@ -81,6 +84,9 @@ struct Rec<2, T> {
   __device__ static T pres(const PV&, const SV& b) { return b.x; }
   __device__ static T rho(const PV&, const SV& b) { return b.y; }
   __device__ static void set_rho(SV& b, T r) { b.y = r; }
+  __device__ static void set_pos(PV& a, T x, T y, T) {
+    a.x = x; a.y = y;
+  }
 };
 
 // wall record: position (absolute or cell-local offset)
@@ -509,6 +515,7 @@ __device__ __forceinline__ T shifted(T x, int d, T cs) {
 // whether this launch may use the lists: disp is the displacement bound of the
 // positions the loop reads
 __device__ __forceinline__ bool list_ok(const Params& P, const DevScalars* sc, double disp) {
+  disp += __longlong_as_double((long long)sc->shift_bits);  // transport shifts, if any
   return P.use_list && !sc->list_bad && 2.0 * disp < 0.999 * sc->skin - 1e-6 * P.h;
 }
 
@@ -649,6 +656,7 @@ __device__ __forceinline__ void density_summation_range(const Params& P, const D
     });
     if (!self_done) sig += wendland(k, T(0));
     const double rho = reinit_density(P, (double)sig, rho_live[i]);
+    if (P.variant & kVariantTransport) B.sigma64[i] = (double)sig;
     rho_live[i] = rho;
     typename R::SV s = recS[i];
     R::set_rho(s, (T)rho);
@@ -714,6 +722,7 @@ __device__ __forceinline__ void density_summation_fx_range(const Params& P, cons
     if (!self_done) sig = df_add(sig, dfl{1.0f, 0.0f});
     const double sigma = P.walpha * ((double)sig.hi + (double)sig.lo);
     const double rho = reinit_density(P, sigma, rho_live[i]);
+    if (P.variant & kVariantTransport) B.sigma64[i] = sigma;
     rho_live[i] = rho;
     typename R::SV s = recS[i];
     R::set_rho(s, (float)rho);
@@ -729,6 +738,116 @@ __global__ void __launch_bounds__(256, 4) k_density_summation_fx(Params P, DevBu
   if (gated && !sc->new_adv) return;
   density_summation_fx_range<D>(P, B, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
                                 gridDim.x * blockDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// Transport-velocity (particle-shifting) correction, once per advection step
+// after the density summation (a method variant): every particle with full
+// kernel support (sigma >= 0.95 sigma0, decided in double like the density)
+// moves by -C h^2 sum_j V_j grad_i W_ij, C = 0.2, over fluid (V_j = m / rho_j)
+// and wall (dp^dim) neighbours.  The walk only computes the shifts (into the
+// prior-acceleration arrays, which the viscous stage overwrites next); the
+// apply pass moves the particles and their records, so every shift uses the
+// positions before any of them.
+template <int D, class T>
+__device__ __forceinline__ void transport_range(const Params& P, const DevBuffers& B,
+                                                const KC<T>& k, DevScalars* sc, int i, int end,
+                                                int stride) {
+  using R = Rec<D, T>;
+  const bool use_list = list_ok(P, sc, 0.0);
+  const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
+  const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
+  const uint32_t* __restrict__ keys = B.binned;
+  T* d0 = (T*)B.aprior[0];
+  T* d1 = (T*)B.aprior[1];
+  T* d2 = (T*)B.aprior[2];
+  const T wallV = (T)P.V;
+  const T coef = (T)(-0.2 * P.h * P.h);
+  for (; i < end; i += stride) {
+    T gx = 0, gy = 0, gz = 0;
+    if (B.sigma64[i] >= 0.95 * P.sigma0) {
+      const Cell ci = decode(keys[i], P);
+      const typename R::PV pi = recP[i];
+      PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
+                      R::pz(pi), k.cs};
+      visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
+        T rx, ry, rz;
+        G.rel(j, dx, dy, dz, w, rx, ry, rz);
+        const T r2 = r2_of(rx, ry, rz);
+        if (!(r2 < k.r2max) || (!w && j == i)) return;
+        const T r = sqrt(r2);
+        T f;
+        if (w) {
+          f = wallV * wendland_dr(k, r) / r;
+        } else {
+          const typename R::PV pj = recP[j];
+          f = div_t(k.m, R::rho(pj, recS[j])) * wendland_dr(k, r) / r;
+        }
+        gx += f * rx;
+        gy += f * ry;
+        gz += f * rz;
+      });
+    }
+    d0[i] = coef * gx;
+    d1[i] = coef * gy;
+    if (D == 3) d2[i] = coef * gz;
+  }
+}
+
+template <int D, class T>
+__global__ void __launch_bounds__(256, kMinBlocks<T>) k_transport(Params P, DevBuffers B, KC<T> k,
+                                                                  int gated) {
+  DevScalars* sc = B.sc;
+  if (!(P.variant & kVariantTransport) || (gated && !sc->new_adv)) return;
+  transport_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+                        gridDim.x * blockDim.x);
+}
+
+// Apply the shifts: positions (FP64 state) and the position records of
+// buffer 0; the largest shift joins the displacement bound of the lists.
+template <int D, class T>
+__device__ __forceinline__ void transport_apply_range(const Params& P, const DevBuffers& B,
+                                                      DevScalars* sc, int i, int end,
+                                                      int stride) {
+  using R = Rec<D, T>;
+  const Live<T> S = live<T>(B, sc->par);
+  typename R::PV* recP = (typename R::PV*)B.recP[0];
+  const uint32_t* __restrict__ keys = B.binned;
+  const T* d0 = (const T*)B.aprior[0];
+  const T* d1 = (const T*)B.aprior[1];
+  const T* d2 = (const T*)B.aprior[2];
+  double m = 0.0;
+  for (; i < end; i += stride) {
+    const double sx = (double)d0[i], sy = (double)d1[i], sz = D == 3 ? (double)d2[i] : 0.0;
+    const double x = S.x0[i] + sx, y = S.x1[i] + sy, z = D == 3 ? S.x2[i] + sz : 0.0;
+    S.x0[i] = x;
+    S.x1[i] = y;
+    if (D == 3) S.x2[i] = z;
+    T ox, oy, oz;
+    Local<T>::enc(P, B.ctab, decode(keys[i], P), x, y, z, ox, oy, oz);
+    typename R::PV p = recP[i];
+    R::set_pos(p, ox, oy, oz);
+    recP[i] = p;
+    const double s2 = sx * sx + sy * sy + sz * sz;
+    m = s2 > m ? s2 : m;
+  }
+  m = sqrt(warp_max(m));
+  __shared__ double wm[32];
+  __syncthreads();
+  if (threadIdx.x % 32 == 0) wm[threadIdx.x / 32] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 1; q < (int)(blockDim.x / 32); ++q) m = fmax(m, wm[q]);
+    atomicMax(&sc->shift_bits, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+template <int D, class T>
+__global__ void k_transport_apply(Params P, DevBuffers B, int gated) {
+  DevScalars* sc = B.sc;
+  if (!(P.variant & kVariantTransport) || (gated && !sc->new_adv)) return;
+  transport_apply_range<D, T>(P, B, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+                              gridDim.x * blockDim.x);
 }
 
 // Viscous force: reads records P, S of buffer 0 (S carries the new rho);
@@ -1103,6 +1222,11 @@ void enqueue_advection_loops(const StageArgs& a, cudaStream_t s, int gated, cuda
     k_density_summation_fx<D><<<gl, L.block_loop, 0, s>>>(P, B, gated);
   else
     k_density_summation<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, gated);
+  if (P.variant & kVariantTransport) {
+    k_transport<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, gated);
+    k_transport_apply<D, T><<<grid_for(P.n, L.block_stream, L.blocks_stream), L.block_stream, 0,
+                              s>>>(P, B, gated);
+  }
   mark(ev, kStageViscous, s);
   k_viscous<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, gated);
 }

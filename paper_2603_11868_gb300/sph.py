@@ -29,7 +29,7 @@ SPH_F_POS, SPH_F_VEL, SPH_F_RHO, SPH_F_P, SPH_F_DRHO, SPH_F_ACC, SPH_F_APRIOR, S
     (1 << k for k in range(8))
 SPH_OPT_RECORD_DIAGNOSTICS, SPH_OPT_USE_GRAPH, SPH_OPT_BLOCK, SPH_OPT_RADIX_BITS = 1, 2, 3, 4
 SPH_OPT_NEIGHBOUR_LIST = 5
-SPH_OPT_DENSITY_RIEMANN, SPH_OPT_REINIT_BLENDED = 6, 7
+SPH_OPT_DENSITY_RIEMANN, SPH_OPT_REINIT_BLENDED, SPH_OPT_TRANSPORT_CORRECTION = 6, 7, 8
 _VECTOR_FIELDS = (SPH_F_POS, SPH_F_VEL, SPH_F_ACC, SPH_F_APRIOR)
 FIELD_NAMES = {"pos": SPH_F_POS, "vel": SPH_F_VEL, "rho": SPH_F_RHO, "p": SPH_F_P,
                "drho": SPH_F_DRHO, "acc": SPH_F_ACC, "aprior": SPH_F_APRIOR,

@@ -1,9 +1,12 @@
-"""GPU parity of the method variants (SPH_OPT_DENSITY_RIEMANN = 0: density
-relaxation with the averaged interface velocity; SPH_OPT_REINIT_BLENDED = 1:
-blended free-surface density reinitialisation) against the oracle running the
-same variant: FP64 within 1e-10 after one step and 1e-8 after 30, mixed
-accelerations within 1e-5 of max(|a_ref|, g) and densities within 1e-6 after
-one step; a batch with the variant equals one-tank contexts exactly."""
+"""GPU parity of the method variants against the oracle running the same variant:
+  - SPH_OPT_DENSITY_RIEMANN = 0: density relaxation with the averaged interface
+    velocity;
+  - SPH_OPT_REINIT_BLENDED = 1: blended free-surface density reinitialisation;
+  - SPH_OPT_TRANSPORT_CORRECTION = 1: transport-velocity (particle-shifting)
+    correction once per advection step.
+FP64 within 1e-10 after one step and 1e-8 after 30, mixed accelerations within
+1e-5 of max(|a_ref|, g) and densities within 1e-6 after one step; a batch with
+the variant equals one-tank contexts exactly."""
 import numpy as np
 import pytest
 
@@ -111,6 +114,75 @@ def test_batch_with_variants_equals_single_tanks(sph):
         _set(sph, s, False, True)
         s.step(25)
         want = s.fields("pos", "vel", "rho", "drho")
+        s.close()
+        for k in want:
+            assert np.array_equal(f[k][b.offsets[t]:b.offsets[t + 1]], want[k]), (t, k)
+    b.close()
+
+
+# --------------------------------------------------------------------------
+# transport-velocity correction (SPH_OPT_TRANSPORT_CORRECTION)
+def _run_tv(sph, O, case, precision, steps):
+    s = sph.Solver(case, precision=precision)
+    s.set_option(sph.SPH_OPT_RECORD_DIAGNOSTICS, 1)
+    s.set_option(sph.SPH_OPT_TRANSPORT_CORRECTION, 1)
+    s.step(steps)
+    got = s.fields(*FIELDS)
+    s.close()
+    o = O.Oracle.from_case(case)
+    o.set_transport_correction(True)
+    o.step(steps)
+    want = {"pos": o.field(O.POS), "vel": o.field(O.VEL), "rho": o.field(O.RHO),
+            "p": o.field(O.P), "drho": o.field(O.DRHO), "acc": o.field(O.ACC),
+            "aprior": o.field(O.APRIOR), "sigma": o.field(O.SIGMA)}
+    return got, want
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_transport_fp64_one_step(sph, O, dim):
+    case = cases.dam_break_2d() if dim == 2 else cases.dam_break_3d(dp=0.02)
+    got, want = _run_tv(sph, O, case, "fp64", 1)
+    for k in FIELDS:
+        assert rel(got[k], want[k]) <= 1e-10, (k, rel(got[k], want[k]))
+
+
+def test_transport_fp64_thirty_steps(sph, O):
+    got, want = _run_tv(sph, O, cases.dam_break_2d(), "fp64", 30)
+    for k in ("pos", "vel", "rho", "p", "drho"):
+        assert rel(got[k], want[k]) <= 1e-8, (k, rel(got[k], want[k]))
+
+
+def test_transport_mixed_one_step(sph, O):
+    case = cases.dam_break_3d(dp=0.02)
+    got, want = _run_tv(sph, O, case, "mixed", 1)
+    g = abs(case.gravity[2])
+    for k in ("acc", "aprior"):
+        err = np.abs(got[k] - want[k]).max() / max(np.abs(want[k]).max(), g)
+        assert err <= 1e-5, (k, err)
+    assert np.abs(got["pos"] - want["pos"]).max() <= 1e-6 * case.dp
+    assert rel(got["rho"], want["rho"]) <= 1e-6
+
+
+def test_transport_moves_particles_and_batches_match(sph):
+    case = cases.dam_break_2d()
+    out = []
+    for on in (0, 1):
+        s = sph.Solver(case, precision="mixed")
+        s.set_option(sph.SPH_OPT_TRANSPORT_CORRECTION, on)
+        s.step(20)
+        out.append(s.field("pos"))
+        s.close()
+    assert not np.array_equal(out[0], out[1])
+    cs = [cases.batched_tank(n, dp=0.02, seed=50 + k) for k, n in enumerate((500, 1100))]
+    b = sph.Batch(cs, precision="mixed")
+    b.set_option(sph.SPH_OPT_TRANSPORT_CORRECTION, 1)
+    b.step(20)
+    f = b.fields("pos", "vel", "rho")
+    for t, c in enumerate(cs):
+        s = sph.Solver(c, precision="mixed")
+        s.set_option(sph.SPH_OPT_TRANSPORT_CORRECTION, 1)
+        s.step(20)
+        want = s.fields("pos", "vel", "rho")
         s.close()
         for k in want:
             assert np.array_equal(f[k][b.offsets[t]:b.offsets[t + 1]], want[k]), (t, k)

@@ -42,7 +42,7 @@ SUBSTEPS = 10
 # Algorithmic (compulsory) bytes per fluid particle and launch of each stage
 # in mixed precision, 3D: every per-particle array read / written once, each
 # neighbour record read once (neighbour re-reads are meant to hit L2), plus
-# the cell offsets and the static wall records.  Derivation in the design doc.
+# the cell offsets and the static wall records.
 BYTES_PER_PARTICLE_MIXED_3D = {
     "keys": 24 + 8,                     # read x; write key, index
     "sort": 3 * (4 + 8 + 8),            # per pass: histogram read, scatter read + write

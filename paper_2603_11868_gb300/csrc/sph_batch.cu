@@ -414,6 +414,25 @@ int sph_create_batch(int n_tanks, const sph_tank* tanks, int precision,
   b->B.cell_begin = (uint32_t*)Af((size_t)total * 4);
   b->B.wall_cb = (uint32_t*)Af((size_t)total * 4);
   b->B.digit_total = (uint32_t*)Af(((size_t)1 << kMaxRadixBits) * 4);
+  // mixed path: each tank's cell-centre table of the record frame
+  std::vector<int> ctab_off(n_tanks);
+  size_t ctab_len = 0;
+  for (int t = 0; t < n_tanks; ++t) {
+    ctab_off[t] = (int)ctab_len;
+    ctab_len += (size_t)(P[t].nx + P[t].ny + P[t].nz);
+  }
+  double* ctab = nullptr;
+  int* ctab_off_dev = nullptr;
+  if (precision == SPH_MIXED) {
+    ctab = (double*)Af(ctab_len * 8);
+    ctab_off_dev = (int*)Af((size_t)n_tanks * sizeof(int));
+    if (!ctab || !ctab_off_dev) {
+      sph_batch_destroy(b);
+      return SPH_E_OOM;
+    }
+  }
+  b->A.ctab = ctab;
+  b->A.ctab_off = ctab_off_dev;
   if (!b->A.tP || !b->A.tK || !b->A.tsc || !b->A.wl_all || !b->A.wl_adv || !b->A.wl_wall ||
       !b->B.cell_begin || !b->B.wall_cb || !b->B.digit_total) {
     sph_batch_destroy(b);
@@ -426,6 +445,15 @@ int sph_create_batch(int n_tanks, const sph_tank* tanks, int precision,
   if (e == cudaSuccess)
     e = cudaMemsetAsync(b->B.digit_total, 0, ((size_t)1 << kMaxRadixBits) * 4, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->A.wl_adv, 0, sizeof(WorkList), s);
+  if (e == cudaSuccess && ctab) {
+    e = cudaMemcpyAsync(ctab_off_dev, ctab_off.data(), sizeof(int) * n_tanks,
+                        cudaMemcpyHostToDevice, s);
+    for (int t = 0; t < n_tanks && e == cudaSuccess; ++t) {
+      launch_centre_table(P[t], ctab + ctab_off[t], s);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // ctab_off is a host temporary
+  }
   if (e != cudaSuccess) {
     int rc = cuda_err(b, e, "sph_create_batch");
     sph_batch_destroy(b);

@@ -32,6 +32,13 @@ __device__ __forceinline__ KC<T> tank_kc(const BatchArgs& A, int t) {
   return ((const KC<T>*)A.tK)[t];
 }
 
+// the shared arrays with tank t's cell-centre table selected
+__device__ __forceinline__ DevBuffers tank_buffers(const BatchArgs& A, const DevBuffers& B, int t) {
+  DevBuffers Bt = B;
+  Bt.ctab = A.ctab ? A.ctab + A.ctab_off[t] : nullptr;
+  return Bt;
+}
+
 // Reorder of the listed tanks: compacted sorted slot cbase + q of a tank
 // fills its slot foff + q from the slot named by the sorted value.
 template <int D, class T>
@@ -43,13 +50,14 @@ __global__ void kb_reorder(BatchArgs A, DevBuffers B, const WorkList* wl) {
     const Params P = A.tP[t];
     const int par = A.tsc[t].par;
     const Live<T> S = live<T>(B, par), Dd = live<T>(B, par ^ 1);
+    const DevBuffers Bt = tank_buffers(A, B, t);
     const int base = wl->cbase[a];
     const int end = min(off + tile, P.n);
     for (int q = off + (int)threadIdx.x; q < end; q += blockDim.x) {
       const uint32_t key = keys[base + q] - P.cell_base;
       const int k = P.foff + q;
       A.bkey[k] = key;
-      reorder_slot<D, T>(P, B, S, Dd, k, perm[base + q], key);
+      reorder_slot<D, T>(P, Bt, S, Dd, k, perm[base + q], key);
     }
   });
 }
@@ -105,7 +113,7 @@ template <int D, class T>
 __global__ void kb_transport_apply(BatchArgs A, DevBuffers B, const WorkList* wl) {
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
     if (P.variant & kVariantTransport)
-      transport_apply_range<D, T>(P, B, A.tsc + t, i, end, blockDim.x);
+      transport_apply_range<D, T>(P, tank_buffers(A, B, t), A.tsc + t, i, end, blockDim.x);
   });
 }
 
@@ -120,7 +128,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) kb_viscous(BatchArgs A, De
 template <int D, class T>
 __global__ void kb_half1(BatchArgs A, DevBuffers B, const WorkList* wl) {
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
-    half1_range<D, T>(P, B, A.tsc + t, i, end, blockDim.x);
+    half1_range<D, T>(P, tank_buffers(A, B, t), A.tsc + t, i, end, blockDim.x);
   });
 }
 
@@ -128,7 +136,8 @@ template <int D, class T>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) kb_pressure(BatchArgs A, DevBuffers B,
                                                                   const WorkList* wl) {
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
-    pressure_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x);
+    pressure_range<D, T>(P, tank_buffers(A, B, t), tank_kc<T>(A, t), A.tsc + t, i, end,
+                         blockDim.x);
   });
 }
 

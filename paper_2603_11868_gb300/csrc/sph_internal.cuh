@@ -223,6 +223,8 @@ struct BatchArgs {
   int n_total, nw_total;
   int tiles_max;       // tiles of wl_all: bound of every fluid list (grid sizing)
   int chunks_max;      // offset chunks of every tank
+  const double* ctab;  // mixed path: every tank's cell-centre table (or null)
+  const int* ctab_off; // first entry of each tank's table
 };
 
 struct BatchStageArgs {

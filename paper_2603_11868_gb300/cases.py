@@ -4,8 +4,9 @@ This module only places particles and states case constants; it holds none of
 the method's arithmetic.  Every workload is a synthetic stand-in for the dam
 breaks the paper benchmarks (section "Performance Evaluation"): fluid on a
 lattice of spacing dp with seeded uniform jitter, static wall particles in
-layers outside each tank face, and the material / gravity constants of the
-case.
+layers outside each tank face (a tank length that is not a whole number of dp
+is rounded to one, so the wall lattice has no gap), and the material /
+gravity constants of the case.
 
 Workloads:
   dam_break_2d      2D dam break, tank 5.366 x 5.366, column 2.0 x 1.0 at the
@@ -66,17 +67,30 @@ def _axis_coords(n_in: int, length: float, dp: float, lo_idx: int, hi_idx: int) 
     """Lattice coordinates along one axis for indices lo_idx..hi_idx-1.
     Indices 0..n_in-1 sit inside the tank at (i + 1/2) dp; indices below 0 sit
     outside the low face at (i + 1/2) dp; indices n_in and above sit outside
-    the high face at length + (i - n_in + 1/2) dp.  Each face therefore gets
-    its own lattice even when length / dp is not an integer."""
+    the high face at length + (i - n_in + 1/2) dp (length = n_in dp, see
+    lattice_length)."""
     i = np.arange(lo_idx, hi_idx, dtype=np.float64)
     inside = (i + 0.5) * dp
     above = length + (i - n_in + 0.5) * dp
     return np.where(i < n_in, inside, above)
 
 
+def lattice_length(length: float, dp: float) -> float:
+    """A tank length on the particle lattice: unchanged when it is a whole
+    number of dp, else rounded to the nearest whole number of dp (at least
+    one).  A high face placed off the lattice would leave the walls normal to
+    it with a gap of dp to 2 dp next to that face, wide enough for fluid to
+    leak through the floor at the far corner once the surge arrives."""
+    n = max(1, int(round(length / dp)))
+    return length if abs(length / dp - n) <= 1e-9 else n * dp
+
+
 def tank_walls(dim: int, tank, dp: float, layers: int, open_top: bool) -> np.ndarray:
     """Wall particles: every lattice point of the tank grown by `layers` on each
-    face (not above the top face when open_top) that lies outside the tank."""
+    face (not above the top face when open_top) that lies outside the tank.
+    Each tank length is taken on the lattice first (lattice_length), so the
+    wall lattice has spacing dp everywhere."""
+    tank = [lattice_length(L, dp) for L in tank]
     n_in = [int(math.floor(L / dp + 1e-9)) for L in tank]
     ranges = []
     for k in range(dim):

@@ -148,7 +148,7 @@ class Oracle:
                 case.U_ref, case.gravity)
         if set_particles:
             if case.wall is not None and len(case.wall):
-                o.set_wall(case.wall)
+                o.set_wall(case.wall, case.wall_vel)
             o.set_fluid(case.fluid, case.vel, case.rho)
         return o
 
@@ -166,9 +166,13 @@ class Oracle:
         if rc:
             raise ValueError("oracle: set_particles failed")
 
-    def set_wall(self, pos):
+    def set_wall(self, pos, vel=None):
+        """Wall particles; vel = prescribed velocity of a sliding wall (None = rest)."""
         pos = np.ascontiguousarray(pos, dtype=np.float64)
-        if lib().osph_set_particles(self._s, 1, len(pos), _ptr(pos), None, None):
+        if vel is not None:
+            vel = np.ascontiguousarray(vel, dtype=np.float64)
+            assert vel.shape == pos.shape
+        if lib().osph_set_particles(self._s, 1, len(pos), _ptr(pos), _ptr(vel), None):
             raise ValueError("oracle: set_particles (wall) failed")
 
     def set_drho(self, drho):

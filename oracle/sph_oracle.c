@@ -52,9 +52,10 @@ struct osim {
   uint32_t *id, *key, *perm;
   long* cb; /* cell_begin, ncell + 1 entries */
 
-  /* wall, sorted once by cell */
+  /* wall, sorted once by cell; vw = prescribed velocity of a sliding wall
+   * (zero for a wall at rest; the positions never change) */
   long nw;
-  double (*xw)[3];
+  double (*xw)[3], (*vw)[3];
   uint32_t *idw, *keyw;
   long* cbw;
 
@@ -176,7 +177,7 @@ static void free_fluid(osim* s) {
 void osph_destroy(osim* s) {
   if (!s) return;
   free_fluid(s);
-  free(s->xw); free(s->idw); free(s->keyw);
+  free(s->xw); free(s->vw); free(s->idw); free(s->keyw);
   free(s->cb); free(s->cbw);
   free(s);
 }
@@ -319,9 +320,10 @@ int osph_set_particles(osim* s, int kind, long n, const double* pos,
     return 0;
   }
   if (kind == 1) {
-    free(s->xw); free(s->idw); free(s->keyw);
+    free(s->xw); free(s->vw); free(s->idw); free(s->keyw);
     s->nw = n;
     s->xw = (double(*)[3])xcalloc((size_t)n, sizeof(double[3]));
+    s->vw = (double(*)[3])xcalloc((size_t)n, sizeof(double[3]));
     s->idw = (uint32_t*)xcalloc((size_t)n, sizeof(uint32_t));
     s->keyw = (uint32_t*)xcalloc((size_t)n, sizeof(uint32_t));
     kv_t* a = (kv_t*)xcalloc((size_t)n, sizeof(kv_t));
@@ -336,7 +338,10 @@ int osph_set_particles(osim* s, int kind, long n, const double* pos,
     qsort(a, (size_t)n, sizeof(kv_t), cmp_kv);
     for (long k = 0; k < n; ++k) {
       uint32_t i = a[k].idx;
-      for (int c = 0; c < 3; ++c) s->xw[k][c] = c < d ? pos[(long)i * d + c] : 0.0;
+      for (int c = 0; c < 3; ++c) {
+        s->xw[k][c] = c < d ? pos[(long)i * d + c] : 0.0;
+        s->vw[k][c] = (c < d && vel) ? vel[(long)i * d + c] : 0.0;
+      }
       s->idw[k] = i;
       s->keyw[k] = a[k].key;
     }
@@ -433,8 +438,13 @@ void osph_set_variant(osim* s, int density_riemann, int reinit_blended) {
 
 /* Viscous force (once per advection step), SPHinXsys form:
  *   a_prior_i = g + (2 mu / rho_i) sum_j V_j (v_i - v_j) W'(r_ij) / (r_ij + 0.01 h)
- * with V_j = m / rho_j for fluid, and for static wall particles V_w = dp^d and
- * v_w = 0.  Self is excluded (r = 0 contributes nothing). */
+ * with V_j = m / rho_j for fluid.  A wall particle (V_w = dp^d) enters with
+ * the mirrored velocity v_R = 2 v_w - v_i of the Riemann wall state in place
+ * of v_j (v_w its prescribed velocity, 0 at rest), so its pair term carries
+ * v_i - v_R = 2 (v_i - v_w): the velocity interpolated half-way between the
+ * fluid particle and its image is v_w, the no-slip condition at the wall
+ * surface (reading; the simpler v_j = v_w gives the wall half that weight and
+ * lets the fluid slip).  Self is excluded (r = 0 contributes nothing). */
 void osph_viscous(osim* s) {
   const double r2max = 4.0 * s->h * s->h;
   const double eps = 0.01 * s->h;
@@ -456,7 +466,7 @@ void osph_viscous(osim* s) {
         if (r2 >= r2max) continue;
         double r = sqrt(r2);
         double coef = s->V * osph_dW(s->dim, s->h, r) / (r + eps);
-        for (int k = 0; k < 3; ++k) a[k] += coef * s->v[i][k];
+        for (int k = 0; k < 3; ++k) a[k] += coef * (2.0 * (s->v[i][k] - s->vw[w][k]));
       }
     }
     for (int k = 0; k < 3; ++k)
@@ -532,15 +542,23 @@ void osph_half1(osim* s, double dt) {
  * For the pair (i, j): e_ij = (x_i - x_j) / r_ij, U_L = -v_i.e_ij,
  * U_R = -v_j.e_ij, and
  *   a_i = -(2 / rho_i) sum_j P*_ij V_j W'(r_ij) e_ij,   V_j = m / rho_j.
- * Wall particle w (static, v_w = 0) supplies a mirrored right state
- * (reading: pressure extrapolated along gravity, density from the inverse
- * equation of state and volume from that density, as in Adami, Hu & Adams,
- * J. Comput. Phys. 231 (2012)):
+ * Wall particle w (fixed position, prescribed velocity v_w: 0 at rest, or
+ * the velocity of a wall sliding along itself, so a_w = 0) supplies a
+ * mirrored right state (reading: pressure extrapolated along gravity,
+ * density from the inverse equation of state and volume from that density,
+ * as in Adami, Hu & Adams, J. Comput. Phys. 231 (2012)):
  *   p_w = p_i + rho_i (x_w - x_i).g,  rho_w = rho0 + p_w / c0^2,
- *   v_R = 2 v_w - v_i = -v_i,  V_w = m / rho_w.
+ *   v_R = 2 v_w - v_i,  V_w = m / rho_w.
  * Then v_i += dt (a_i + a_prior_i). */
 /* Pressure acceleration of storage slot i with the given density and
  * pressure arrays (indexed by storage slot). */
+/* v_R . e for the mirrored wall state v_R = 2 v_w - v_i */
+static double mirror_dot(const double vi[3], const double vw[3], const double e[3]) {
+  double d = 0.0;
+  for (int k = 0; k < 3; ++k) d += (2.0 * vw[k] - vi[k]) * e[k];
+  return d;
+}
+
 static void pressure_acc_of(const osim* s, long i, const double* rho, const double* p,
                             double out[3]) {
   const double r2max = 4.0 * s->h * s->h;
@@ -574,7 +592,7 @@ static void pressure_acc_of(const osim* s, long i, const double* rho, const doub
       double pw = p[i] + rho[i] * gdot;
       double rhow = s->rho0 + pw / (c0 * c0);
       double UL = -(s->v[i][0] * e[0] + s->v[i][1] * e[1] + s->v[i][2] * e[2]);
-      double UR = -UL;
+      double UR = -mirror_dot(s->v[i], s->vw[w], e);
       double Ps, Us;
       osph_riemann(p[i], pw, rho[i], rhow, UL, UR, c0, &Ps, &Us);
       double f = Ps * (s->m / rhow) * osph_dW(s->dim, s->h, r);
@@ -645,7 +663,7 @@ void osph_half2(osim* s, double dt) {
         double pw = s->p[i] + s->rho[i] * gdot;
         double rhow = s->rho0 + pw / (c0 * c0);
         double UL = -(s->v[i][0] * e[0] + s->v[i][1] * e[1] + s->v[i][2] * e[2]);
-        double UR = -UL;
+        double UR = -mirror_dot(s->v[i], s->vw[w], e);
         double Ps, Us;
         osph_riemann(s->p[i], pw, s->rho[i], rhow, UL, UR, c0, &Ps, &Us);
         if (!s->density_riemann) Us = 0.5 * (UL + UR);

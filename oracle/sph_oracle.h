@@ -51,8 +51,11 @@ osim* osph_create(int dim, const double lo[3], const double hi[3], double dp,
                   const double g[3]);
 void osph_destroy(osim* s);
 
-/* kind 0 = fluid, 1 = wall.  vel / rho may be NULL (0 / rho0).  Wall velocity
- * and density are ignored (static wall).  Returns 0 on success. */
+/* kind 0 = fluid, 1 = wall.  vel / rho may be NULL (0 / rho0).  A wall's
+ * vel is its prescribed velocity (NULL = at rest): the wall particles keep
+ * their positions, so a nonzero velocity models a wall sliding along itself
+ * (a lid, a belt, a Couette plate); it enters the mirrored Riemann state and
+ * the viscous force.  Wall density is ignored.  Returns 0 on success. */
 int osph_set_particles(osim* s, int kind, long n, const double* pos,
                        const double* vel, const double* rho);
 /* method variants: density_riemann = 1 (default) takes the Riemann U* in the

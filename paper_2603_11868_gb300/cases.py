@@ -20,6 +20,12 @@ Workloads:
   uniform_cube      N particles uniform in the unit cube, h chosen for a mean
                     of `neighbours` particles within 2h.
   batched_tanks     many independent 2D dam-break tanks of log-uniform size.
+  sliding_lid_channel_2d
+                    closed 2D channel, length 4 x height 1, completely filled,
+                    its top wall sliding along x at U = 1 (no gravity,
+                    Re = U H / nu = 10): far from the ends the steady flow is
+                    the zero-net-flux Couette-Poiseuille profile
+                    u = U eta (3 eta - 2), eta = y / H.
   dam_break_obstacle_3d
                     3D dam break whose surge hits a box obstacle on the floor
                     (the kind of test the paper's second workload is): tank
@@ -53,6 +59,7 @@ class Case:
     vel: np.ndarray | None = None    # (n, dim) or None (rest)
     rho: np.ndarray | None = None    # (n,) or None (rho0)
     meta: dict = field(default_factory=dict)
+    wall_vel: np.ndarray | None = None  # (nw, dim) prescribed wall velocity, or None (rest)
 
     @property
     def n(self) -> int:
@@ -257,3 +264,31 @@ def dam_break_obstacle_3d(dp: float = 0.02, seed: int = 7, jitter: float = 0.01,
                 (0.0, 0.0, -g), lo, hi, fluid, wall,
                 meta=dict(tank=tank, column=column, box=box, box_x=box_x, layers=layers,
                           seed=seed, n_obstacle=len(obstacle)))
+
+
+def sliding_lid_channel_2d(dp: float = 0.05, length: float = 4.0, height: float = 1.0,
+                           U: float = 1.0, nu: float = 0.1, c0: float = 20.0,
+                           compression: float = 1.004, layers: int = 4,
+                           rho0: float = 1.0) -> Case:
+    """Closed 2D channel filled with fluid at rest; the wall layers above the
+    top face (corners included) slide along x at U, the others rest.  The
+    fluid lattice is `compression` times finer than dp, centred in the
+    channel, so the summed density starts above rho0 everywhere: the
+    background pressure c0^2 rho0 (compression^2 - 1) keeps the pressure
+    positive along the channel, where the free-surface clamp of the density
+    summation would otherwise flatten the low-pressure half."""
+    nx, ny = int(round(length / dp)), int(round(height / dp))
+    dpf = dp / compression
+    xs = 0.5 * (length - nx * dpf) + (np.arange(nx) + 0.5) * dpf
+    ys = 0.5 * (height - ny * dpf) + (np.arange(ny) + 0.5) * dpf
+    Y, X = np.meshgrid(ys, xs, indexing="ij")
+    fluid = np.ascontiguousarray(np.stack([X.ravel(), Y.ravel()], axis=1))
+    tank = (length, height)
+    wall = tank_walls(2, tank, dp, layers, open_top=False)
+    wall_vel = np.zeros_like(wall)
+    wall_vel[wall[:, 1] > height, 0] = U
+    lo, hi = _domain(2, tank, dp, layers, 0.0)
+    return Case("sliding_lid_channel_2d", 2, dp, 1.3 * dp, rho0, c0, nu * rho0, c0 / 10.0,
+                (0.0, 0.0), lo, hi, fluid, wall,
+                meta=dict(tank=tank, U=U, H=height, L=length, nu=nu, layers=layers),
+                wall_vel=np.ascontiguousarray(wall_vel))

@@ -12,10 +12,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
 PIN_FILES = ["tests/test_oracle_kernel.py", "tests/test_oracle_neighbours.py",
-             "tests/test_oracle_physics.py", "tests/test_oracle_variants.py"]
+             "tests/test_oracle_physics.py", "tests/test_oracle_variants.py",
+             "tests/test_oracle_walls.py"]
 
-_WALL_P = ("double UR = -UL;\n      double Ps, Us;\n      osph_riemann(p[i], pw, rho[i], "
-           "rhow, UL, UR, c0, &Ps, &Us);\n      double f")
 MUTATIONS = {
     "riemann_ustar_sign": ("*Ustar = 0.5 * (UL + UR) + (pL - pR)",
                            "*Ustar = 0.5 * (UL + UR) + (pR - pL)"),
@@ -27,7 +26,14 @@ MUTATIONS = {
                            "for (int k = 0; k < 3; ++k) out[k] = 2.0 / rho[i] * a[k];"),
     "wall_gravity_sign": ("gdot += (s->xw[w][k] - s->x[i][k]) * s->g[k];",
                           "gdot += (s->x[i][k] - s->xw[w][k]) * s->g[k];"),
-    "wall_mirror_velocity": (_WALL_P, _WALL_P.replace("double UR = -UL;", "double UR = UL;")),
+    "wall_mirror_velocity": ("d += (2.0 * vw[k] - vi[k]) * e[k];",
+                             "d += (2.0 * vw[k] + vi[k]) * e[k];"),
+    "wall_mirror_factor": ("d += (2.0 * vw[k] - vi[k]) * e[k];",
+                           "d += (vw[k] - vi[k]) * e[k];"),
+    "wall_viscous_mirror": ("a[k] += coef * (2.0 * (s->v[i][k] - s->vw[w][k]));",
+                            "a[k] += coef * (s->v[i][k] - s->vw[w][k]);"),
+    "wall_viscous_velocity_sign": ("a[k] += coef * (2.0 * (s->v[i][k] - s->vw[w][k]));",
+                                   "a[k] += coef * (2.0 * (s->v[i][k] + s->vw[w][k]));"),
     "continuity_sign": ("sum += (s->m / s->rho[j]) * osph_dW(s->dim, s->h, r) * (UL - Us);",
                         "sum += (s->m / s->rho[j]) * osph_dW(s->dim, s->h, r) * (Us - UL);"),
     "viscous_operands": ("a[k] += coef * (s->v[i][k] - s->v[j][k]);",

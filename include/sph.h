@@ -13,9 +13,9 @@
  * the paper's cell-linked list, particle sorting and direct search (section
  * "Cell linked-list, direct search and sorting") driving the weakly
  * compressible SPH interactions: Wendland C2 kernel, density summation,
- * viscous force, Riemann-based pressure and density relaxation, static wall
- * particles with a mirrored Riemann state, and the dual advection / acoustic
- * time-step criteria.
+ * viscous force, Riemann-based pressure and density relaxation, wall
+ * particles (at rest or sliding) with a mirrored Riemann state, and the dual
+ * advection / acoustic time-step criteria.
  *
  * Conventions (all entry points):
  *  - Every call returns an sph_status (0 = SPH_OK) unless stated otherwise.
@@ -152,9 +152,17 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
  *   SPH_FLUID: vel (n * dim) and rho (n) may be NULL (rest, rho0).  Resets
  *     time and step counters, the carried density rate and the schedule; the
  *     particles are binned and sorted once.  User order is the given order.
- *   SPH_WALL: static wall particles; vel and rho must be NULL.  Sorted once.
+ *   SPH_WALL: wall particles, which keep their positions; sorted once.  vel
+ *     is NULL (walls at rest) or the prescribed velocity of each wall
+ *     particle (n * dim): a wall sliding along itself (a lid, a belt, a
+ *     Couette plate), whose lattice is unchanged by the motion.  The velocity
+ *     enters the mirrored wall state v_R = 2 v_w - v_i of the pressure and
+ *     density relaxation and the viscous force, which takes v_i - v_R =
+ *     2 (v_i - v_w) for a wall neighbour; the wall pressure extrapolation is
+ *     unchanged (no wall acceleration).  rho must be NULL.
  * n may be 0 and must be below 2^25.  Fails with SPH_E_INVALID on a NULL pos
- * with n > 0 or on too many particles. */
+ * with n > 0, on too many particles, on a wall density or on a non-finite
+ * wall velocity. */
 int sph_set_particles(sph_ctx* ctx, int kind, size_t n, const double* pos, const double* vel,
                       const double* rho);
 
@@ -361,8 +369,9 @@ int sph_create_batch(int n_tanks, const sph_tank* tanks, int precision,
 /* Sets the particles of one kind for every tank: counts[t] particles for
  * tank t (counts has n_tanks entries, a count may be 0), pos holds
  * sum(counts) * dim doubles, tank 0's particles first (vel, rho as
- * sph_set_particles: NULL = zero velocity / the tank's rho0; walls take
- * positions only).  The total of each kind must stay below 2^25. */
+ * sph_set_particles: NULL = zero velocity / the tank's rho0; walls may take
+ * prescribed sliding velocities, no density).  The total of each kind must
+ * stay below 2^25. */
 int sph_batch_set_particles(sph_batch* b, int kind, const size_t* counts, const double* pos,
                             const double* vel, const double* rho);
 

@@ -482,9 +482,16 @@ int sph_batch_set_particles(sph_batch* b, int kind, const size_t* counts, const 
   if (total > 0 && !pos) return set_err(b, SPH_E_INVALID, "pos is NULL");
   if (kind != SPH_FLUID && kind != SPH_WALL)
     return set_err(b, SPH_E_INVALID, "unknown particle kind");
-  if (kind == SPH_WALL && (vel || rho))
-    return set_err(b, SPH_E_INVALID, "wall particles take positions only");
+  if (kind == SPH_WALL && rho) return set_err(b, SPH_E_INVALID, "wall particles take no density");
   const int d = b->dim;
+  // prescribed (sliding) wall velocities: the walls read them only if one is nonzero
+  bool moving = false;
+  if (kind == SPH_WALL && vel) {
+    for (size_t q = 0; q < total * (size_t)d; ++q) {
+      if (!std::isfinite(vel[q])) return set_err(b, SPH_E_INVALID, "wall velocity is not finite");
+      moving = moving || vel[q] != 0.0;
+    }
+  }
   cudaStream_t s = b->mem.stream;
   int rc = enter(b);
   if (rc) return rc;
@@ -498,6 +505,10 @@ int sph_batch_set_particles(sph_batch* b, int kind, const size_t* counts, const 
     } else {
       b->P[t].nw = (int)counts[t];
       b->P[t].woff = (int)off;
+      // every tank reads the (possibly zero) velocities of its walls: with
+      // v_w = 0 the wall terms are bit-identical to those of walls at rest
+      b->P[t].variant = moving ? (b->P[t].variant | kVariantMovingWall)
+                               : (b->P[t].variant & ~kVariantMovingWall);
     }
     off += counts[t];
   }
@@ -566,6 +577,7 @@ int sph_batch_set_particles(sph_batch* b, int kind, const size_t* counts, const 
   B.wallP = B.wall_id = nullptr;
   B.wall_xyz = nullptr;
   B.wallI = nullptr;
+  B.wall_vel = nullptr;
   if (n == 0) {
     CKB(cudaMemsetAsync(B.wall_cb, 0, (size_t)b->total_cells * 4, s));
     CKB(cudaStreamSynchronize(s));
@@ -577,9 +589,11 @@ int sph_batch_set_particles(sph_batch* b, int kind, const size_t* counts, const 
   B.wall_id = (uint32_t*)Al(n * 4);
   B.wall_xyz = (double*)Al(n * 3 * 8);
   B.wallI = b->precision == SPH_MIXED ? Al(n * (d == 3 ? 16 : 8)) : nullptr;
+  B.wall_vel = moving ? Al(n * (d == 3 ? 4 : 2) * ts) : nullptr;
   std::vector<Block> tmp;
   DevBuffers W = B;
-  W.io = (double*)b->mem.get(n * 3 * 8, tmp);
+  // staging: positions SoA (3 n), then the velocities SoA (3 n) when moving
+  W.io = (double*)b->mem.get(n * (moving ? 6 : 3) * 8, tmp);
   for (int p = 0; p < 2; ++p) {
     W.keys[p] = (uint32_t*)b->mem.get(n * 4, tmp);
     W.vals[p] = (uint32_t*)b->mem.get(n * 4, tmp);
@@ -588,11 +602,15 @@ int sph_batch_set_particles(sph_batch* b, int kind, const size_t* counts, const 
   W.tile_hist = (uint32_t*)b->mem.get(tiles * ((size_t)1 << kMaxRadixBits) * 4, tmp);
   const bool ok = B.wallP && B.wall_id && B.wall_xyz && W.io && W.keys[0] && W.keys[1] &&
                   W.vals[0] && W.vals[1] && W.tile_hist &&
-                  (b->precision != SPH_MIXED || B.wallI);
+                  (b->precision != SPH_MIXED || B.wallI) && (!moving || B.wall_vel);
   if (!ok) {
     b->mem.release(tmp);
     b->mem.release(b->wall_blocks);
-    for (int t = 0; t < b->T; ++t) b->P[t].nw = 0;
+    B.wall_vel = nullptr;
+    for (int t = 0; t < b->T; ++t) {
+      b->P[t].nw = 0;
+      b->P[t].variant &= ~kVariantMovingWall;
+    }
     b->NW = 0;
     upload_tables(b);
     return set_err(b, SPH_E_OOM, "device allocation failed (wall buffers)");
@@ -601,6 +619,13 @@ int sph_batch_set_particles(sph_batch* b, int kind, const size_t* counts, const 
   double* soa[3] = {W.io, W.io + n, W.io + 2 * n};
   if (d == 2) CKB(cudaMemsetAsync(W.io + 2 * n, 0, n * 8, s));
   launch_deinterleave(B.wall_xyz, (int)n, d, soa, s);
+  if (moving) {
+    // the AoS scratch is free again once the positions are deinterleaved
+    CKB(cudaMemcpyAsync(B.wall_xyz, vel, n * d * 8, cudaMemcpyHostToDevice, s));
+    double* vsoa[3] = {W.io + 3 * n, W.io + 4 * n, W.io + 5 * n};
+    if (d == 2) CKB(cudaMemsetAsync(W.io + 5 * n, 0, n * 8, s));
+    launch_deinterleave(B.wall_xyz, (int)n, d, vsoa, s);
+  }
   BatchStageArgs a = args(b);
   a.B = W;
   if (b->precision == SPH_FP64)

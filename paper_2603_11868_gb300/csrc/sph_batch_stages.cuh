@@ -65,7 +65,7 @@ __global__ void kb_reorder(BatchArgs A, DevBuffers B, const WorkList* wl) {
 template <int D, class T>
 __global__ void kb_wall_gather(BatchArgs A, DevBuffers B, const double* __restrict__ ux,
                                const double* __restrict__ uy, const double* __restrict__ uz,
-                               double* wx, double* wy, double* wz) {
+                               double* wx, double* wy, double* wz, const double* uv) {
   const uint32_t* __restrict__ perm = B.vals[B.sorted_buf];
   const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
   const WorkList* wl = A.wl_wall;
@@ -75,8 +75,8 @@ __global__ void kb_wall_gather(BatchArgs A, DevBuffers B, const double* __restri
     const int base = wl->cbase[a];
     const int end = min(off + tile, P.nw);
     for (int q = off + (int)threadIdx.x; q < end; q += blockDim.x)
-      wall_slot<D, T>(P, B, ux, uy, uz, wx, wy, wz, P.woff + q, perm[base + q],
-                      keys[base + q] - P.cell_base);
+      wall_slot<D, T>(P, B, ux, uy, uz, wx, wy, wz, uv, (size_t)A.nw_total, P.woff + q,
+                      perm[base + q], keys[base + q] - P.cell_base);
   });
 }
 
@@ -231,8 +231,10 @@ void enqueue_batch_wall_setup_t(const BatchStageArgs& a, cudaStream_t s) {
                          1 << L.radix_bits, clamp_grid(wtiles, L.blocks_stream), 256, s);
   B.sorted_buf = launch_radix_sort(L, keys, vals, A.nw_total, B.tile_hist, B.digit_total,
                                    nullptr, 0, s);
+  // velocity staging after the positions: io + 3 nw (x | y | z)
+  const double* uv = B.wall_vel ? B.io + 3 * nw : nullptr;
   kb_wall_gather<D, T><<<clamp_grid(wtiles, L.blocks_stream), 256, 0, s>>>(
-      A, B, io[0][0], io[0][1], io[0][2], wx, wy, wz);
+      A, B, io[0][0], io[0][1], io[0][2], wx, wy, wz, uv);
   launch_batch_cell_offsets(A, A.wl_wall, 1, clamp_grid(A.chunks_max, L.sms * 8),
                             B.keys[B.sorted_buf], B.wall_cb, 0, s);
 }

@@ -471,7 +471,16 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
     return leave(c);
   }
   if (kind == SPH_WALL) {
-    if (vel || rho) return set_err(c, SPH_E_INVALID, "wall particles take positions only");
+    if (rho) return set_err(c, SPH_E_INVALID, "wall particles take no density");
+    // a prescribed (sliding) velocity: the walls read it only if one is nonzero
+    bool moving = false;
+    if (vel) {
+      for (size_t q = 0; q < n * (size_t)d; ++q) {
+        if (!std::isfinite(vel[q]))
+          return set_err(c, SPH_E_INVALID, "wall velocity is not finite");
+        moving = moving || vel[q] != 0.0;
+      }
+    }
     int rc = enter(c);
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));
@@ -479,6 +488,8 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
     dev_free_list(c, c->wall_blocks);
     c->cap_nw = 0;
     c->P.nw = (int)n;
+    c->B.wall_vel = nullptr;
+    c->P.variant &= ~kVariantMovingWall;
     if (n == 0) {
       c->B.wallP = nullptr;
       c->B.wall_id = nullptr;
@@ -494,9 +505,11 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
     c->B.wall_id = (uint32_t*)A(n * 4);
     c->B.wall_xyz = (double*)A(n * 3 * 8);
     c->B.wallI = c->precision == SPH_MIXED ? A(n * (d == 3 ? 16 : 8)) : nullptr;
+    c->B.wall_vel = moving ? A(n * (d == 3 ? 4 : 2) * ts) : nullptr;
     std::vector<Block> tmp;
     DevBuffers W = c->B;
-    W.io = (double*)dev_alloc(c, n * 3 * 8, tmp);
+    // staging: positions SoA (3 n), then the velocities SoA (3 n) when moving
+    W.io = (double*)dev_alloc(c, n * (moving ? 6 : 3) * 8, tmp);
     for (int p = 0; p < 2; ++p) {
       W.keys[p] = (uint32_t*)dev_alloc(c, n * 4, tmp);
       W.vals[p] = (uint32_t*)dev_alloc(c, n * 4, tmp);
@@ -504,12 +517,13 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
     const size_t tiles = (n + kSortTile - 1) / kSortTile;
     W.tile_hist = (uint32_t*)dev_alloc(c, tiles * ((size_t)1 << kMaxRadixBits) * 4, tmp);
     bool ok = c->B.wallP && c->B.wall_id && c->B.wall_xyz && W.io && W.keys[0] && W.keys[1] &&
-              (c->precision != SPH_MIXED || c->B.wallI) &&
+              (c->precision != SPH_MIXED || c->B.wallI) && (!moving || c->B.wall_vel) &&
               W.vals[0] && W.vals[1] && W.tile_hist;
     if (!ok) {
       dev_free_list(c, tmp);
       dev_free_list(c, c->wall_blocks);
       c->P.nw = 0;
+      c->B.wall_vel = nullptr;
       return set_err(c, SPH_E_OOM, "device allocation failed (wall buffers)");
     }
     // host AoS -> wall_xyz (scratch here) -> SoA [x | y | z] staging
@@ -517,6 +531,14 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
     double* soa[3] = {W.io, W.io + n, W.io + 2 * n};
     if (d == 2) CK(cudaMemsetAsync(W.io + 2 * n, 0, n * 8, c->stream));
     launch_deinterleave(c->B.wall_xyz, (int)n, d, soa, c->stream);
+    if (moving) {
+      // the AoS scratch is free again once the positions are deinterleaved
+      CK(cudaMemcpyAsync(c->B.wall_xyz, vel, n * d * 8, cudaMemcpyHostToDevice, c->stream));
+      double* vsoa[3] = {W.io + 3 * n, W.io + 4 * n, W.io + 5 * n};
+      if (d == 2) CK(cudaMemsetAsync(W.io + 5 * n, 0, n * 8, c->stream));
+      launch_deinterleave(c->B.wall_xyz, (int)n, d, vsoa, c->stream);
+      c->P.variant |= kVariantMovingWall;
+    }
     StageArgs a = args(c);
     a.B = W;
     if (c->precision == SPH_FP64)

@@ -54,6 +54,7 @@ enum {
 constexpr int kVariantNoRiemann = 1;
 constexpr int kVariantBlended = 2;
 constexpr int kVariantTransport = 4;  // transport-velocity correction each advection step
+constexpr int kVariantMovingWall = 8;  // walls with a prescribed (sliding) velocity
 
 // error flag bits (sticky, device)
 constexpr int kFlagOutOfDomain = 1;
@@ -83,7 +84,8 @@ struct Params {
   // method variants: kVariantNoRiemann -> the density relaxation takes the
   // average of the two states instead of the Riemann U*; kVariantBlended ->
   // blended free-surface density reinitialisation instead of the clamp;
-  // kVariantTransport -> transport-velocity correction after the summation
+  // kVariantTransport -> transport-velocity correction after the summation;
+  // kVariantMovingWall -> the wall terms read the prescribed wall velocity
   int variant;
   // position of this tank in the arrays of a batch (all zero for one tank):
   // first fluid slot, first wall slot, first entry of its cell offsets
@@ -168,6 +170,7 @@ struct DevBuffers {
   uint32_t* wall_id;
   double* wall_xyz;  // sorted wall positions, double SoA (3 nw)
   void* wallI;       // mixed mode: wall fixed-point offsets (int4 / int2)
+  void* wall_vel;    // prescribed wall velocity (T4 / T2, sorted), null when every wall rests
   DevScalars* sc;
   double* io;  // staging, n * dim doubles (also wall staging)
   uint32_t* u32_io;

@@ -555,6 +555,16 @@ struct PairGeo {
   }
 };
 
+// v_w . e for wall particle j with a prescribed velocity (kVariantMovingWall):
+// a wall sliding along itself keeps its position; its velocity enters the
+// mirrored state v_R = 2 v_w - v_i, so U_R = -U_L - 2 v_w . e.
+template <int D, class T>
+__device__ __forceinline__ T wall_vel_dot(const DevBuffers& B, int j, T ex, T ey, T ez) {
+  using WR = WallRec<D, T>;
+  const typename WR::WV vw = ((const typename WR::WV*)B.wall_vel)[j];
+  return vw.x * ex + vw.y * ey + WR::z(vw) * ez;
+}
+
 // List build (right after the rebuild, positions = binned positions): one
 // direct search per particle that records the candidates closer than
 // 2h + skin.  The membership test runs in the pair type on the loop records;
@@ -851,8 +861,10 @@ __global__ void k_transport_apply(Params P, DevBuffers B, int gated) {
 }
 
 // Viscous force: reads records P, S of buffer 0 (S carries the new rho);
-// writes a_prior = g + viscous acceleration.  Positions are those of the
-// rebuild, so the lists are always usable here (unless one overflowed).
+// writes a_prior = g + viscous acceleration.  A wall particle enters with the
+// mirrored velocity 2 v_w - v_i, so its pair term carries 2 (v_i - v_w) (the
+// factor folded into its volume).  Positions are those of the rebuild, so the
+// lists are always usable here (unless one overflowed).
 template <int D, class T>
 __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers& B, const KC<T>& k,
                                               DevScalars* sc, int i, int end, int stride) {
@@ -864,7 +876,8 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
   T* ap0 = (T*)B.aprior[0];
   T* ap1 = (T*)B.aprior[1];
   T* ap2 = (T*)B.aprior[2];
-  const T wallV = (T)P.V;
+  const T wallV2 = (T)(2.0 * P.V);
+  const bool moving = (P.variant & kVariantMovingWall) != 0;
   for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
     const typename R::PV pi = recP[i];
@@ -880,10 +893,18 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
       if (!(r2 < k.r2max) || (!w && j == i)) return;
       const T r = sqrt(r2);
       if (w) {
-        const T coef = wallV * wendland_dr(k, r) / (r + k.eps);
-        ax += coef * vxi;
-        ay += coef * vyi;
-        az += coef * vzi;
+        const T coef = wallV2 * wendland_dr(k, r) / (r + k.eps);
+        T ux = vxi, uy = vyi, uz = vzi;
+        if (moving) {
+          using WR = WallRec<D, T>;
+          const typename WR::WV vw = ((const typename WR::WV*)B.wall_vel)[j];
+          ux -= vw.x;
+          uy -= vw.y;
+          uz -= WR::z(vw);
+        }
+        ax += coef * ux;
+        ay += coef * uy;
+        az += coef * uz;
       } else {
         const typename R::PV pj = recP[j];
         const typename R::SV sj = recS[j];
@@ -999,6 +1020,7 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
         p_j = p_i + rho_i * gdot;
         rho_j = k.rho0 + p_j * k.inv_c0sq;
         UR = -UL;
+        if (P.variant & kVariantMovingWall) UR -= T(2) * wall_vel_dot<D, T>(B, j, ex, ey, ez);
       } else {
         UR = -(R::vx(pj, sj) * ex + R::vy(pj, sj) * ey + R::vz(pj, sj) * ez);
         p_j = R::pres(pj, sj);
@@ -1111,8 +1133,9 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
         const T pw_ = p_i + rho_i * gdot;
         const T rho_w = k.rho0 + pw_ * k.inv_c0sq;
         const T rbar = k.half * (rho_i + rho_w);
-        // U_R = -U_L, so (U_L + U_R)/2 = 0
-        const T Us = k.riemann * div_t(p_i - pw_, T(2) * rbar * k.c0);
+        // U_R = -U_L - 2 v_w.e, so (U_L + U_R)/2 = -v_w.e (0 at rest)
+        T Us = k.riemann * div_t(p_i - pw_, T(2) * rbar * k.c0);
+        if (P.variant & kVariantMovingWall) Us -= wall_vel_dot<D, T>(B, j, ex, ey, ez);
         sum += div_t(k.m, rho_w) * wendland_dr(k, r) * (UL - Us);
       } else {
         const T UR = -(R::vx(pj, sj) * ex + R::vy(pj, sj) * ey + R::vz(pj, sj) * ez);
@@ -1143,15 +1166,18 @@ __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) k_density_relax(Params
 }
 
 // Wall setup: gather sorted wall positions (double SoA for the parity kernel,
-// records for the loops) and ids from the unsorted staging copy.
-// Slot k of the sorted walls takes staging entry j, binned in cell `key` of
-// its tank's grid; (wx, wy, wz) is the double SoA of all sorted walls.
+// records for the loops), ids and, for moving walls, the prescribed
+// velocities from the unsorted staging copy.  Slot k of the sorted walls takes
+// staging entry j, binned in cell `key` of its tank's grid; (wx, wy, wz) is
+// the double SoA of all sorted walls; uv the velocity SoA staging (x | y | z,
+// vstride apart), read only when wall_vel is set.
 template <int D, class T>
 __device__ __forceinline__ void wall_slot(const Params& P, const DevBuffers& B,
                                           const double* __restrict__ ux,
                                           const double* __restrict__ uy,
                                           const double* __restrict__ uz, double* wx, double* wy,
-                                          double* wz, int k, uint32_t j, uint32_t key) {
+                                          double* wz, const double* __restrict__ uv,
+                                          size_t vstride, int k, uint32_t j, uint32_t key) {
   using WR = WallRec<D, T>;
   typename WR::WV* out = (typename WR::WV*)B.wallP;
   double x = ux[j], y = uy[j], z = D == 3 ? uz[j] : 0.0;
@@ -1163,6 +1189,9 @@ __device__ __forceinline__ void wall_slot(const Params& P, const DevBuffers& B,
   const Cell ck = decode(key, P);
   Local<T>::enc(P, B.ctab, ck, x, y, z, ox, oy, oz);
   out[k] = WR::make(ox, oy, oz);
+  if (B.wall_vel)
+    ((typename WR::WV*)B.wall_vel)[k] =
+        WR::make((T)uv[j], (T)uv[vstride + j], D == 3 ? (T)uv[2 * vstride + j] : T(0));
   if constexpr (Local<T>::kLocal)
     ((typename FxRec<D>::V*)B.wallI)[k] = fx_encode<D>(P, ck, x, y, z);
 }
@@ -1170,11 +1199,11 @@ __device__ __forceinline__ void wall_slot(const Params& P, const DevBuffers& B,
 template <int D, class T>
 __global__ void k_wall_gather(Params P, DevBuffers B, const double* __restrict__ ux,
                               const double* __restrict__ uy, const double* __restrict__ uz,
-                              double* wx, double* wy, double* wz) {
+                              double* wx, double* wy, double* wz, const double* uv) {
   const uint32_t* perm = B.vals[B.sorted_buf];
   const uint32_t* keys = B.keys[B.sorted_buf];
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.nw; k += gridDim.x * blockDim.x)
-    wall_slot<D, T>(P, B, ux, uy, uz, wx, wy, wz, k, perm[k], keys[k]);
+    wall_slot<D, T>(P, B, ux, uy, uz, wx, wy, wz, uv, (size_t)P.nw, k, perm[k], keys[k]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1286,8 +1315,10 @@ void enqueue_wall_setup_t(const StageArgs& a, cudaStream_t s) {
   uint32_t* vals[2] = {B.vals[0], B.vals[1]};
   launch_cell_keys(P, L, xs, keys[0], vals[0], P.nw, nullptr, 0, B.digit_total, s);
   B.sorted_buf = launch_radix_sort(L, keys, vals, P.nw, B.tile_hist, B.digit_total, B.sc, 0, s);
+  // velocity staging after the positions: io + 3 nw (x | y | z)
+  const double* uv = B.wall_vel ? B.io + 3 * (size_t)P.nw : nullptr;
   k_wall_gather<D, T><<<grid_for(P.nw, 256, L.blocks_stream), 256, 0, s>>>(P, B, ux, uy, uz, wx,
-                                                                          wy, wz);
+                                                                          wy, wz, uv);
   launch_cell_offsets(B.keys[B.sorted_buf], P.nw, P.ncell, B.wall_cb, B.sc, 0, 0, s);
 }
 

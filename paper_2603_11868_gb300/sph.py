@@ -518,7 +518,10 @@ class Batch:
         walls = [c.wall if c.wall is not None else np.zeros((0, self.dim)) for c in self.cases]
         wcounts = [len(w) for w in walls]
         if sum(wcounts):
-            sph_batch_set_particles(self.b, SPH_WALL, wcounts, np.concatenate(walls))
+            wvel = None if all(getattr(c, "wall_vel", None) is None for c in self.cases) else \
+                np.concatenate([c.wall_vel if getattr(c, "wall_vel", None) is not None
+                                else np.zeros_like(w) for c, w in zip(self.cases, walls)])
+            sph_batch_set_particles(self.b, SPH_WALL, wcounts, np.concatenate(walls), wvel)
         vel = None if all(c.vel is None for c in self.cases) else np.concatenate(
             [c.vel if c.vel is not None else np.zeros_like(c.fluid) for c in self.cases])
         rho = None if all(c.rho is None for c in self.cases) else np.concatenate(
@@ -635,7 +638,7 @@ class Solver:
                               case.mu, case.U_ref, case.gravity, self.precision,
                               self._allocator.struct if self._allocator else None, stream or 0)
         if case.wall is not None and len(case.wall):
-            sph_set_particles(self.ctx, SPH_WALL, case.wall)
+            sph_set_particles(self.ctx, SPH_WALL, case.wall, getattr(case, "wall_vel", None))
         sph_set_particles(self.ctx, SPH_FLUID, case.fluid, case.vel, case.rho)
 
     @property

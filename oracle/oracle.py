@@ -62,6 +62,8 @@ def lib():
             L.osph_set_particles.restype = i
             L.osph_set_particles.argtypes = [vp, i, l, vp, vp, vp]
             L.osph_set_drho.restype = i; L.osph_set_drho.argtypes = [vp, vp]
+            L.osph_set_wall_translation.restype = i
+            L.osph_set_wall_translation.argtypes = [vp, vp]
             L.osph_set_variant.restype = None; L.osph_set_variant.argtypes = [vp, i, i]
             L.osph_set_transport_correction.restype = None
             L.osph_set_transport_correction.argtypes = [vp, i]
@@ -149,6 +151,8 @@ class Oracle:
         if set_particles:
             if case.wall is not None and len(case.wall):
                 o.set_wall(case.wall, case.wall_vel)
+                if getattr(case, "wall_moves", None) is not None:
+                    o.set_wall_translation(case.wall_moves)
             o.set_fluid(case.fluid, case.vel, case.rho)
         return o
 
@@ -174,6 +178,12 @@ class Oracle:
             assert vel.shape == pos.shape
         if lib().osph_set_particles(self._s, 1, len(pos), _ptr(pos), _ptr(vel), None):
             raise ValueError("oracle: set_particles (wall) failed")
+
+    def set_wall_translation(self, moves):
+        """moves[u] != 0: wall u moves with its velocity (None clears)."""
+        if moves is not None:
+            moves = np.ascontiguousarray(moves, dtype=np.uint8)
+        lib().osph_set_wall_translation(self._s, _ptr(moves))
 
     def set_drho(self, drho):
         drho = np.ascontiguousarray(drho, dtype=np.float64)

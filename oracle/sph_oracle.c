@@ -52,12 +52,18 @@ struct osim {
   uint32_t *id, *key, *perm;
   long* cb; /* cell_begin, ncell + 1 entries */
 
-  /* wall, sorted once by cell; vw = prescribed velocity of a sliding wall
-   * (zero for a wall at rest; the positions never change) */
+  /* wall, sorted by cell: once, or at every rebuild when some walls
+   * translate; vw = prescribed wall velocity (zero at rest).  A wall slides
+   * along itself (fixed position) unless it translates: then it moves with
+   * its velocity, x_w(t) = x_w(0) + v_w t.  xw0, vwu, wmoves keep the given
+   * positions, velocities and translation flags in user order. */
   long nw;
   double (*xw)[3], (*vw)[3];
   uint32_t *idw, *keyw;
   long* cbw;
+  double (*xw0)[3], (*vwu)[3];
+  unsigned char* wmoves;
+  int wtranslate; /* some wall translates */
 
   double t, tau, dt_ad, dt_ac;
   long n_ac, n_adv;
@@ -178,6 +184,7 @@ void osph_destroy(osim* s) {
   if (!s) return;
   free_fluid(s);
   free(s->xw); free(s->vw); free(s->idw); free(s->keyw);
+  free(s->xw0); free(s->vwu); free(s->wmoves);
   free(s->cb); free(s->cbw);
   free(s);
 }
@@ -253,6 +260,44 @@ static void permute_u(uint32_t* a, const uint32_t* perm, long n) {
   free(t);
 }
 
+/* Wall positions at time t: x_w(0) + v_w t for translating walls, the given
+ * position for the others (sorted slots, from the user-order copies). */
+static void place_walls(osim* s, double t) {
+  for (long k = 0; k < s->nw; ++k) {
+    uint32_t u = s->idw[k];
+    if (!s->wmoves[u]) continue;
+    for (int c = 0; c < 3; ++c) s->xw[k][c] = s->xw0[u][c] + t * s->vwu[u][c];
+  }
+}
+
+/* Bin the walls at time t: keys of their positions at t, a sort by key with
+ * ties in user order, and the wall cell offsets. */
+static void bin_walls(osim* s, double t) {
+  long n = s->nw;
+  kv_t* a = (kv_t*)xcalloc((size_t)(n > 0 ? n : 1), sizeof(kv_t));
+  int oob = 0;
+  for (long u = 0; u < n; ++u) {
+    double xu[3];
+    for (int c = 0; c < 3; ++c)
+      xu[c] = s->wmoves[u] ? s->xw0[u][c] + t * s->vwu[u][c] : s->xw0[u][c];
+    a[u].key = cell_key(s, xu, &oob);
+    a[u].idx = (uint32_t)u;
+  }
+  if (oob) s->flags |= 1;
+  qsort(a, (size_t)n, sizeof(kv_t), cmp_kv);
+  for (long k = 0; k < n; ++k) {
+    uint32_t u = a[k].idx;
+    s->idw[k] = u;
+    s->keyw[k] = a[k].key;
+    for (int c = 0; c < 3; ++c) {
+      s->xw[k][c] = s->wmoves[u] ? s->xw0[u][c] + t * s->vwu[u][c] : s->xw0[u][c];
+      s->vw[k][c] = s->vwu[u][c];
+    }
+  }
+  free(a);
+  cell_offsets(s, s->keyw, n, s->cbw);
+}
+
 /* Rebuild of the cell-linked list: keys from the current FP64 positions, a
  * stable sort by key (ties keep the current storage order), reorder of every
  * per-particle field, and CSR cell offsets. */
@@ -281,6 +326,18 @@ void osph_rebuild(osim* s) {
   permute1(s->sigma, s->perm, n);
   permute_u(s->id, s->perm, n);
   cell_offsets(s, s->key, n, s->cb);
+  /* translating walls are binned again at the rebuild time */
+  if (s->wtranslate) bin_walls(s, s->t);
+}
+
+int osph_set_wall_translation(osim* s, const unsigned char* moves) {
+  s->wtranslate = 0;
+  for (long u = 0; u < s->nw; ++u) {
+    s->wmoves[u] = moves ? (moves[u] ? 1 : 0) : 0;
+    if (s->wmoves[u]) s->wtranslate = 1;
+  }
+  bin_walls(s, s->t);
+  return 0;
 }
 
 int osph_set_particles(osim* s, int kind, long n, const double* pos,
@@ -321,32 +378,22 @@ int osph_set_particles(osim* s, int kind, long n, const double* pos,
   }
   if (kind == 1) {
     free(s->xw); free(s->vw); free(s->idw); free(s->keyw);
+    free(s->xw0); free(s->vwu); free(s->wmoves);
     s->nw = n;
     s->xw = (double(*)[3])xcalloc((size_t)n, sizeof(double[3]));
     s->vw = (double(*)[3])xcalloc((size_t)n, sizeof(double[3]));
     s->idw = (uint32_t*)xcalloc((size_t)n, sizeof(uint32_t));
     s->keyw = (uint32_t*)xcalloc((size_t)n, sizeof(uint32_t));
-    kv_t* a = (kv_t*)xcalloc((size_t)n, sizeof(kv_t));
-    int oob = 0;
-    for (long i = 0; i < n; ++i) {
-      double xi[3] = {0, 0, 0};
-      for (int k = 0; k < d; ++k) xi[k] = pos[i * d + k];
-      a[i].key = cell_key(s, xi, &oob);
-      a[i].idx = (uint32_t)i;
-    }
-    if (oob) s->flags |= 1;
-    qsort(a, (size_t)n, sizeof(kv_t), cmp_kv);
-    for (long k = 0; k < n; ++k) {
-      uint32_t i = a[k].idx;
+    s->xw0 = (double(*)[3])xcalloc((size_t)n, sizeof(double[3]));
+    s->vwu = (double(*)[3])xcalloc((size_t)n, sizeof(double[3]));
+    s->wmoves = (unsigned char*)xcalloc((size_t)n, 1);
+    s->wtranslate = 0;
+    for (long i = 0; i < n; ++i)
       for (int c = 0; c < 3; ++c) {
-        s->xw[k][c] = c < d ? pos[(long)i * d + c] : 0.0;
-        s->vw[k][c] = (c < d && vel) ? vel[(long)i * d + c] : 0.0;
+        s->xw0[i][c] = c < d ? pos[i * d + c] : 0.0;
+        s->vwu[i][c] = (c < d && vel) ? vel[i * d + c] : 0.0;
       }
-      s->idw[k] = i;
-      s->keyw[k] = a[k].key;
-    }
-    free(a);
-    cell_offsets(s, s->keyw, n, s->cbw);
+    bin_walls(s, 0.0);
     return 0;
   }
   return 1;
@@ -529,13 +576,16 @@ double osph_vmax2(const osim* s) {
 }
 
 /* First half of the acoustic step [Z17]: density by the carried rate, pressure
- * by the linear equation of state, positions by half a step. */
+ * by the linear equation of state, positions by half a step (translating
+ * walls to t + dt/2). */
 void osph_half1(osim* s, double dt) {
   for (long i = 0; i < s->n; ++i) {
     s->rho[i] += 0.5 * dt * s->drho[i];
     s->p[i] = s->c0 * s->c0 * (s->rho[i] - s->rho0);
     for (int k = 0; k < s->dim; ++k) s->x[i][k] += 0.5 * dt * s->v[i][k];
   }
+  /* translating walls follow to the same time (reading) */
+  if (s->wtranslate) place_walls(s, s->t + 0.5 * dt);
 }
 
 /* Riemann-based pressure relaxation [Z17], then the velocity kick.
@@ -620,7 +670,8 @@ void osph_pressure_relaxation(osim* s, double dt) {
       s->v[i][k] += dt * (s->acc[i][k] + s->aprior[i][k]);
 }
 
-/* Second half of the acoustic step [Z17]: positions by half a step, then the
+/* Second half of the acoustic step [Z17]: positions by half a step
+ * (translating walls to t + dt), then the
  * Riemann-based density relaxation
  *   drho_i = -2 rho_i sum_j V_j W'(r_ij) (U_L - U*_ij)
  * (fluid V_j = m / rho_j; wall: mirrored state and V_w = m / rho_w as in
@@ -634,6 +685,7 @@ void osph_half2(osim* s, double dt) {
   long cells[27];
   for (long i = 0; i < s->n; ++i)
     for (int k = 0; k < s->dim; ++k) s->x[i][k] += 0.5 * dt * s->v[i][k];
+  if (s->wtranslate) place_walls(s, s->t + dt);
   for (long i = 0; i < s->n; ++i) {
     int nc = neighbour_cells(s, s->key[i], cells);
     double sum = 0.0;

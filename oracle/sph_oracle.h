@@ -58,6 +58,13 @@ void osph_destroy(osim* s);
  * the viscous force.  Wall density is ignored.  Returns 0 on success. */
 int osph_set_particles(osim* s, int kind, long n, const double* pos,
                        const double* vel, const double* rho);
+/* translating walls (default none): moves[u] != 0 makes wall particle u
+ * (user order of the last wall set) move with its velocity,
+ * x_w(t) = x_w(0) + v_w t, t the simulation time; the other walls keep their
+ * positions.  Translating walls are binned again at every rebuild and follow
+ * the fluid's half-drifts: at t + dt/2 for the pressure relaxation, at
+ * t + dt for the density relaxation.  NULL clears.  Returns 0. */
+int osph_set_wall_translation(osim* s, const unsigned char* moves);
 /* method variants: density_riemann = 1 (default) takes the Riemann U* in the
  * density relaxation, 0 the average of the two states; reinit_blended = 0
  * (default) reinitialises the density with the free-surface clamp

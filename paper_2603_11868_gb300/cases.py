@@ -26,6 +26,10 @@ Workloads:
                     Re = U H / nu = 10): far from the ends the steady flow is
                     the zero-net-flux Couette-Poiseuille profile
                     u = U eta (3 eta - 2), eta = y / H.
+  piston_channel_2d closed 2D channel of fluid at rest (no gravity, inviscid)
+                    whose left wall block translates into it at V = c0 / 20
+                    from t = 0: a compression wave runs ahead at about c0
+                    with p = rho0 c0 V and u = V behind it (linear acoustics).
   dam_break_obstacle_3d
                     3D dam break whose surge hits a box obstacle on the floor
                     (the kind of test the paper's second workload is): tank
@@ -60,6 +64,7 @@ class Case:
     rho: np.ndarray | None = None    # (n,) or None (rho0)
     meta: dict = field(default_factory=dict)
     wall_vel: np.ndarray | None = None  # (nw, dim) prescribed wall velocity, or None (rest)
+    wall_moves: np.ndarray | None = None  # (nw,) 1: the wall translates with its velocity
 
     @property
     def n(self) -> int:
@@ -292,3 +297,24 @@ def sliding_lid_channel_2d(dp: float = 0.05, length: float = 4.0, height: float 
                 (0.0, 0.0), lo, hi, fluid, wall,
                 meta=dict(tank=tank, U=U, H=height, L=length, nu=nu, layers=layers),
                 wall_vel=np.ascontiguousarray(wall_vel))
+
+
+def piston_channel_2d(dp: float = 0.05, length: float = 4.0, height: float = 0.5,
+                      V: float = 1.0, c0: float = 20.0, layers: int = 4,
+                      rho0: float = 1.0, mu: float = 0.0) -> Case:
+    """Closed 2D channel filled with fluid at rest on the lattice; the wall
+    layers left of x = 0 (corners included) translate along +x at V from
+    t = 0 (wall_moves), the others rest.  No gravity."""
+    nx, ny = int(round(length / dp)), int(round(height / dp))
+    fluid = fluid_block(2, (0.0, 0.0), (nx * dp, ny * dp), dp, 0.0, None)
+    tank = (length, height)
+    wall = tank_walls(2, tank, dp, layers, open_top=False)
+    piston = wall[:, 0] < 0
+    wall_vel = np.zeros_like(wall)
+    wall_vel[piston, 0] = V
+    lo, hi = _domain(2, tank, dp, layers, 0.0)
+    return Case("piston_channel_2d", 2, dp, 1.3 * dp, rho0, c0, mu, c0 / 10.0, (0.0, 0.0),
+                lo, hi, np.ascontiguousarray(fluid), wall,
+                meta=dict(tank=tank, V=V, L=length, H=height, layers=layers),
+                wall_vel=np.ascontiguousarray(wall_vel),
+                wall_moves=piston.astype(np.uint8))

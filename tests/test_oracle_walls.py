@@ -10,6 +10,17 @@
   u = U eta (3 eta - 2), eta = y / H (lubrication / Couette-Poiseuille).
   This pins the viscous operator, the no-slip wall term (the mirrored wall
   velocity) and the wall velocity itself against the mathematics.
+
+Translating walls (x_w(t) = x_w(0) + v_w t):
+- frame invariance of one acoustic step: fluid and walls all moving at V
+  (the walls translating) give the step of the same state at rest, shifted
+  by V dt, to rounding;
+- the acoustic piston: an impulsively started piston at V drives a plateau
+  with p = rho0 c0 V and u = V behind a front moving at about c0, and the fluid
+  ahead of the front stays exactly at rest;
+- after the piston has crossed cells, a rebuild bins the walls where they
+  are: wall keys are the cells of x_w(0) + v_w t and the cell list gives the
+  brute-force neighbour sets.
 """
 import numpy as np
 import pytest
@@ -97,3 +108,87 @@ def test_sliding_lid_channel_matches_the_closed_form(oracle_mod):
     assert err <= 0.03 * c.meta["U"], (err, u, ref)
     # zero net flux through the mid-channel section
     assert abs(u.mean()) <= 0.01 * c.meta["U"]
+
+
+# --------------------------------------------------------------------------
+# translating walls
+def _box_with_motion(oracle_mod, V, translate, seed=90):
+    fluid, wall, lo, hi, rho = _jittered_box(2, 12, 0.05, seed)
+    # room for the walls to travel
+    lo = tuple(l - 0.5 for l in lo)
+    hi = tuple(h + 0.5 for h in hi)
+    rng = np.random.default_rng(seed + 1)
+    vel = rng.normal(scale=0.3, size=fluid.shape) + V
+    c = cases.Case("box", 2, 0.05, 0.065, 1.0, 10.0, 0.0, 1.0, (0.0, -1.0), lo, hi, fluid,
+                   wall, vel=vel, rho=rho, wall_vel=np.tile(V, (len(wall), 1)) if translate
+                   else None, wall_moves=np.ones(len(wall), np.uint8) if translate else None)
+    return oracle_mod.Oracle.from_case(c)
+
+
+def test_translating_frame_is_invisible_to_one_step(oracle_mod):
+    V = np.array([0.7, -0.4])
+    dt = 2e-3
+    rest = _box_with_motion(oracle_mod, np.zeros(2), False)
+    moving = _box_with_motion(oracle_mod, V, True)
+    for o in (rest, moving):
+        o.half1(dt)
+        o.pressure_relaxation(dt)
+        o.half2(dt)
+    pr, pm = rest.field(oracle_mod.POS), moving.field(oracle_mod.POS)
+    assert np.abs((pm - V * dt) - pr).max() < 1e-13
+    vr, vm = rest.field(oracle_mod.VEL), moving.field(oracle_mod.VEL)
+    assert np.abs((vm - V) - vr).max() < 1e-12
+    for f in (oracle_mod.RHO, oracle_mod.DRHO, oracle_mod.ACC):
+        a, b = rest.field(f), moving.field(f)
+        assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max(), f
+    # walls that do not translate break the invariance (the pin is not vacuous)
+    still = _box_with_motion(oracle_mod, V, False)
+    still.half1(dt)
+    still.pressure_relaxation(dt)
+    still.half2(dt)
+    assert np.abs(still.field(oracle_mod.ACC) - rest.field(oracle_mod.ACC)).max() > 1e-3
+
+
+def piston_plateau(pos, vel, p, case, t):
+    V, c0 = case.meta["V"], case.c0
+    xp, xf = V * t, V * t + c0 * t
+    plateau = (pos[:, 0] > xp + 0.5) & (pos[:, 0] < xf - 0.5)
+    ahead = (pos[:, 0] > xf + 0.6) & (pos[:, 0] < case.meta["L"] - 0.2)
+    return plateau, ahead
+
+
+def test_piston_drives_the_acoustic_state(oracle_mod):
+    c = cases.piston_channel_2d()
+    o = oracle_mod.Oracle.from_case(c)
+    while o.scalars()["t"] < 0.1:
+        o.step(1)
+    t = o.scalars()["t"]
+    pos, vel, p = o.field(oracle_mod.POS), o.field(oracle_mod.VEL), o.field(oracle_mod.P)
+    plateau, ahead = piston_plateau(pos, vel, p, c, t)
+    assert plateau.sum() > 100 and ahead.sum() > 100
+    V = c.meta["V"]
+    assert abs(p[plateau].mean() / (c.rho0 * c.c0 * V) - 1) < 0.03
+    assert abs(vel[plateau, 0].mean() / V - 1) < 0.03
+    assert np.abs(p[ahead]).max() < 1e-3 * c.rho0 * c.c0 * V
+    assert np.abs(vel[ahead]).max() < 1e-3 * V
+
+
+def test_translating_walls_are_binned_where_they_are(oracle_mod):
+    c = cases.piston_channel_2d(V=2.0)
+    o = oracle_mod.Oracle.from_case(c)
+    o.step(130)
+    t = o.scalars()["t"]
+    assert c.meta["V"] * t > 2.5 * 2 * c.h  # the piston crossed more than two cells
+    o.rebuild()
+    ws = o.wall_state()
+    x = c.wall + c.wall_moves[:, None] * c.wall_vel * t
+    cs = 2 * c.h
+    nc = np.ceil((np.array(c.hi) - np.array(c.lo)) / cs).astype(np.int64)
+    cell = np.floor((x - np.array(c.lo)) / cs).astype(np.int64)
+    keys = cell[:, 1] * nc[0] + cell[:, 0]
+    assert np.array_equal(ws["keys"], np.sort(keys))
+    assert np.array_equal(keys[ws["ids"]], ws["keys"])
+    cf, cw, hs = o.neighbour_stats(brute=False)
+    bf, bw, bh = o.neighbour_stats(brute=True)
+    assert np.array_equal(cw, bw) and np.array_equal(hs, bh)
+    assert cw.sum() > 0

@@ -32,6 +32,12 @@ MUTATIONS = {
                            "d += (vw[k] - vi[k]) * e[k];"),
     "wall_viscous_mirror": ("a[k] += coef * (2.0 * (s->v[i][k] - s->vw[w][k]));",
                             "a[k] += coef * (s->v[i][k] - s->vw[w][k]);"),
+    "translate_half_step_time": ("if (s->wtranslate) place_walls(s, s->t + 0.5 * dt);",
+                                 "if (s->wtranslate) place_walls(s, s->t + dt);"),
+    "translate_speed": ("for (int c = 0; c < 3; ++c) s->xw[k][c] = s->xw0[u][c] + t * s->vwu[u][c];",
+                        "for (int c = 0; c < 3; ++c) s->xw[k][c] = s->xw0[u][c] + 0.5 * t * s->vwu[u][c];"),
+    "translate_not_rebinned": ("if (s->wtranslate) bin_walls(s, s->t);",
+                               "if (0) bin_walls(s, s->t);"),
     "wall_viscous_velocity_sign": ("a[k] += coef * (2.0 * (s->v[i][k] - s->vw[w][k]));",
                                    "a[k] += coef * (2.0 * (s->v[i][k] + s->vw[w][k]));"),
     "continuity_sign": ("sum += (s->m / s->rho[j]) * osph_dW(s->dim, s->h, r) * (UL - Us);",

@@ -166,6 +166,21 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
 int sph_set_particles(sph_ctx* ctx, int kind, size_t n, const double* pos, const double* vel,
                       const double* rho);
 
+/* Makes walls translate: moves (nw bytes, user order of the last SPH_WALL
+ * set) marks the wall particles that move with their prescribed velocity,
+ * x_w(t) = x_w(0) + v_w t, t the simulation time and x_w(0) the position
+ * given to sph_set_particles; the others keep their positions (at rest or
+ * sliding).  Translating walls are binned again at every rebuild (at the
+ * step's start time) and follow the fluid's half-drifts: at t + dt/2 for the
+ * pressure relaxation, at t + dt for the density relaxation.  The neighbour
+ * lists stay exact: their bound also covers the walls' drift since the
+ * rebuild.  NULL (or all zero) clears.  The walls are binned again at once,
+ * at the current time.  A new SPH_WALL set clears the translation.  A wall
+ * that leaves the box is clamped and flagged like a fluid particle.
+ * Single tanks only (batches have no translating walls).  SPH_E_OOM when the
+ * wall buffers cannot be allocated. */
+int sph_set_wall_translation(sph_ctx* ctx, const uint8_t* moves);
+
 /* Queues n acoustic steps of the dual-criteria schedule.  Each step: when the
  * elapsed time of the current advection step has reached its length (or on
  * the first step), a new advection step begins (length 0.25 h / max(U_ref,

@@ -43,6 +43,14 @@ struct sph_batch {
 
 namespace {
 
+// The neighbour lists name walls by their sorted slot: walls sorted anew
+// outside a rebuild send every tank's loops to direct search until its next
+// rebuild.
+__global__ void kb_lists_bad(DevScalars* tsc, int T) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < T) tsc[t].list_bad = 1;
+}
+
 int set_err(sph_batch* b, int code, const std::string& msg) {
   if (b) b->err = msg;
   return code;
@@ -632,6 +640,8 @@ int sph_batch_set_particles(sph_batch* b, int kind, const size_t* counts, const 
     enqueue_batch_wall_setup_fp64(a, s);
   else
     enqueue_batch_wall_setup_mixed(a, s);
+  CKB(cudaGetLastError());
+  kb_lists_bad<<<(b->T + 255) / 256, 256, 0, s>>>(b->A.tsc, b->T);
   CKB(cudaGetLastError());
   CKB(cudaStreamSynchronize(s));
   b->mem.release(tmp);

@@ -6,6 +6,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -36,7 +38,9 @@ struct sph_ctx {
   double dp = 0;
   size_t cap_n = 0;   // capacity of per-particle buffers
   size_t cap_nw = 0;  // capacity of wall buffers
-  std::vector<Block> fluid_blocks, wall_blocks, fixed_blocks;
+  // trans_blocks: the buffers of translating walls (sph_set_wall_translation)
+  std::vector<Block> fluid_blocks, wall_blocks, fixed_blocks, trans_blocks;
+  std::vector<double> wall_vel_host;  // given wall velocities (n * dim), empty at rest
   std::string err;
   bool fluid_set = false;
 };
@@ -51,6 +55,27 @@ int set_err(sph_ctx* c, int code, const std::string& msg) {
 int cuda_err(sph_ctx* c, cudaError_t e, const char* where) {
   if (e == cudaSuccess) return SPH_OK;
   return set_err(c, SPH_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// The neighbour lists name walls by their sorted slot: once the walls are
+// sorted anew outside a rebuild, the loops take direct search until the next
+// rebuild builds fresh lists.
+cudaError_t invalidate_lists(sph_ctx* c) {
+  const int one = 1;
+  return cudaMemcpyAsync((char*)c->B.sc + offsetof(DevScalars, list_bad), &one, sizeof(int),
+                         cudaMemcpyHostToDevice, c->stream);
+}
+
+// forgets the translating walls (their buffers are freed by the caller)
+void clear_translation(sph_ctx* c) {
+  c->B.wall_moves = nullptr;
+  c->B.wall_io = nullptr;
+  c->B.wall_key = nullptr;
+  c->B.wkeys[0] = c->B.wkeys[1] = nullptr;
+  c->B.wvals[0] = c->B.wvals[1] = nullptr;
+  c->B.wtile_hist = nullptr;
+  c->P.variant &= ~kVariantTranslatingWall;
+  c->P.wall_vmax = 0.0;
 }
 
 #define CK(call)                                  \
@@ -485,10 +510,14 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));
     drop_graph(c);
+    dev_free_list(c, c->trans_blocks);
     dev_free_list(c, c->wall_blocks);
+    clear_translation(c);
     c->cap_nw = 0;
     c->P.nw = (int)n;
     c->B.wall_vel = nullptr;
+    c->B.wall_x0 = c->B.wall_v0 = nullptr;
+    c->wall_vel_host.clear();
     c->P.variant &= ~kVariantMovingWall;
     if (n == 0) {
       c->B.wallP = nullptr;
@@ -508,8 +537,9 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
     c->B.wall_vel = moving ? A(n * (d == 3 ? 4 : 2) * ts) : nullptr;
     std::vector<Block> tmp;
     DevBuffers W = c->B;
-    // staging: positions SoA (3 n), then the velocities SoA (3 n) when moving
-    W.io = (double*)dev_alloc(c, n * (moving ? 6 : 3) * 8, tmp);
+    // the walls as given, kept for translating walls: positions SoA (3 n),
+    // then the velocities SoA (3 n) when moving
+    W.io = (double*)A(n * (moving ? 6 : 3) * 8);
     for (int p = 0; p < 2; ++p) {
       W.keys[p] = (uint32_t*)dev_alloc(c, n * 4, tmp);
       W.vals[p] = (uint32_t*)dev_alloc(c, n * 4, tmp);
@@ -538,7 +568,10 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
       if (d == 2) CK(cudaMemsetAsync(W.io + 5 * n, 0, n * 8, c->stream));
       launch_deinterleave(c->B.wall_xyz, (int)n, d, vsoa, c->stream);
       c->P.variant |= kVariantMovingWall;
+      c->wall_vel_host.assign(vel, vel + n * d);
     }
+    c->B.wall_x0 = W.io;
+    c->B.wall_v0 = moving ? W.io + 3 * n : nullptr;
     StageArgs a = args(c);
     a.B = W;
     if (c->precision == SPH_FP64)
@@ -546,12 +579,73 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
     else
       enqueue_wall_setup_mixed(a, c->stream);
     CK(cudaGetLastError());
+    CK(invalidate_lists(c));
     CK(cudaStreamSynchronize(c->stream));
     dev_free_list(c, tmp);
     c->cap_nw = n;
     return leave(c);
   }
   return set_err(c, SPH_E_INVALID, "unknown particle kind");
+}
+
+int sph_set_wall_translation(sph_ctx* c, const uint8_t* moves) {
+  if (!c) return SPH_E_INVALID;
+  int rc = enter(c);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graph(c);
+  dev_free_list(c, c->trans_blocks);
+  clear_translation(c);
+  const size_t n = (size_t)c->P.nw;
+  if (n == 0) return leave(c);
+  const int d = c->P.dim;
+  bool any = false;
+  double vmax = 0.0;
+  if (moves) {
+    for (size_t u = 0; u < n; ++u) {
+      if (!moves[u]) continue;
+      any = true;
+      if (c->wall_vel_host.empty()) continue;
+      double v2 = 0.0;
+      for (int k = 0; k < d; ++k) v2 += c->wall_vel_host[u * d + k] * c->wall_vel_host[u * d + k];
+      vmax = std::max(vmax, std::sqrt(v2));
+    }
+  }
+  // walls given no velocity are at rest: nothing to translate
+  if (!c->B.wall_v0) any = false;
+  auto A = [&](size_t bytes) { return dev_alloc(c, bytes, c->trans_blocks); };
+  uint8_t* dm = any ? (uint8_t*)A(n) : nullptr;
+  c->B.wall_io = (double*)A(n * 3 * 8);
+  c->B.wall_key = (uint32_t*)A(n * 4);
+  for (int p = 0; p < 2; ++p) {
+    c->B.wkeys[p] = (uint32_t*)A(n * 4);
+    c->B.wvals[p] = (uint32_t*)A(n * 4);
+  }
+  const size_t tiles = (n + kSortTile - 1) / kSortTile;
+  c->B.wtile_hist = (uint32_t*)A(tiles * ((size_t)1 << kMaxRadixBits) * 4);
+  const bool ok = (!any || dm) && c->B.wall_io && c->B.wall_key && c->B.wkeys[0] &&
+                  c->B.wkeys[1] && c->B.wvals[0] && c->B.wvals[1] && c->B.wtile_hist;
+  if (!ok) {
+    dev_free_list(c, c->trans_blocks);
+    clear_translation(c);
+    return set_err(c, SPH_E_OOM, "device allocation failed (translating walls)");
+  }
+  if (any) {
+    CK(cudaMemcpyAsync(dm, moves, n, cudaMemcpyHostToDevice, c->stream));
+    c->B.wall_moves = dm;
+    c->P.variant |= kVariantTranslatingWall;
+    c->P.wall_vmax = vmax;
+  }
+  // walls binned again where they are now (back at their given positions
+  // when none translates)
+  if (c->precision == SPH_FP64)
+    enqueue_wall_rebin_fp64(args(c), c->stream);
+  else
+    enqueue_wall_rebin_mixed(args(c), c->stream);
+  CK(cudaGetLastError());
+  CK(invalidate_lists(c));
+  CK(cudaStreamSynchronize(c->stream));
+  return leave(c);
 }
 
 int sph_step(sph_ctx* c, int n) {
@@ -878,7 +972,7 @@ int sph_autotune(sph_ctx* c, int steps_per_trial, sph_tuning* best) {
   mem.has_alloc = c->has_alloc;
   mem.stream = c->stream;
   Snapshot snap;
-  if (!snap.take(mem, {&c->fluid_blocks, &c->wall_blocks, &c->fixed_blocks}))
+  if (!snap.take(mem, {&c->fluid_blocks, &c->wall_blocks, &c->fixed_blocks, &c->trans_blocks}))
     return set_err(c, SPH_E_OOM, "device allocation failed (autotuner snapshot)");
   const LaunchCfg L0 = c->L;
   const Params P0 = c->P;
@@ -943,6 +1037,7 @@ void sph_destroy(sph_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   drop_graph(c);
   dev_free_list(c, c->fluid_blocks);
+  dev_free_list(c, c->trans_blocks);
   dev_free_list(c, c->wall_blocks);
   dev_free_list(c, c->fixed_blocks);
   if (c->ev_in) cudaEventDestroy(c->ev_in);

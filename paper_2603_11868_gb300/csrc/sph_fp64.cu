@@ -38,4 +38,11 @@ void enqueue_wall_setup_fp64(const StageArgs& a, cudaStream_t s) {
     stages::enqueue_wall_setup_t<3, double>(a, s);
 }
 
+void enqueue_wall_rebin_fp64(const StageArgs& a, cudaStream_t s) {
+  if (a.P.dim == 2)
+    stages::enqueue_wall_rebin_t<2, double>(a, s, 0, 1);
+  else
+    stages::enqueue_wall_rebin_t<3, double>(a, s, 0, 1);
+}
+
 }  // namespace sphgb

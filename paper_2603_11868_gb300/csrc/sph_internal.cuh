@@ -55,6 +55,9 @@ constexpr int kVariantNoRiemann = 1;
 constexpr int kVariantBlended = 2;
 constexpr int kVariantTransport = 4;  // transport-velocity correction each advection step
 constexpr int kVariantMovingWall = 8;  // walls with a prescribed (sliding) velocity
+// some walls translate with their velocity: binned again at every rebuild,
+// moved with the fluid's half-drifts
+constexpr int kVariantTranslatingWall = 16;
 
 // error flag bits (sticky, device)
 constexpr int kFlagOutOfDomain = 1;
@@ -85,8 +88,10 @@ struct Params {
   // average of the two states instead of the Riemann U*; kVariantBlended ->
   // blended free-surface density reinitialisation instead of the clamp;
   // kVariantTransport -> transport-velocity correction after the summation;
-  // kVariantMovingWall -> the wall terms read the prescribed wall velocity
+  // kVariantMovingWall -> the wall terms read the prescribed wall velocity;
+  // kVariantTranslatingWall -> some walls move with their velocity
   int variant;
+  double wall_vmax;  // largest speed of a translating wall (0 when none translates)
   // position of this tank in the arrays of a batch (all zero for one tank):
   // first fluid slot, first wall slot, first entry of its cell offsets
   int foff, woff;
@@ -113,6 +118,8 @@ struct DevScalars {
   // bit pattern of the largest transport-velocity shift of this advection step
   // (part of every particle's displacement since the rebuild)
   unsigned long long shift_bits;
+  double t0;     // start time of the current acoustic step
+  double t_reb;  // time of the last rebuild (translating walls were binned then)
 };
 
 template <class T>
@@ -171,6 +178,19 @@ struct DevBuffers {
   double* wall_xyz;  // sorted wall positions, double SoA (3 nw)
   void* wallI;       // mixed mode: wall fixed-point offsets (int4 / int2)
   void* wall_vel;    // prescribed wall velocity (T4 / T2, sorted), null when every wall rests
+  // walls as given (user order, double SoA x | y | z of nw each): positions,
+  // velocities (null: all at rest)
+  const double* wall_x0;
+  const double* wall_v0;
+  // translating walls: flags (user order; null: none translates), positions
+  // placed at the binning time (user order SoA) and the wall sort's own
+  // ping-pong and histogram buffers
+  const uint8_t* wall_moves;
+  double* wall_io;
+  uint32_t* wall_key;  // binned cell key of each sorted wall
+  uint32_t* wkeys[2];
+  uint32_t* wvals[2];
+  uint32_t* wtile_hist;
   DevScalars* sc;
   double* io;  // staging, n * dim doubles (also wall staging)
   uint32_t* u32_io;
@@ -302,6 +322,11 @@ void enqueue_initial_sort_mixed(const StageArgs& a, cudaStream_t s);
 // to scratch of its own so that the fluid's sorted keys survive.
 void enqueue_wall_setup_fp64(const StageArgs& a, cudaStream_t s);
 void enqueue_wall_setup_mixed(const StageArgs& a, cudaStream_t s);
+// Walls binned again at the current time (sc->t): positions x0 + t v0 for the
+// translating walls, x0 for the others, then the sort in the wall buffers of
+// `a.B` (wall_io, wkeys, wvals, wtile_hist), the gather and the wall offsets.
+void enqueue_wall_rebin_fp64(const StageArgs& a, cudaStream_t s);
+void enqueue_wall_rebin_mixed(const StageArgs& a, cudaStream_t s);
 
 // --- neighbour search (sph_nsearch.cu), precision independent
 // keys from positions x[par] (or an explicit coordinate set), vals = iota

@@ -55,4 +55,11 @@ void enqueue_wall_setup_mixed(const StageArgs& a, cudaStream_t s) {
     stages::enqueue_wall_setup_t<3, float>(a, s);
 }
 
+void enqueue_wall_rebin_mixed(const StageArgs& a, cudaStream_t s) {
+  if (a.P.dim == 2)
+    stages::enqueue_wall_rebin_t<2, float>(a, s, 0, 1);
+  else
+    stages::enqueue_wall_rebin_t<3, float>(a, s, 0, 1);
+}
+
 }  // namespace sphgb

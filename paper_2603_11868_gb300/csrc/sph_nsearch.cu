@@ -347,20 +347,24 @@ __device__ __forceinline__ void control_one(const Params& P, DevScalars* sc) {
     sc->n_adv += 1;
     sc->started = 1;
     // skin for this advection step: twice the distance covered at the current
-    // top speed (plus what gravity can add) over the step and one overshooting
-    // acoustic step, with margin; the loops check the bound and fall back to
-    // direct search if it is ever exceeded
+    // top speed (plus what gravity can add; at least the speed of a
+    // translating wall) over the step and one overshooting acoustic step, with
+    // margin; the loops check the bound and fall back to direct search if it
+    // is ever exceeded
     const double gmag = sqrt(P.g[0] * P.g[0] + P.g[1] * P.g[1] + P.g[2] * P.g[2]);
     const double span = sc->dt_ad + 1.5 * dt;
-    double skin = 2.5 * (vmax + gmag * span) * span + 0.02 * P.h;
+    const double vs = vmax > P.wall_vmax ? vmax : P.wall_vmax;
+    double skin = 2.5 * (vs + gmag * span) * span + 0.02 * P.h;
     sc->skin = skin < P.skin_max ? skin : P.skin_max;
     sc->list_bad = 0;
     sc->shift_bits = 0ull;
+    sc->t_reb = sc->t;
     disp = 0.0;
   }
   sc->new_adv = adv;
   sc->dt_ac = dt;
   sc->tau += dt;
+  sc->t0 = sc->t;
   sc->t += dt;
   sc->n_ac += 1;
   sc->vmax2_next = 0ull;

@@ -975,7 +975,11 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
   const int par = sc->par;
   const double dt = sc->dt_ac;
   const double hdt = 0.5 * dt;
-  const bool use_list = list_ok(P, sc, sc->disp_p);
+  // translating walls have moved by at most wall_vmax times the time since
+  // their binning; a wall pair needs the sum of both drifts below the skin,
+  // which 2 max(fluid, wall) bounds
+  const bool use_list =
+      list_ok(P, sc, fmax(sc->disp_p, P.wall_vmax * (sc->t0 + hdt - sc->t_reb)));
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
   const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
   typename R::PV* outP = (typename R::PV*)B.recP[1];
@@ -1096,7 +1100,8 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
   // positions after the second half-drift: bound grows by dt/2 * top speed after the kick
   const double disp2 =
       sc->disp_p + hdt * sqrt(__longlong_as_double((long long)sc->vmax2_next));
-  const bool use_list = list_ok(P, sc, disp2);
+  const bool use_list =
+      list_ok(P, sc, fmax(disp2, P.wall_vmax * (sc->t0 + 2.0 * hdt - sc->t_reb)));
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[1];
   const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[1];
   const uint32_t* __restrict__ keys = B.binned;
@@ -1185,6 +1190,7 @@ __device__ __forceinline__ void wall_slot(const Params& P, const DevBuffers& B,
   wy[k] = y;
   if (D == 3) wz[k] = z;
   B.wall_id[k] = j;
+  if (B.wall_key) B.wall_key[k] = key;
   T ox, oy, oz;
   const Cell ck = decode(key, P);
   Local<T>::enc(P, B.ctab, ck, x, y, z, ox, oy, oz);
@@ -1199,11 +1205,57 @@ __device__ __forceinline__ void wall_slot(const Params& P, const DevBuffers& B,
 template <int D, class T>
 __global__ void k_wall_gather(Params P, DevBuffers B, const double* __restrict__ ux,
                               const double* __restrict__ uy, const double* __restrict__ uz,
-                              double* wx, double* wy, double* wz, const double* uv) {
+                              double* wx, double* wy, double* wz, const double* uv, int gated) {
+  if (gated && !B.sc->new_adv) return;
   const uint32_t* perm = B.vals[B.sorted_buf];
   const uint32_t* keys = B.keys[B.sorted_buf];
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.nw; k += gridDim.x * blockDim.x)
     wall_slot<D, T>(P, B, ux, uy, uz, wx, wy, wz, uv, (size_t)P.nw, k, perm[k], keys[k]);
+}
+
+// Translating walls.  k_wall_place writes every wall's position at the
+// binning time (the step's start time at a rebuild, the current time when
+// `now`) into wall_io: x0 + t v0 for a translating wall, x0 for the others.
+template <int D>
+__global__ void k_wall_place(Params P, DevBuffers B, int gated, int now) {
+  DevScalars* sc = B.sc;
+  if (gated && !sc->new_adv) return;
+  const double t = now ? sc->t : sc->t0;
+  const size_t nw = (size_t)P.nw;
+  for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < nw;
+       u += (size_t)gridDim.x * blockDim.x) {
+    const bool moves = B.wall_moves && B.wall_moves[u] && B.wall_v0;
+    for (int c = 0; c < 3; ++c) {
+      const double x = B.wall_x0[c * nw + u];
+      B.wall_io[c * nw + u] = moves ? x + t * B.wall_v0[c * nw + u] : x;
+    }
+  }
+}
+
+// Moves the translating walls (sorted slots) to the fluid's time: t0 + dt/2
+// after the first half-drift (`half`), t0 + dt after the second; their
+// records stay relative to the cell they were binned in.
+template <int D, class T>
+__global__ void k_wall_move(Params P, DevBuffers B, int half) {
+  using WR = WallRec<D, T>;
+  const DevScalars* sc = B.sc;
+  const double t = sc->t0 + (half ? 0.5 : 1.0) * sc->dt_ac;
+  const size_t nw = (size_t)P.nw;
+  typename WR::WV* out = (typename WR::WV*)B.wallP;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nw;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t u = B.wall_id[k];
+    if (!B.wall_moves || !B.wall_v0 || !B.wall_moves[u]) continue;
+    const double x = B.wall_x0[u] + t * B.wall_v0[u];
+    const double y = B.wall_x0[nw + u] + t * B.wall_v0[nw + u];
+    const double z = D == 3 ? B.wall_x0[2 * nw + u] + t * B.wall_v0[2 * nw + u] : 0.0;
+    B.wall_xyz[k] = x;
+    B.wall_xyz[nw + k] = y;
+    if (D == 3) B.wall_xyz[2 * nw + k] = z;
+    T ox, oy, oz;
+    Local<T>::enc(P, B.ctab, decode(B.wall_key[k], P), x, y, z, ox, oy, oz);
+    out[k] = WR::make(ox, oy, oz);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1216,6 +1268,31 @@ inline int grid_for(int n, int block, int cap) {
 // Records ev[k] before stage k (and ev[kStages] after the last) when given.
 inline void mark(cudaEvent_t* ev, int k, cudaStream_t s) {
   if (ev) cudaEventRecord(ev[k], s);
+}
+
+// Translating walls binned again: placed at the binning time, keys, a stable
+// sort in the wall buffers, the gather of records and ids, the wall offsets.
+template <int D, class T>
+void enqueue_wall_rebin_t(const StageArgs& a, cudaStream_t s, int gated, int now) {
+  const Params& P = a.P;
+  const LaunchCfg& L = a.L;
+  if (P.nw <= 0) return;
+  DevBuffers W = a.B;
+  const size_t nw = (size_t)P.nw;
+  const int gw = grid_for(P.nw, 256, L.blocks_stream);
+  k_wall_place<D><<<gw, 256, 0, s>>>(P, W, gated, now);
+  const double* xs[3] = {W.wall_io, W.wall_io + nw, W.wall_io + 2 * nw};
+  launch_cell_keys(P, L, xs, W.wkeys[0], W.wvals[0], P.nw, W.sc, gated, W.digit_total, s);
+  const int cur = launch_radix_sort(L, W.wkeys, W.wvals, P.nw, W.wtile_hist, W.digit_total, W.sc,
+                                    gated, s);
+  W.keys[0] = W.wkeys[0];
+  W.keys[1] = W.wkeys[1];
+  W.vals[0] = W.wvals[0];
+  W.vals[1] = W.wvals[1];
+  W.sorted_buf = cur;
+  k_wall_gather<D, T><<<gw, 256, 0, s>>>(P, W, xs[0], xs[1], xs[2], W.wall_xyz,
+                                         W.wall_xyz + nw, W.wall_xyz + 2 * nw, W.wall_v0, gated);
+  launch_cell_offsets(W.wkeys[cur], P.nw, P.ncell, W.wall_cb, W.sc, gated, 0, s);
 }
 
 template <int D, class T>
@@ -1234,6 +1311,7 @@ void enqueue_rebuild(const StageArgs& a, cudaStream_t s, int gated, cudaEvent_t*
       P, B, gated);
   mark(ev, kStageOffsets, s);
   launch_cell_offsets(B.keys[B.sorted_buf], P.n, P.ncell, B.cell_begin, B.sc, gated, 1, s);
+  if (P.variant & kVariantTranslatingWall) enqueue_wall_rebin_t<D, T>(a, s, gated, 0);
 }
 
 // Stages after the rebuild of an advection step; gated: each kernel returns at
@@ -1268,10 +1346,14 @@ void enqueue_acoustic_t(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev = nu
   const KC<T> k = make_kc<T>(P);
   const int gl = grid_for(P.n, L.block_loop, L.blocks_loop);
   const int gs = grid_for(P.n, L.block_stream, L.blocks_stream);
+  const bool translating = (P.variant & kVariantTranslatingWall) && P.nw > 0;
+  const int gw = grid_for(P.nw, 256, L.blocks_stream);
   mark(ev, kStageHalf1, s);
   k_half1<D, T><<<gs, L.block_stream, 0, s>>>(P, B);
+  if (translating) k_wall_move<D, T><<<gw, 256, 0, s>>>(P, B, 1);
   mark(ev, kStagePressure, s);
   k_pressure<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k);
+  if (translating) k_wall_move<D, T><<<gw, 256, 0, s>>>(P, B, 0);
   mark(ev, kStageDensityRelax, s);
   k_density_relax<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k);
   mark(ev, kStages, s);
@@ -1318,7 +1400,7 @@ void enqueue_wall_setup_t(const StageArgs& a, cudaStream_t s) {
   // velocity staging after the positions: io + 3 nw (x | y | z)
   const double* uv = B.wall_vel ? B.io + 3 * (size_t)P.nw : nullptr;
   k_wall_gather<D, T><<<grid_for(P.nw, 256, L.blocks_stream), 256, 0, s>>>(P, B, ux, uy, uz, wx,
-                                                                          wy, wz, uv);
+                                                                          wy, wz, uv, 0);
   launch_cell_offsets(B.keys[B.sorted_buf], P.nw, P.ncell, B.wall_cb, B.sc, 0, 0, s);
 }
 

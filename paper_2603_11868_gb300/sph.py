@@ -50,7 +50,8 @@ EXPORTS = ("sph_create", "sph_set_particles", "sph_step", "sph_get_fields", "sph
            "sph_batch_count", "sph_batch_tank_count", "sph_batch_cell_count",
            "sph_batch_profile_stages", "sph_batch_kernels_per_step", "sph_batch_set_option",
            "sph_batch_synchronize", "sph_batch_last_error", "sph_batch_destroy",
-           "sph_autotune", "sph_batch_autotune", "sph_debug_list_lengths")
+           "sph_autotune", "sph_batch_autotune", "sph_debug_list_lengths",
+           "sph_set_wall_translation")
 SPH_MAX_TANKS = 1024
 SPH_NOALLOC_MAX_PARTICLES = 1 << 20
 STAGE_NAMES = ("control", "keys", "sort", "reorder", "offsets", "density_sum", "viscous",
@@ -114,6 +115,8 @@ def load(path: str | None = None):
                                  C.POINTER(sph_allocator), vp, C.POINTER(vp)]
         L.sph_set_particles.restype = i
         L.sph_set_particles.argtypes = [vp, i, sz, vp, vp, vp]
+        L.sph_set_wall_translation.restype = i
+        L.sph_set_wall_translation.argtypes = [vp, vp]
         L.sph_step.restype = i
         L.sph_step.argtypes = [vp, i]
         L.sph_get_fields.restype = i
@@ -234,6 +237,11 @@ def sph_set_particles(ctx, kind, pos, vel=None, rho=None):
     rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
     _check(ctx, load().sph_set_particles(ctx, int(kind), len(pos), _ptr(pos), _ptr(vel),
                                          _ptr(rho)))
+
+
+def sph_set_wall_translation(ctx, moves=None):
+    moves = None if moves is None else np.ascontiguousarray(moves, dtype=np.uint8)
+    _check(ctx, load().sph_set_wall_translation(ctx, _ptr(moves)))
 
 
 def sph_step(ctx, n):
@@ -500,6 +508,10 @@ class Batch:
     def __init__(self, cases, precision: str = "mixed", torch_memory: bool = True,
                  stream: int | None = None):
         self.cases = list(cases)
+        if any(getattr(c, "wall_moves", None) is not None and np.any(c.wall_moves)
+               for c in self.cases):
+            raise ValueError("batches have no translating walls (sph_set_wall_translation "
+                             "is a single-tank call)")
         self.dim = self.cases[0].dim
         self.precision = SPH_FP64 if precision == "fp64" else SPH_MIXED
         self._allocator = None
@@ -639,6 +651,8 @@ class Solver:
                               self._allocator.struct if self._allocator else None, stream or 0)
         if case.wall is not None and len(case.wall):
             sph_set_particles(self.ctx, SPH_WALL, case.wall, getattr(case, "wall_vel", None))
+            if getattr(case, "wall_moves", None) is not None:
+                sph_set_wall_translation(self.ctx, case.wall_moves)
         sph_set_particles(self.ctx, SPH_FLUID, case.fluid, case.vel, case.rho)
 
     @property

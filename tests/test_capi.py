@@ -113,3 +113,9 @@ def test_batch_argument_validation_needs_no_device(lib):
     assert lib.sph_batch_step(None, 1) == sph.SPH_E_INVALID
     assert lib.sph_batch_tank_count(None) == 0
     assert lib.sph_batch_destroy(None) is None
+
+
+def test_batches_refuse_translating_walls():
+    from paper_2603_11868_gb300 import cases, sph
+    with pytest.raises(ValueError):
+        sph.Batch([cases.piston_channel_2d()])

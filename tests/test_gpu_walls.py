@@ -145,3 +145,111 @@ def test_sliding_lid_channel_matches_the_closed_form(sph, dp, bar):
     err = np.abs(u - ref).max()
     assert err <= bar * c.meta["U"], (err, u, ref)
     assert abs(u.mean()) <= 0.01 * c.meta["U"]
+
+
+# --------------------------------------------------------------------------
+# translating walls (sph_set_wall_translation)
+def pushing_wall_3d():
+    """3D dam break whose back wall (x < 0) translates into the column."""
+    c = cases.dam_break_3d(dp=0.02, seed=6)
+    back = c.wall[:, 0] < 0
+    wv = np.zeros_like(c.wall)
+    wv[back, 0] = 0.5
+    c.wall_vel = wv
+    c.wall_moves = back.astype(np.uint8)
+    return c
+
+
+TRANSLATING = {"piston_2d": lambda: cases.piston_channel_2d(V=2.0), "push_3d": pushing_wall_3d}
+
+
+@pytest.mark.parametrize("name", sorted(TRANSLATING))
+def test_translating_fp64_one_step(sph, O, name):
+    case = TRANSLATING[name]()
+    got, want = _run(sph, O, case, "fp64", 1)
+    for k in FIELDS:
+        if k == "p":
+            # the piston's fluid starts at rest at the lattice density: after
+            # one step p is round-off on both sides, so it is measured against
+            # the pressure of a unit-speed impact, rho0 c0 (1 m/s)
+            err = np.abs(got[k] - want[k]).max() / max(np.abs(want[k]).max(),
+                                                       case.rho0 * case.c0)
+        else:
+            err = rel(got[k], want[k])
+        assert err <= 1e-10, (k, err)
+
+
+def test_translating_fp64_across_cells(sph, O):
+    """130 steps: the piston crosses more than two cells, so its walls are
+    binned again several times; the states and the neighbour sets agree."""
+    case = TRANSLATING["piston_2d"]()
+    s = sph.Solver(case, precision="fp64")
+    s.step(130)
+    got = s.fields("pos", "vel", "rho", "p")
+    stats = s.neighbour_stats()
+    t = s.scalars()["t"]
+    s.close()
+    o = O.Oracle.from_case(case)
+    o.step(130)
+    assert case.meta["V"] * t > 2.5 * 2 * case.h
+    want = {"pos": o.field(O.POS), "vel": o.field(O.VEL), "rho": o.field(O.RHO),
+            "p": o.field(O.P)}
+    for k in want:
+        assert rel(got[k], want[k]) <= 1e-8, (k, rel(got[k], want[k]))
+    for g, w in zip(stats, o.neighbour_stats()):
+        assert np.array_equal(g, w)
+
+
+@pytest.mark.parametrize("name", sorted(TRANSLATING))
+def test_translating_mixed_one_step(sph, O, name):
+    case = TRANSLATING[name]()
+    got, want = _run(sph, O, case, "mixed", 1)
+    g = max(abs(x) for x in case.gravity) or 1.0
+    for k in ("acc", "aprior"):
+        err = np.abs(got[k] - want[k]).max() / max(np.abs(want[k]).max(), g)
+        assert err <= 1e-5, (k, err)
+    assert rel(got["rho"], want["rho"]) <= 1e-6
+
+
+def test_translating_mixed_long_run_tracks_the_oracle(sph, O):
+    case = TRANSLATING["piston_2d"]()
+    s = sph.Solver(case, precision="mixed")
+    s.step(130)
+    got = s.fields("pos", "rho")
+    s.close()
+    o = O.Oracle.from_case(case)
+    o.step(130)
+    assert np.abs(got["pos"] - o.field(O.POS)).max() <= 1e-3 * case.dp
+    assert rel(got["rho"], o.field(O.RHO)) <= 1e-5
+
+
+def test_piston_acoustic_state_on_the_gpu(sph):
+    from test_oracle_walls import piston_plateau  # same folder (pytest prepends it)
+    c = cases.piston_channel_2d()
+    s = sph.Solver(c, precision="mixed")
+    while s.scalars()["t"] < 0.1:
+        s.step(1)
+    t = s.scalars()["t"]
+    f = s.fields("pos", "vel", "p")
+    s.close()
+    plateau, ahead = piston_plateau(f["pos"], f["vel"], f["p"], c, t)
+    V = c.meta["V"]
+    assert abs(f["p"][plateau].mean() / (c.rho0 * c.c0 * V) - 1) < 0.03
+    assert abs(f["vel"][plateau, 0].mean() / V - 1) < 0.03
+    assert np.abs(f["p"][ahead]).max() < 1e-3 * c.rho0 * c.c0 * V
+
+
+def test_clearing_the_translation_puts_the_walls_back(sph, O):
+    case = TRANSLATING["piston_2d"]()
+    s = sph.Solver(case, precision="fp64")
+    s.step(40)
+    sph.sph_set_wall_translation(s.ctx, None)
+    s.step(5)
+    got = s.fields("pos", "rho")
+    s.close()
+    o = O.Oracle.from_case(case)
+    o.step(40)
+    o.set_wall_translation(None)
+    o.step(5)
+    assert rel(got["pos"], o.field(O.POS)) <= 1e-10
+    assert rel(got["rho"], o.field(O.RHO)) <= 1e-10

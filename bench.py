@@ -539,6 +539,8 @@ def run_ours(args):
             "fp64_value": fp64,
             "speedup_vs_fp64": (value / ws / fp64) if fp64 else None,
             "gpips": (value * mean_nb * 2 / 1e9) if mean_nb else None,
+            # the same throughput counting wall particles too
+            "fluid_and_wall_steps_per_s": value * (n + nw) / n,
             "sim_time": sc["t"], "source_fingerprint": fp, "tuning": tuning,
         }
         print(json.dumps(line), flush=True)

@@ -166,6 +166,34 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
 int sph_set_particles(sph_ctx* ctx, int kind, size_t n, const double* pos, const double* vel,
                       const double* rho);
 
+/* Checkpoint / resume.  A checkpoint holds the schedule state (time, step
+ * counters, advection-step clock, time steps, velocity maximum, list bounds,
+ * error flags) and every fluid particle's live state in storage order:
+ * position, velocity, density (double), carried density rate and prior
+ * acceleration (the precision's pair type), user id and binned cell key.
+ * Restored into a context with the same setup (sph_create arguments, wall
+ * particles and their velocities, wall translation, method options), the
+ * run continues exactly as it would have: the same bits in either precision.
+ * Walls are not stored; translating walls are placed from the stored times.
+ * The neighbour lists are built anew from the stored positions with the
+ * stored skin; they accept the same pairs in the same order, so the sums are
+ * those of the uninterrupted run.
+ *
+ * sph_checkpoint_bytes: size of a checkpoint of the current state (0 without
+ *   fluid particles).  No synchronisation.
+ * sph_checkpoint_save: writes it into buf (host, at least that many bytes);
+ *   synchronises; returns the sticky device error, if any, after writing.
+ *   SPH_E_STATE without fluid particles, SPH_E_INVALID for a missing or
+ *   short buffer.
+ * sph_checkpoint_load: replaces the fluid particles and the schedule state by
+ *   the checkpoint in buf (bytes long).  SPH_E_INVALID for a buffer that is
+ *   not a checkpoint of this library version, is too short, or belongs to a
+ *   different setup (domain, spacing, material, gravity, precision, wall
+ *   count, translation or method options). */
+size_t sph_checkpoint_bytes(const sph_ctx* ctx);
+int sph_checkpoint_save(sph_ctx* ctx, void* buf, size_t bytes);
+int sph_checkpoint_load(sph_ctx* ctx, const void* buf, size_t bytes);
+
 /* Makes walls translate: moves (nw bytes, user order of the last SPH_WALL
  * set) marks the wall particles that move with their prescribed velocity,
  * x_w(t) = x_w(0) + v_w t, t the simulation time and x_w(0) the position

@@ -588,6 +588,185 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
   return set_err(c, SPH_E_INVALID, "unknown particle kind");
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoints: the schedule scalars and the live state in storage order
+// (positions, velocities, densities, carried density rates, prior
+// accelerations, user ids, binned cell keys), behind a header that names the
+// setup it belongs to.
+namespace {
+constexpr char kCkptMagic[8] = {'S', 'P', 'H', 'C', 'K', 'P', 'T', '1'};
+constexpr int32_t kCkptVersion = 1;
+
+struct CkptHeader {
+  char magic[8];
+  int32_t version, dim, precision, variant;
+  int64_t n, nw, ncell;
+  int32_t nx, ny, nz, pad_;
+  double h, cs, rho0, c0, mu, U_ref, m, V, wall_vmax;
+  double lo[3], g[3];
+  uint64_t scalars_bytes;
+};
+
+void ckpt_header(const sph_ctx* c, CkptHeader* hd) {
+  memset(hd, 0, sizeof(*hd));
+  memcpy(hd->magic, kCkptMagic, 8);
+  const Params& P = c->P;
+  hd->version = kCkptVersion;
+  hd->dim = P.dim;
+  hd->precision = c->precision;
+  hd->variant = P.variant;
+  hd->n = P.n;
+  hd->nw = P.nw;
+  hd->ncell = P.ncell;
+  hd->nx = P.nx;
+  hd->ny = P.ny;
+  hd->nz = P.nz;
+  hd->h = P.h;
+  hd->cs = P.cs;
+  hd->rho0 = P.rho0;
+  hd->c0 = P.c0;
+  hd->mu = P.mu;
+  hd->U_ref = P.U_ref;
+  hd->m = P.m;
+  hd->V = P.V;
+  hd->wall_vmax = P.wall_vmax;
+  for (int k = 0; k < 3; ++k) {
+    hd->lo[k] = P.lo[k];
+    hd->g[k] = P.g[k];
+  }
+  hd->scalars_bytes = sizeof(DevScalars);
+}
+
+// bytes per fluid particle: x, v (double), rho (double), drho (pair type),
+// a_prior (pair type), id, binned key
+size_t ckpt_per_particle(const sph_ctx* c) {
+  const size_t d = (size_t)c->P.dim, ts = tsize(c);
+  return 2 * d * 8 + 8 + ts + d * ts + 4 + 4;
+}
+}  // namespace
+
+size_t sph_checkpoint_bytes(const sph_ctx* c) {
+  if (!c || !c->fluid_set) return 0;
+  return sizeof(CkptHeader) + sizeof(DevScalars) + (size_t)c->P.n * ckpt_per_particle(c);
+}
+
+int sph_checkpoint_save(sph_ctx* c, void* buf, size_t bytes) {
+  if (!c) return SPH_E_INVALID;
+  if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
+  if (!buf || bytes < sph_checkpoint_bytes(c))
+    return set_err(c, SPH_E_INVALID, "checkpoint buffer missing or too small");
+  int rc = enter(c);
+  if (rc) return rc;
+  DevScalars hs;
+  rc = read_scalars(c, &hs);
+  if (rc) return rc;
+  CkptHeader hd;
+  ckpt_header(c, &hd);
+  char* p = (char*)buf;
+  memcpy(p, &hd, sizeof(hd));
+  p += sizeof(hd);
+  memcpy(p, &hs, sizeof(hs));
+  p += sizeof(hs);
+  const size_t n = (size_t)c->P.n, ts = tsize(c);
+  const int d = c->P.dim, par = hs.par;
+  const DevBuffers& B = c->B;
+  auto D2H = [&](const void* src, size_t nbytes) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(p, src, nbytes, cudaMemcpyDeviceToHost, c->stream);
+    p += nbytes;
+    return e;
+  };
+  for (int k = 0; k < d; ++k) CK(D2H(B.x[par][k], n * 8));
+  for (int k = 0; k < d; ++k) CK(D2H(B.v[par][k], n * 8));
+  CK(D2H(B.rho[par], n * 8));
+  CK(D2H(B.drho[par], n * ts));
+  for (int k = 0; k < d; ++k) CK(D2H(B.aprior[k], n * ts));
+  CK(D2H(B.id[par], n * 4));
+  CK(D2H(B.keys[B.sorted_buf], n * 4));
+  CK(cudaStreamSynchronize(c->stream));
+  rc = leave(c);
+  return rc ? rc : flags_status(c, hs);
+}
+
+int sph_checkpoint_load(sph_ctx* c, const void* buf, size_t bytes) {
+  if (!c) return SPH_E_INVALID;
+  if (!buf || bytes < sizeof(CkptHeader) + sizeof(DevScalars))
+    return set_err(c, SPH_E_INVALID, "checkpoint buffer missing or too small");
+  CkptHeader hd, mine;
+  memcpy(&hd, buf, sizeof(hd));
+  if (memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != kCkptVersion ||
+      hd.scalars_bytes != sizeof(DevScalars))
+    return set_err(c, SPH_E_INVALID, "not a checkpoint of this library version");
+  ckpt_header(c, &mine);
+  const bool same = hd.dim == mine.dim && hd.precision == mine.precision &&
+                    hd.variant == mine.variant && hd.nw == mine.nw && hd.ncell == mine.ncell &&
+                    hd.nx == mine.nx && hd.ny == mine.ny && hd.nz == mine.nz &&
+                    hd.h == mine.h && hd.cs == mine.cs && hd.rho0 == mine.rho0 &&
+                    hd.c0 == mine.c0 && hd.mu == mine.mu && hd.U_ref == mine.U_ref &&
+                    hd.m == mine.m && hd.V == mine.V && hd.wall_vmax == mine.wall_vmax &&
+                    memcmp(hd.lo, mine.lo, sizeof(hd.lo)) == 0 &&
+                    memcmp(hd.g, mine.g, sizeof(hd.g)) == 0;
+  if (!same)
+    return set_err(c, SPH_E_INVALID,
+                   "checkpoint of a different setup (domain, material, precision, walls, "
+                   "translation or method options)");
+  if (hd.n <= 0 || hd.n >= (1ll << 25)) return set_err(c, SPH_E_INVALID, "bad particle count");
+  const size_t n = (size_t)hd.n;
+  if (bytes < sizeof(CkptHeader) + sizeof(DevScalars) + n * ckpt_per_particle(c))
+    return set_err(c, SPH_E_INVALID, "checkpoint buffer too small for its particle count");
+  int rc = enter(c);
+  if (rc) return rc;
+  rc = alloc_fluid(c, n);
+  if (rc) return rc;
+  drop_graph(c);
+  c->P.n = (int)n;
+  configure_launch(c);
+  DevScalars hs;
+  const char* p = (const char*)buf + sizeof(hd);
+  memcpy(&hs, p, sizeof(hs));
+  p += sizeof(hs);
+  // the state goes to copy 0; the lists are built anew below
+  hs.par = 0;
+  const size_t ts = tsize(c);
+  const int d = c->P.dim;
+  DevBuffers& B = c->B;
+  auto H2D = [&](void* dst, size_t nbytes) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(dst, p, nbytes, cudaMemcpyHostToDevice, c->stream);
+    p += nbytes;
+    return e;
+  };
+  for (int k = 0; k < d; ++k) CK(H2D(B.x[0][k], n * 8));
+  for (int k = 0; k < d; ++k) CK(H2D(B.v[0][k], n * 8));
+  CK(H2D(B.rho[0], n * 8));
+  CK(H2D(B.drho[0], n * ts));
+  for (int k = 0; k < d; ++k) CK(H2D(B.aprior[k], n * ts));
+  CK(H2D(B.id[0], n * 4));
+  CK(H2D(B.keys[B.sorted_buf], n * 4));
+  for (int k = 0; k < d; ++k) CK(cudaMemsetAsync(B.acc[k], 0, n * ts, c->stream));
+  CK(cudaMemsetAsync(B.sigma, 0, n * ts, c->stream));
+  CK(cudaMemcpyAsync(B.sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, c->stream));
+  launch_cell_offsets(B.keys[B.sorted_buf], (int)n, c->P.ncell, B.cell_begin, B.sc, 0, 0,
+                      c->stream);
+  // translating walls: binned at the saved rebuild time, moved to the saved time
+  if ((c->P.variant & kVariantTranslatingWall) && c->P.nw > 0) {
+    if (c->precision == SPH_FP64)
+      enqueue_wall_rebin_fp64(args(c), c->stream, 1);
+    else
+      enqueue_wall_rebin_mixed(args(c), c->stream, 1);
+  }
+  // neighbour lists from the restored positions with the saved skin (a list
+  // that overflowed before the save stays marked bad)
+  if (!hs.list_bad) {
+    if (c->precision == SPH_FP64)
+      enqueue_restore_lists_fp64(args(c), c->stream);
+    else
+      enqueue_restore_lists_mixed(args(c), c->stream);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  c->fluid_set = true;
+  return leave(c);
+}
+
 int sph_set_wall_translation(sph_ctx* c, const uint8_t* moves) {
   if (!c) return SPH_E_INVALID;
   int rc = enter(c);
@@ -639,9 +818,9 @@ int sph_set_wall_translation(sph_ctx* c, const uint8_t* moves) {
   // walls binned again where they are now (back at their given positions
   // when none translates)
   if (c->precision == SPH_FP64)
-    enqueue_wall_rebin_fp64(args(c), c->stream);
+    enqueue_wall_rebin_fp64(args(c), c->stream, 0);
   else
-    enqueue_wall_rebin_mixed(args(c), c->stream);
+    enqueue_wall_rebin_mixed(args(c), c->stream, 0);
   CK(cudaGetLastError());
   CK(invalidate_lists(c));
   CK(cudaStreamSynchronize(c->stream));

@@ -38,11 +38,19 @@ void enqueue_wall_setup_fp64(const StageArgs& a, cudaStream_t s) {
     stages::enqueue_wall_setup_t<3, double>(a, s);
 }
 
-void enqueue_wall_rebin_fp64(const StageArgs& a, cudaStream_t s) {
+void enqueue_wall_rebin_fp64(const StageArgs& a, cudaStream_t s, int at_rebuild) {
+  const int when = at_rebuild ? stages::kBinAtRebuild : stages::kBinNow;
   if (a.P.dim == 2)
-    stages::enqueue_wall_rebin_t<2, double>(a, s, 0, 1);
+    stages::enqueue_wall_rebin_t<2, double>(a, s, 0, when);
   else
-    stages::enqueue_wall_rebin_t<3, double>(a, s, 0, 1);
+    stages::enqueue_wall_rebin_t<3, double>(a, s, 0, when);
+}
+
+void enqueue_restore_lists_fp64(const StageArgs& a, cudaStream_t s) {
+  if (a.P.dim == 2)
+    stages::enqueue_restore_lists_t<2, double>(a, s);
+  else
+    stages::enqueue_restore_lists_t<3, double>(a, s);
 }
 
 }  // namespace sphgb

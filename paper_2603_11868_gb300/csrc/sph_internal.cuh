@@ -322,11 +322,17 @@ void enqueue_initial_sort_mixed(const StageArgs& a, cudaStream_t s);
 // to scratch of its own so that the fluid's sorted keys survive.
 void enqueue_wall_setup_fp64(const StageArgs& a, cudaStream_t s);
 void enqueue_wall_setup_mixed(const StageArgs& a, cudaStream_t s);
-// Walls binned again at the current time (sc->t): positions x0 + t v0 for the
-// translating walls, x0 for the others, then the sort in the wall buffers of
-// `a.B` (wall_io, wkeys, wvals, wtile_hist), the gather and the wall offsets.
-void enqueue_wall_rebin_fp64(const StageArgs& a, cudaStream_t s);
-void enqueue_wall_rebin_mixed(const StageArgs& a, cudaStream_t s);
+// Walls binned again: positions x0 + t v0 for the translating walls, x0 for
+// the others, at the current time (sc->t), or with at_rebuild at the time of
+// the last rebuild (sc->t_reb) and then moved on to the current time (a
+// restored state); the sort runs in the wall buffers of `a.B` (wall_io,
+// wkeys, wvals, wtile_hist), then the gather and the wall offsets.
+void enqueue_wall_rebin_fp64(const StageArgs& a, cudaStream_t s, int at_rebuild);
+void enqueue_wall_rebin_mixed(const StageArgs& a, cudaStream_t s, int at_rebuild);
+// Neighbour lists of a restored state, built from its current positions with
+// its stored skin (the loops then give the sums of the uninterrupted run).
+void enqueue_restore_lists_fp64(const StageArgs& a, cudaStream_t s);
+void enqueue_restore_lists_mixed(const StageArgs& a, cudaStream_t s);
 
 // --- neighbour search (sph_nsearch.cu), precision independent
 // keys from positions x[par] (or an explicit coordinate set), vals = iota

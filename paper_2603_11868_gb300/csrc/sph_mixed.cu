@@ -55,11 +55,19 @@ void enqueue_wall_setup_mixed(const StageArgs& a, cudaStream_t s) {
     stages::enqueue_wall_setup_t<3, float>(a, s);
 }
 
-void enqueue_wall_rebin_mixed(const StageArgs& a, cudaStream_t s) {
+void enqueue_wall_rebin_mixed(const StageArgs& a, cudaStream_t s, int at_rebuild) {
+  const int when = at_rebuild ? stages::kBinAtRebuild : stages::kBinNow;
   if (a.P.dim == 2)
-    stages::enqueue_wall_rebin_t<2, float>(a, s, 0, 1);
+    stages::enqueue_wall_rebin_t<2, float>(a, s, 0, when);
   else
-    stages::enqueue_wall_rebin_t<3, float>(a, s, 0, 1);
+    stages::enqueue_wall_rebin_t<3, float>(a, s, 0, when);
+}
+
+void enqueue_restore_lists_mixed(const StageArgs& a, cudaStream_t s) {
+  if (a.P.dim == 2)
+    stages::enqueue_restore_lists_t<2, float>(a, s);
+  else
+    stages::enqueue_restore_lists_t<3, float>(a, s);
 }
 
 }  // namespace sphgb

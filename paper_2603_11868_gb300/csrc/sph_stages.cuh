@@ -418,6 +418,26 @@ __device__ __forceinline__ void reorder_slot(const Params& P, const DevBuffers& 
   }
 }
 
+// Loop records of buffer 0 from the live state as it stands (no update), in
+// the frame of each slot's binned cell: the positions a list build reads.
+template <int D, class T>
+__global__ void k_encode_records(Params P, DevBuffers B) {
+  using R = Rec<D, T>;
+  const Live<T> S = live<T>(B, B.sc->par);
+  typename R::PV* recP = (typename R::PV*)B.recP[0];
+  typename R::SV* recS = (typename R::SV*)B.recS[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    const double x = S.x0[i], y = S.x1[i], z = D == 3 ? S.x2[i] : 0.0;
+    const double vx = S.v0[i], vy = S.v1[i], vz = D == 3 ? S.v2[i] : 0.0;
+    const double rho = S.rho[i];
+    T ox, oy, oz;
+    Local<T>::enc(P, B.ctab, decode(B.binned[i], P), x, y, z, ox, oy, oz);
+    const T p = (T)(P.c0sq * (rho - P.rho0));
+    recP[i] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p);
+    recS[i] = R::makeS((T)vx, (T)vy, (T)vz, (T)rho, p);
+  }
+}
+
 template <int D, class T>
 __global__ void k_reorder(Params P, DevBuffers B, int gated) {
   DevScalars* sc = B.sc;
@@ -1214,13 +1234,17 @@ __global__ void k_wall_gather(Params P, DevBuffers B, const double* __restrict__
 }
 
 // Translating walls.  k_wall_place writes every wall's position at the
-// binning time (the step's start time at a rebuild, the current time when
-// `now`) into wall_io: x0 + t v0 for a translating wall, x0 for the others.
+// binning time into wall_io: x0 + t v0 for a translating wall, x0 for the
+// others.  The binning time is the step's start time at a rebuild
+// (kBinAtStepStart), the current time (kBinNow), or the time of the last
+// rebuild (kBinAtRebuild, when a saved state is restored).
+constexpr int kBinAtStepStart = 0, kBinNow = 1, kBinAtRebuild = 2;
+
 template <int D>
-__global__ void k_wall_place(Params P, DevBuffers B, int gated, int now) {
+__global__ void k_wall_place(Params P, DevBuffers B, int gated, int when) {
   DevScalars* sc = B.sc;
   if (gated && !sc->new_adv) return;
-  const double t = now ? sc->t : sc->t0;
+  const double t = when == kBinNow ? sc->t : (when == kBinAtRebuild ? sc->t_reb : sc->t0);
   const size_t nw = (size_t)P.nw;
   for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < nw;
        u += (size_t)gridDim.x * blockDim.x) {
@@ -1272,15 +1296,17 @@ inline void mark(cudaEvent_t* ev, int k, cudaStream_t s) {
 
 // Translating walls binned again: placed at the binning time, keys, a stable
 // sort in the wall buffers, the gather of records and ids, the wall offsets.
+// kBinAtRebuild then moves the walls on to the current time, as the steps
+// since that rebuild left them.
 template <int D, class T>
-void enqueue_wall_rebin_t(const StageArgs& a, cudaStream_t s, int gated, int now) {
+void enqueue_wall_rebin_t(const StageArgs& a, cudaStream_t s, int gated, int when) {
   const Params& P = a.P;
   const LaunchCfg& L = a.L;
   if (P.nw <= 0) return;
   DevBuffers W = a.B;
   const size_t nw = (size_t)P.nw;
   const int gw = grid_for(P.nw, 256, L.blocks_stream);
-  k_wall_place<D><<<gw, 256, 0, s>>>(P, W, gated, now);
+  k_wall_place<D><<<gw, 256, 0, s>>>(P, W, gated, when);
   const double* xs[3] = {W.wall_io, W.wall_io + nw, W.wall_io + 2 * nw};
   launch_cell_keys(P, L, xs, W.wkeys[0], W.wvals[0], P.nw, W.sc, gated, W.digit_total, s);
   const int cur = launch_radix_sort(L, W.wkeys, W.wvals, P.nw, W.wtile_hist, W.digit_total, W.sc,
@@ -1293,6 +1319,7 @@ void enqueue_wall_rebin_t(const StageArgs& a, cudaStream_t s, int gated, int now
   k_wall_gather<D, T><<<gw, 256, 0, s>>>(P, W, xs[0], xs[1], xs[2], W.wall_xyz,
                                          W.wall_xyz + nw, W.wall_xyz + 2 * nw, W.wall_v0, gated);
   launch_cell_offsets(W.wkeys[cur], P.nw, P.ncell, W.wall_cb, W.sc, gated, 0, s);
+  if (when == kBinAtRebuild) k_wall_move<D, T><<<gw, 256, 0, s>>>(P, W, 0);
 }
 
 template <int D, class T>
@@ -1311,7 +1338,7 @@ void enqueue_rebuild(const StageArgs& a, cudaStream_t s, int gated, cudaEvent_t*
       P, B, gated);
   mark(ev, kStageOffsets, s);
   launch_cell_offsets(B.keys[B.sorted_buf], P.n, P.ncell, B.cell_begin, B.sc, gated, 1, s);
-  if (P.variant & kVariantTranslatingWall) enqueue_wall_rebin_t<D, T>(a, s, gated, 0);
+  if (P.variant & kVariantTranslatingWall) enqueue_wall_rebin_t<D, T>(a, s, gated, kBinAtStepStart);
 }
 
 // Stages after the rebuild of an advection step; gated: each kernel returns at
@@ -1374,6 +1401,23 @@ template <int D, class T>
 void enqueue_advection_t(const StageArgs& a, cudaStream_t s) {
   enqueue_rebuild<D, T>(a, s, 0, nullptr);
   enqueue_advection_loops<D, T>(a, s, 0, nullptr);
+}
+
+// Lists for a restored state: built from the positions as they stand with
+// the stored skin.  Every pair that comes within 2h before the next rebuild
+// is in them while the stored displacement bound holds (it counts the drift
+// since the rebuild, which covers the drift since now), and a list's sums
+// depend only on the pairs within 2h, visited in candidate order: the same
+// sums as the lists of the rebuild.
+template <int D, class T>
+void enqueue_restore_lists_t(const StageArgs& a, cudaStream_t s) {
+  const Params& P = a.P;
+  const LaunchCfg& L = a.L;
+  if (!P.use_list || P.n <= 0) return;
+  k_encode_records<D, T><<<grid_for(P.n, L.block_stream, L.blocks_stream), L.block_stream, 0,
+                           s>>>(P, a.B);
+  k_build_lists<D, T><<<grid_for(P.n, L.block_loop, L.blocks_loop), L.block_loop, 0, s>>>(
+      P, a.B, make_kc<T>(P), 0);
 }
 
 template <int D, class T>

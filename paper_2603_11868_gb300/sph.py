@@ -51,7 +51,8 @@ EXPORTS = ("sph_create", "sph_set_particles", "sph_step", "sph_get_fields", "sph
            "sph_batch_profile_stages", "sph_batch_kernels_per_step", "sph_batch_set_option",
            "sph_batch_synchronize", "sph_batch_last_error", "sph_batch_destroy",
            "sph_autotune", "sph_batch_autotune", "sph_debug_list_lengths",
-           "sph_set_wall_translation")
+           "sph_set_wall_translation", "sph_checkpoint_bytes", "sph_checkpoint_save",
+           "sph_checkpoint_load")
 SPH_MAX_TANKS = 1024
 SPH_NOALLOC_MAX_PARTICLES = 1 << 20
 STAGE_NAMES = ("control", "keys", "sort", "reorder", "offsets", "density_sum", "viscous",
@@ -117,6 +118,12 @@ def load(path: str | None = None):
         L.sph_set_particles.argtypes = [vp, i, sz, vp, vp, vp]
         L.sph_set_wall_translation.restype = i
         L.sph_set_wall_translation.argtypes = [vp, vp]
+        L.sph_checkpoint_bytes.restype = sz
+        L.sph_checkpoint_bytes.argtypes = [vp]
+        L.sph_checkpoint_save.restype = i
+        L.sph_checkpoint_save.argtypes = [vp, vp, sz]
+        L.sph_checkpoint_load.restype = i
+        L.sph_checkpoint_load.argtypes = [vp, vp, sz]
         L.sph_step.restype = i
         L.sph_step.argtypes = [vp, i]
         L.sph_get_fields.restype = i
@@ -242,6 +249,18 @@ def sph_set_particles(ctx, kind, pos, vel=None, rho=None):
 def sph_set_wall_translation(ctx, moves=None):
     moves = None if moves is None else np.ascontiguousarray(moves, dtype=np.uint8)
     _check(ctx, load().sph_set_wall_translation(ctx, _ptr(moves)))
+
+
+def sph_checkpoint_save(ctx):
+    n = load().sph_checkpoint_bytes(ctx)
+    buf = np.empty(n, dtype=np.uint8)
+    _check(ctx, load().sph_checkpoint_save(ctx, _ptr(buf), n))
+    return buf
+
+
+def sph_checkpoint_load(ctx, buf):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(ctx, load().sph_checkpoint_load(ctx, _ptr(buf), buf.size))
 
 
 def sph_step(ctx, n):
@@ -699,6 +718,14 @@ class Solver:
 
     def neighbour_stats(self):
         return sph_debug_neighbour_stats(self.ctx, self.n)
+
+    def checkpoint(self) -> np.ndarray:
+        """The run's state as a byte array (sph_checkpoint_save)."""
+        return sph_checkpoint_save(self.ctx)
+
+    def restore(self, buf) -> None:
+        """Continue from a checkpoint of a solver with the same setup."""
+        sph_checkpoint_load(self.ctx, buf)
 
     def profile_stages(self, n: int):
         return sph_profile_stages(self.ctx, n)

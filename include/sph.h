@@ -87,7 +87,8 @@ enum sph_status {
   SPH_E_OUT_OF_DOMAIN = 4,  /* a particle left the box: it was clamped into the edge cell */
   SPH_E_NONFINITE = 5,      /* a velocity or density became NaN or infinite            */
   SPH_E_TIMEOUT = 6,        /* sph_synchronize gave up waiting                         */
-  SPH_E_STATE = 7           /* no fluid particles set yet                              */
+  SPH_E_STATE = 7,          /* no fluid particles set yet                              */
+  SPH_E_INDEX = 8           /* debug build only: an index check failed (access skipped) */
 };
 
 enum sph_kind { SPH_FLUID = 0, SPH_WALL = 1 };

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <cstddef>
 #include <cmath>
 #include <string>
 #include <thread>
@@ -182,6 +183,9 @@ int read_scalars(sph_batch* b, std::vector<DevScalars>& hs) {
 
 int flags_status(sph_batch* b, const std::vector<DevScalars>& hs) {
   for (int t = 0; t < (int)hs.size(); ++t) {
+    if (hs[t].flags & kFlagIndex)
+      return set_err(b, SPH_E_INDEX, "an index check of the debug build failed (recorded on "
+                                     "tank " + std::to_string(t) + ")");
     if (hs[t].flags & kFlagNonFinite)
       return set_err(b, SPH_E_NONFINITE,
                      "tank " + std::to_string(t) + ": a velocity or density became non-finite");
@@ -415,6 +419,8 @@ int sph_create_batch(int n_tanks, const sph_tank* tanks, int precision,
   b->A.tP = (const Params*)Af(sizeof(Params) * n_tanks);
   b->A.tK = Af(ksize * n_tanks);
   b->A.tsc = (DevScalars*)Af(sizeof(DevScalars) * n_tanks);
+  // debug-build index checks record on tank 0's flags
+  b->B.dbg_flags = b->A.tsc ? (int*)((char*)b->A.tsc + offsetof(DevScalars, flags)) : nullptr;
   b->A.wl_all = (WorkList*)Af(sizeof(WorkList));
   b->A.wl_adv = (WorkList*)Af(sizeof(WorkList));
   b->A.wl_wall = (WorkList*)Af(sizeof(WorkList));

@@ -224,6 +224,8 @@ int read_scalars(sph_ctx* c, DevScalars* hs) {
 }
 
 int flags_status(sph_ctx* c, const DevScalars& hs) {
+  if (hs.flags & kFlagIndex)
+    return set_err(c, SPH_E_INDEX, "an index check of the debug build failed");
   if (hs.flags & kFlagNonFinite)
     return set_err(c, SPH_E_NONFINITE, "a velocity or density became non-finite");
   if (hs.flags & kFlagOutOfDomain)
@@ -412,6 +414,7 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
   configure_launch(c);
   // fixed buffers: scalars and the two CSR offset arrays
   c->B.sc = (DevScalars*)dev_alloc(c, sizeof(DevScalars), c->fixed_blocks);
+  c->B.dbg_flags = c->B.sc ? (int*)((char*)c->B.sc + offsetof(DevScalars, flags)) : nullptr;
   c->B.cell_begin = (uint32_t*)dev_alloc(c, ((size_t)P.ncell + 1) * 4, c->fixed_blocks);
   c->B.wall_cb = (uint32_t*)dev_alloc(c, ((size_t)P.ncell + 1) * 4, c->fixed_blocks);
   c->B.digit_total = (uint32_t*)dev_alloc(c, ((size_t)1 << kMaxRadixBits) * 4, c->fixed_blocks);
@@ -713,6 +716,21 @@ int sph_checkpoint_load(sph_ctx* c, const void* buf, size_t bytes) {
   const size_t n = (size_t)hd.n;
   if (bytes < sizeof(CkptHeader) + sizeof(DevScalars) + n * ckpt_per_particle(c))
     return set_err(c, SPH_E_INVALID, "checkpoint buffer too small for its particle count");
+  {
+    // the ids and binned keys index device arrays: check them on the host
+    // (keys in the grid and in storage order, ids a permutation)
+    const char* q = (const char*)buf + sizeof(CkptHeader) + sizeof(DevScalars) +
+                    n * (ckpt_per_particle(c) - 8);
+    const uint32_t* ids = (const uint32_t*)q;
+    const uint32_t* keys = (const uint32_t*)(q + n * 4);
+    std::vector<uint8_t> seen(n, 0);
+    for (size_t k = 0; k < n; ++k) {
+      if (keys[k] >= c->P.ncell || (k > 0 && keys[k] < keys[k - 1]) || ids[k] >= n ||
+          seen[ids[k]])
+        return set_err(c, SPH_E_INVALID, "checkpoint with bad cell keys or particle ids");
+      seen[ids[k]] = 1;
+    }
+  }
   int rc = enter(c);
   if (rc) return rc;
   rc = alloc_fluid(c, n);

@@ -62,6 +62,7 @@ constexpr int kVariantTranslatingWall = 16;
 // error flag bits (sticky, device)
 constexpr int kFlagOutOfDomain = 1;
 constexpr int kFlagNonFinite = 2;
+constexpr int kFlagIndex = 4;  // debug builds: an index check failed (the access was skipped)
 
 struct Params {
   int dim;
@@ -192,10 +193,27 @@ struct DevBuffers {
   uint32_t* wvals[2];
   uint32_t* wtile_hist;
   DevScalars* sc;
+  int* dbg_flags;  // where debug-build index checks record kFlagIndex
   double* io;  // staging, n * dim doubles (also wall staging)
   uint32_t* u32_io;
   unsigned long long* u64_io;
 };
+
+// Debug builds (-DSPH_DEBUG): index checks that record kFlagIndex and skip
+// the access instead of trapping, the stand-in for a memory checker; release
+// builds compile them away.  SPH_DBG_IN(B, i, lo, hi) is lo <= i < hi.
+#ifdef SPH_DEBUG
+__device__ __forceinline__ bool dbg_in(const DevBuffers& B, long long i, long long lo,
+                                       long long hi) {
+  if (i >= lo && i < hi) return true;
+  if (B.dbg_flags) atomicOr(B.dbg_flags, kFlagIndex);
+  return false;
+}
+#define SPH_DBG_IN(B, i, lo, hi) \
+  ::sphgb::dbg_in((B), (long long)(i), (long long)(lo), (long long)(hi))
+#else
+#define SPH_DBG_IN(B, i, lo, hi) true
+#endif
 
 struct LaunchCfg {
   int sms;           // multiprocessors

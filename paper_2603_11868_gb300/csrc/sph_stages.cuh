@@ -392,6 +392,7 @@ __device__ __forceinline__ void reorder_slot(const Params& P, const DevBuffers& 
   using R = Rec<D, T>;
   typename R::PV* recP = (typename R::PV*)B.recP[0];
   typename R::SV* recS = (typename R::SV*)B.recS[0];
+  if (!SPH_DBG_IN(B, j, P.foff, P.foff + P.n)) return;
   {
     double x = S.x0[j], y = S.x1[j], z = D == 3 ? S.x2[j] : 0.0;
     double vx = S.v0[j], vy = S.v1[j], vz = D == 3 ? S.v2[j] : 0.0;
@@ -497,6 +498,9 @@ struct ListWriter {
 template <int D, class V>
 __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffers& B, Cell ci,
                                                  int i, bool use_list, V&& v) {
+  if (!SPH_DBG_IN(B, ci.x, 0, P.nx) || !SPH_DBG_IN(B, ci.y, 0, P.ny) ||
+      !SPH_DBG_IN(B, ci.z, 0, D == 3 ? P.nz : 1))
+    return;
   if (use_list) {
     const int cnt = (int)B.nl_cnt[i];
     const uint32_t* __restrict__ e = B.nl + nl_slot(i, 0, P.list_cap);
@@ -508,8 +512,10 @@ __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffe
       const uint32_t x = x0;
       x0 = x1;
       x1 = k + 2 < cnt ? __ldcs(e + (size_t)(k + 2) * 32u) : 0u;
-      v((int)(x & kIdxMask), (int)((x >> 25) & 3u) - 1, (int)((x >> 27) & 3u) - 1,
-        (int)((x >> 29) & 3u) - 1, (x >> 31) != 0u);
+      const int j = (int)(x & kIdxMask);
+      const bool w = (x >> 31) != 0u;
+      if (!SPH_DBG_IN(B, j, w ? P.woff : P.foff, w ? P.woff + P.nw : P.foff + P.n)) continue;
+      v(j, (int)((x >> 25) & 3u) - 1, (int)((x >> 27) & 3u) - 1, (int)((x >> 29) & 3u) - 1, w);
     }
     return;
   }
@@ -517,10 +523,14 @@ __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffe
   const uint32_t* __restrict__ wcb = B.wall_cb + P.cell_base;
   for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
     const uint32_t e = cb[c + 1];
-    for (uint32_t j = cb[c]; j < e; ++j) v((int)j, dx, dy, dz, false);
+    if (SPH_DBG_IN(B, cb[c], P.foff, P.foff + P.n + 1) &&
+        SPH_DBG_IN(B, e, cb[c], P.foff + P.n + 1))
+      for (uint32_t j = cb[c]; j < e; ++j) v((int)j, dx, dy, dz, false);
     if (P.nw > 0) {
       const uint32_t we = wcb[c + 1];
-      for (uint32_t w = wcb[c]; w < we; ++w) v((int)w, dx, dy, dz, true);
+      if (SPH_DBG_IN(B, wcb[c], P.woff, P.woff + P.nw + 1) &&
+          SPH_DBG_IN(B, we, wcb[c], P.woff + P.nw + 1))
+        for (uint32_t w = wcb[c]; w < we; ++w) v((int)w, dx, dy, dz, true);
     }
   });
 }
@@ -1205,6 +1215,7 @@ __device__ __forceinline__ void wall_slot(const Params& P, const DevBuffers& B,
                                           size_t vstride, int k, uint32_t j, uint32_t key) {
   using WR = WallRec<D, T>;
   typename WR::WV* out = (typename WR::WV*)B.wallP;
+  if (!SPH_DBG_IN(B, j, 0, vstride)) return;
   double x = ux[j], y = uy[j], z = D == 3 ? uz[j] : 0.0;
   wx[k] = x;
   wy[k] = y;

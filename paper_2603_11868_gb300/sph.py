@@ -603,6 +603,9 @@ class Batch:
     def autotune(self, steps_per_trial=10):
         return sph_batch_autotune(self.b, steps_per_trial)
 
+    def synchronize(self, timeout_s=0.0):
+        sph_batch_synchronize(self.b, timeout_s)
+
     def close(self):
         if getattr(self, "b", None):
             sph_batch_destroy(self.b)

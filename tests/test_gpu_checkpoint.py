@@ -100,3 +100,31 @@ def test_checkpoint_of_another_setup_is_refused(sph):
     c.restore(buf)  # the right setup takes it
     c.step(1)
     c.close()
+
+
+def test_corrupt_checkpoint_is_refused_on_the_host(sph):
+    """Keys outside the grid or out of storage order, and ids that are no
+    permutation, are caught before anything is uploaded."""
+    case = cases.dam_break_2d()
+    a = sph.Solver(case, precision="fp64")
+    a.step(5)
+    buf = a.checkpoint()
+    a.close()
+    n = case.n
+    ids_at = buf.size - 8 * n
+    keys = buf[ids_at + 4 * n:].view(np.uint32)
+    ids = buf[ids_at:ids_at + 4 * n].view(np.uint32)
+    s = sph.Solver(case, precision="fp64")
+    for mutate in (lambda k, i: k.__setitem__(-1, 0xFFFFFFF0),
+                   lambda k, i: k.__setitem__(0, k[-1] + 1),
+                   lambda k, i: i.__setitem__(1, i[0])):
+        bad = buf.copy()
+        k = bad[ids_at + 4 * n:].view(np.uint32)
+        i = bad[ids_at:ids_at + 4 * n].view(np.uint32)
+        mutate(k, i)
+        with pytest.raises(sph.SphError):
+            s.restore(bad)
+    assert keys.size == n and ids.size == n
+    s.restore(buf)
+    s.step(2)
+    s.close()

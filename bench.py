@@ -153,7 +153,9 @@ def apply_tuning(obj, args):
         obj.set_option(sph.SPH_OPT_RADIX_BITS, radix)
         obj.set_option(sph.SPH_OPT_NEIGHBOUR_LIST, lists)
         return {"block": blk, "radix_bits": radix, "neighbour_list": lists, "trials": 0}
-    return None if args.no_autotune else obj.autotune(args.substeps)
+    if args.no_autotune:
+        return None
+    return sph.tune(obj, args.substeps, cache=args.tune_cache)
 
 
 def replica_value(el: float, units: float, dist, device) -> tuple[float, float]:
@@ -569,6 +571,9 @@ def main():
                     help="keep the default launch configuration")
     ap.add_argument("--tanks", type=int, default=256,
                     help="tank count of the batched workload (the bench line is 256)")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of autotuner choices keyed by GPU and problem (reused "
+                         "when present, written after tuning)")
     ap.add_argument("--tuning", default=None,
                     help="block,radix_bits,lists: fixed launch configuration, no autotuner")
     args = ap.parse_args()

@@ -485,6 +485,7 @@ int sph_create_batch(int n_tanks, const sph_tank* tanks, int precision,
 
 int sph_batch_set_particles(sph_batch* b, int kind, const size_t* counts, const double* pos,
                             const double* vel, const double* rho) {
+  TraceRange trace_("sph_batch_set_particles");
   if (!b) return SPH_E_INVALID;
   if (!counts) return set_err(b, SPH_E_INVALID, "counts is NULL");
   size_t total = 0;
@@ -655,6 +656,7 @@ int sph_batch_set_particles(sph_batch* b, int kind, const size_t* counts, const 
 }
 
 int sph_batch_step(sph_batch* b, int n) {
+  TraceRange trace_("sph_batch_step");
   if (!b) return SPH_E_INVALID;
   if (n < 0) return set_err(b, SPH_E_INVALID, "negative step count");
   if (!b->fluid_set) return set_err(b, SPH_E_STATE, "no fluid particles set");
@@ -703,6 +705,7 @@ int sph_batch_synchronize(sph_batch* b, double timeout_s) {
 }
 
 int sph_batch_get_fields(sph_batch* b, unsigned mask, double* out) {
+  TraceRange trace_("sph_batch_get_fields");
   if (!b || (!out && mask)) return SPH_E_INVALID;
   if (mask & ~0xffu) return set_err(b, SPH_E_INVALID, "unknown field bit");
   if (!b->fluid_set) return set_err(b, SPH_E_STATE, "no fluid particles set");
@@ -945,6 +948,7 @@ int sph_batch_set_option(sph_batch* b, int option, long value) {
 }
 
 int sph_batch_autotune(sph_batch* b, int steps_per_trial, sph_tuning* best) {
+  TraceRange trace_("sph_batch_autotune");
   if (!b || !best || steps_per_trial < 1) return SPH_E_INVALID;
   if (!b->fluid_set) return set_err(b, SPH_E_STATE, "no fluid particles set");
   int rc = enter(b);

@@ -448,6 +448,7 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
 
 int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const double* vel,
                       const double* rho) {
+  TraceRange trace_("sph_set_particles");
   if (!c) return SPH_E_INVALID;
   if (n > 0 && !pos) return set_err(c, SPH_E_INVALID, "pos is NULL");
   if (n >= (1ull << 25)) return set_err(c, SPH_E_INVALID, "at most 2^25 - 1 particles per kind");
@@ -654,6 +655,7 @@ size_t sph_checkpoint_bytes(const sph_ctx* c) {
 }
 
 int sph_checkpoint_save(sph_ctx* c, void* buf, size_t bytes) {
+  TraceRange trace_("sph_checkpoint_save");
   if (!c) return SPH_E_INVALID;
   if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
   if (!buf || bytes < sph_checkpoint_bytes(c))
@@ -691,6 +693,7 @@ int sph_checkpoint_save(sph_ctx* c, void* buf, size_t bytes) {
 }
 
 int sph_checkpoint_load(sph_ctx* c, const void* buf, size_t bytes) {
+  TraceRange trace_("sph_checkpoint_load");
   if (!c) return SPH_E_INVALID;
   if (!buf || bytes < sizeof(CkptHeader) + sizeof(DevScalars))
     return set_err(c, SPH_E_INVALID, "checkpoint buffer missing or too small");
@@ -786,6 +789,7 @@ int sph_checkpoint_load(sph_ctx* c, const void* buf, size_t bytes) {
 }
 
 int sph_set_wall_translation(sph_ctx* c, const uint8_t* moves) {
+  TraceRange trace_("sph_set_wall_translation");
   if (!c) return SPH_E_INVALID;
   int rc = enter(c);
   if (rc) return rc;
@@ -846,6 +850,7 @@ int sph_set_wall_translation(sph_ctx* c, const uint8_t* moves) {
 }
 
 int sph_step(sph_ctx* c, int n) {
+  TraceRange trace_("sph_step");
   if (!c) return SPH_E_INVALID;
   if (n < 0) return set_err(c, SPH_E_INVALID, "negative step count");
   if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
@@ -891,6 +896,7 @@ int sph_synchronize(sph_ctx* c, double timeout_s) {
 }
 
 int sph_get_fields(sph_ctx* c, unsigned mask, double* out) {
+  TraceRange trace_("sph_get_fields");
   if (!c || (!out && mask)) return SPH_E_INVALID;
   if (mask & ~0xffu) return set_err(c, SPH_E_INVALID, "unknown field bit");
   if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
@@ -1038,6 +1044,7 @@ int sph_debug_list_lengths(sph_ctx* c, uint32_t* lengths) {
 }
 
 int sph_profile_stages(sph_ctx* c, int n, double* ms, long* rebuilds) {
+  TraceRange trace_("sph_profile_stages");
   if (!c || !ms || n < 0) return SPH_E_INVALID;
   if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
   int rc = enter(c);
@@ -1159,6 +1166,7 @@ int sph_set_option(sph_ctx* c, int option, long value) {
 }
 
 int sph_autotune(sph_ctx* c, int steps_per_trial, sph_tuning* best) {
+  TraceRange trace_("sph_autotune");
   if (!c || !best || steps_per_trial < 1) return SPH_E_INVALID;
   if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
   int rc = enter(c);

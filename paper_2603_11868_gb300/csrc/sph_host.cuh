@@ -8,9 +8,20 @@
 #include <cmath>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sph.h"
 
 namespace sphgb {
+
+// Host trace range over one public call (NVTX: shows up in nsys / ncu
+// timelines under the call's name; free when no tool is attached).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 struct Block {
   void* p;

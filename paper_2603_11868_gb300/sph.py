@@ -351,6 +351,60 @@ def sph_autotune(ctx, steps_per_trial=10):
     return t.as_dict()
 
 
+class TuningCache:
+    """Autotuner choices kept in a JSON file, keyed by the GPU's name and the
+    problem's configuration (dimension, precision, particle and wall counts,
+    cell grid, smoothing length), so that a later run of the same problem on
+    the same kind of GPU takes the choice without the trials."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    @staticmethod
+    def key(obj) -> str:
+        import torch
+        gpu = torch.cuda.get_device_name() if torch.cuda.is_available() else "none"
+        cfg = obj.tuning_signature()
+        return gpu + "|" + ",".join(f"{k}={cfg[k]}" for k in sorted(cfg))
+
+    def _read(self) -> dict:
+        import json
+        try:
+            with open(self.path) as fh:
+                return json.load(fh)
+        except (OSError, ValueError):
+            return {}
+
+    def get(self, obj):
+        return self._read().get(self.key(obj))
+
+    def put(self, obj, tuning: dict) -> None:
+        import json
+        data = self._read()
+        data[self.key(obj)] = {k: int(tuning[k]) for k in ("block", "radix_bits",
+                                                           "neighbour_list")}
+        tmp = self.path + f".{os.getpid()}.tmp"
+        with open(tmp, "w") as fh:
+            json.dump(data, fh, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
+
+
+def tune(obj, steps_per_trial=10, cache: str | None = None) -> dict:
+    """Autotune a Solver or Batch, or take a cached choice (TuningCache)."""
+    if cache:
+        tc = TuningCache(cache)
+        hit = tc.get(obj)
+        if hit:
+            obj.set_option(SPH_OPT_BLOCK, hit["block"])
+            obj.set_option(SPH_OPT_RADIX_BITS, hit["radix_bits"])
+            obj.set_option(SPH_OPT_NEIGHBOUR_LIST, hit["neighbour_list"])
+            return dict(hit, trials=0, cached=True)
+    t = obj.autotune(steps_per_trial)
+    if cache:
+        TuningCache(cache).put(obj, t)
+    return t
+
+
 class NeighbourSearch:
     """sph_nsearch_*: keys, radix sort, reorder, offsets and one density pass
     over device positions (torch tensors, float32 or float64)."""
@@ -606,6 +660,10 @@ class Batch:
     def synchronize(self, timeout_s=0.0):
         sph_batch_synchronize(self.b, timeout_s)
 
+    def tuning_signature(self) -> dict:
+        return {"kind": "batch", "dim": self.dim, "precision": int(self.precision),
+                "tanks": self.tanks, "n": self.n, "nw": self.nw}
+
     def close(self):
         if getattr(self, "b", None):
             sph_batch_destroy(self.b)
@@ -721,6 +779,11 @@ class Solver:
 
     def neighbour_stats(self):
         return sph_debug_neighbour_stats(self.ctx, self.n)
+
+    def tuning_signature(self) -> dict:
+        c = self.case
+        return {"kind": "tank", "dim": c.dim, "precision": int(self.precision), "n": self.n,
+                "nw": self.nw, "cells": self.ncell, "h_over_dp": round(c.h / c.dp, 6)}
 
     def checkpoint(self) -> np.ndarray:
         """The run's state as a byte array (sph_checkpoint_save)."""

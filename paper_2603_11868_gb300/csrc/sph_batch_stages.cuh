@@ -103,9 +103,11 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) kb_density_summation(Batch
 template <int D, class T>
 __global__ void __launch_bounds__(256, kMinBlocks<T>) kb_transport(BatchArgs A, DevBuffers B,
                                                                    const WorkList* wl) {
+  __shared__ ShiftTable tab;
+  if constexpr (Local<T>::kLocal) fill_shift_table(tab);
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
     if (P.variant & kVariantTransport)
-      transport_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x);
+      transport_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x, &tab);
   });
 }
 
@@ -120,8 +122,10 @@ __global__ void kb_transport_apply(BatchArgs A, DevBuffers B, const WorkList* wl
 template <int D, class T>
 __global__ void __launch_bounds__(256, kMinBlocks<T>) kb_viscous(BatchArgs A, DevBuffers B,
                                                                  const WorkList* wl) {
+  __shared__ ShiftTable tab;
+  if constexpr (Local<T>::kLocal) fill_shift_table(tab);
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
-    viscous_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x);
+    viscous_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x, &tab);
   });
 }
 
@@ -135,17 +139,21 @@ __global__ void kb_half1(BatchArgs A, DevBuffers B, const WorkList* wl) {
 template <int D, class T>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) kb_pressure(BatchArgs A, DevBuffers B,
                                                                   const WorkList* wl) {
+  __shared__ ShiftTable tab;
+  if constexpr (Local<T>::kLocal) fill_shift_table(tab);
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
     pressure_range<D, T>(P, tank_buffers(A, B, t), tank_kc<T>(A, t), A.tsc + t, i, end,
-                         blockDim.x);
+                         blockDim.x, &tab);
   });
 }
 
 template <int D, class T>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) kb_density_relax(BatchArgs A, DevBuffers B,
                                                                        const WorkList* wl) {
+  __shared__ ShiftTable tab;
+  if constexpr (Local<T>::kLocal) fill_shift_table(tab);
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
-    density_relax_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x);
+    density_relax_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x, &tab);
   });
 }
 

@@ -493,11 +493,28 @@ struct ListWriter {
   }
 };
 
+// The cell offsets of a list entry as floats: bits 25..30 of an entry hold
+// (dx + 1) | (dy + 1) << 2 | (dz + 1) << 4, so the float loops read
+// (dx, dy, dz) from this 64-entry table in shared memory (one load) instead
+// of decoding and converting three fields.  Every block fills it once.
+struct ShiftTable {
+  float4 d[64];
+};
+__device__ __forceinline__ void fill_shift_table(ShiftTable& t) {
+  for (int c = threadIdx.x; c < 64; c += blockDim.x)
+    t.d[c] = make_float4((float)((c & 3) - 1), (float)(((c >> 2) & 3) - 1),
+                         (float)(((c >> 4) & 3) - 1), 0.0f);
+  __syncthreads();
+}
+
 // Visit the candidates of target i either through its list or through the
-// 3^D cells; v(j, dx, dy, dz, wall) does the test and the arithmetic.
-template <int D, class V>
+// 3^D cells; v(j, dx, dy, dz, wall) does the test and the arithmetic.  With
+// kTab the list path passes the offsets as floats from `tab` (the same
+// values; direct search passes ints).
+template <int D, bool kTab = false, class V>
 __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffers& B, Cell ci,
-                                                 int i, bool use_list, V&& v) {
+                                                 int i, bool use_list, V&& v,
+                                                 const ShiftTable* tab = nullptr) {
   if (!SPH_DBG_IN(B, ci.x, 0, P.nx) || !SPH_DBG_IN(B, ci.y, 0, P.ny) ||
       !SPH_DBG_IN(B, ci.z, 0, D == 3 ? P.nz : 1))
     return;
@@ -515,7 +532,13 @@ __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffe
       const int j = (int)(x & kIdxMask);
       const bool w = (x >> 31) != 0u;
       if (!SPH_DBG_IN(B, j, w ? P.woff : P.foff, w ? P.woff + P.nw : P.foff + P.n)) continue;
-      v(j, (int)((x >> 25) & 3u) - 1, (int)((x >> 27) & 3u) - 1, (int)((x >> 29) & 3u) - 1, w);
+      if constexpr (kTab) {
+        const float4 d = tab->d[(x >> 25) & 63u];
+        v(j, d.x, d.y, d.z, w);
+      } else {
+        v(j, (int)((x >> 25) & 3u) - 1, (int)((x >> 27) & 3u) - 1, (int)((x >> 29) & 3u) - 1,
+          w);
+      }
     }
     return;
   }
@@ -535,11 +558,17 @@ __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffe
   });
 }
 
-// x - d * cs in the record frame (x itself for absolute positions)
+// x - d * cs in the record frame (x itself for absolute positions); d is the
+// cell offset, an int or the same value as a float (ShiftTable)
 template <class T>
 __device__ __forceinline__ T shifted(T x, int d, T cs) {
   if constexpr (!Local<T>::kLocal) return x;
   return fmaf(-(float)d, cs, x);
+}
+template <class T>
+__device__ __forceinline__ T shifted(T x, float d, T cs) {
+  if constexpr (!Local<T>::kLocal) return x;
+  return fmaf(-d, cs, x);
 }
 
 // whether this launch may use the lists: disp is the displacement bound of the
@@ -558,19 +587,22 @@ struct PairGeo {
   const typename WR::WV* __restrict__ wall;
   T xi, yi, zi;
   T cs;
-  __device__ __forceinline__ void rel_rec(const typename R::PV& pj, int dx, int dy, int dz,
-                                          T& rx, T& ry, T& rz) const {
+  template <class S>
+  __device__ __forceinline__ void rel_rec(const typename R::PV& pj, S dx, S dy, S dz, T& rx,
+                                          T& ry, T& rz) const {
     rx = dsub(shifted<T>(xi, dx, cs), R::px(pj));
     ry = dsub(shifted<T>(yi, dy, cs), R::py(pj));
     rz = dsub(shifted<T>(zi, dz, cs), R::pz(pj));
   }
-  __device__ __forceinline__ void rel_wall(const typename WR::WV& pw, int dx, int dy, int dz,
-                                           T& rx, T& ry, T& rz) const {
+  template <class S>
+  __device__ __forceinline__ void rel_wall(const typename WR::WV& pw, S dx, S dy, S dz, T& rx,
+                                           T& ry, T& rz) const {
     rx = dsub(shifted<T>(xi, dx, cs), pw.x);
     ry = dsub(shifted<T>(yi, dy, cs), pw.y);
     rz = dsub(shifted<T>(zi, dz, cs), WR::z(pw));
   }
-  __device__ __forceinline__ void rel(int j, int dx, int dy, int dz, bool w, T& rx, T& ry,
+  template <class S>
+  __device__ __forceinline__ void rel(int j, S dx, S dy, S dz, bool w, T& rx, T& ry,
                                       T& rz) const {
     const T bx = shifted<T>(xi, dx, cs);
     const T by = shifted<T>(yi, dy, cs);
@@ -792,7 +824,8 @@ __global__ void __launch_bounds__(256, 4) k_density_summation_fx(Params P, DevBu
 template <int D, class T>
 __device__ __forceinline__ void transport_range(const Params& P, const DevBuffers& B,
                                                 const KC<T>& k, DevScalars* sc, int i, int end,
-                                                int stride) {
+                                                int stride,
+                                     const ShiftTable* tab) {
   using R = Rec<D, T>;
   const bool use_list = list_ok(P, sc, 0.0);
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
@@ -810,7 +843,8 @@ __device__ __forceinline__ void transport_range(const Params& P, const DevBuffer
       const typename R::PV pi = recP[i];
       PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
                       R::pz(pi), k.cs};
-      visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
+      visit_neighbours<D, Local<T>::kLocal>(
+          P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w) {
         T rx, ry, rz;
         G.rel(j, dx, dy, dz, w, rx, ry, rz);
         const T r2 = r2_of(rx, ry, rz);
@@ -826,7 +860,7 @@ __device__ __forceinline__ void transport_range(const Params& P, const DevBuffer
         gx += f * rx;
         gy += f * ry;
         gz += f * rz;
-      });
+      }, tab);
     }
     d0[i] = coef * gx;
     d1[i] = coef * gy;
@@ -839,8 +873,10 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_transport(Params P, DevB
                                                                   int gated) {
   DevScalars* sc = B.sc;
   if (!(P.variant & kVariantTransport) || (gated && !sc->new_adv)) return;
+  __shared__ ShiftTable tab;
+  if constexpr (Local<T>::kLocal) fill_shift_table(tab);
   transport_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
-                        gridDim.x * blockDim.x);
+                        gridDim.x * blockDim.x, &tab);
 }
 
 // Apply the shifts: positions (FP64 state) and the position records of
@@ -897,7 +933,8 @@ __global__ void k_transport_apply(Params P, DevBuffers B, int gated) {
 // lists are always usable here (unless one overflowed).
 template <int D, class T>
 __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers& B, const KC<T>& k,
-                                              DevScalars* sc, int i, int end, int stride) {
+                                              DevScalars* sc, int i, int end, int stride,
+                                     const ShiftTable* tab) {
   using R = Rec<D, T>;
   const bool use_list = list_ok(P, sc, 0.0);
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
@@ -916,7 +953,8 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
                     R::pz(pi), k.cs};
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     T ax = 0, ay = 0, az = 0;
-    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
+    visit_neighbours<D, Local<T>::kLocal>(
+        P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w) {
       T rx, ry, rz;
       G.rel(j, dx, dy, dz, w, rx, ry, rz);
       const T r2 = r2_of(rx, ry, rz);
@@ -943,7 +981,7 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
         ay += coef * (vyi - R::vy(pj, sj));
         az += coef * (vzi - R::vz(pj, sj));
       }
-    });
+    }, tab);
     const T f = div_t(k.two_mu, R::rho(pi, si));
     ap0[i] = k.g[0] + f * ax;
     ap1[i] = k.g[1] + f * ay;
@@ -956,8 +994,10 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_viscous(Params P, DevBuf
                                                                 int gated) {
   DevScalars* sc = B.sc;
   if (gated && !sc->new_adv) return;
+  __shared__ ShiftTable tab;
+  if constexpr (Local<T>::kLocal) fill_shift_table(tab);
   viscous_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
-                      gridDim.x * blockDim.x);
+                      gridDim.x * blockDim.x, &tab);
 }
 
 // First half of the acoustic step; writes records of buffer 0.
@@ -1000,7 +1040,8 @@ __global__ void k_half1(Params P, DevBuffers B) {
 // Reads records of buffer 0, writes records of buffer 1.
 template <int D, class T>
 __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers& B, const KC<T>& k,
-                                               DevScalars* sc, int i, int end, int stride) {
+                                               DevScalars* sc, int i, int end, int stride,
+                                     const ShiftTable* tab) {
   using R = Rec<D, T>;
   const int par = sc->par;
   const double dt = sc->dt_ac;
@@ -1030,7 +1071,8 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     const T p_i = R::pres(pi, si), rho_i = R::rho(pi, si);
     T ax = 0, ay = 0, az = 0;
-    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
+    visit_neighbours<D, Local<T>::kLocal>(
+        P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w) {
       T rx, ry, rz;
       typename R::PV pj;
       typename R::SV sj;
@@ -1069,7 +1111,7 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
       ax += f * ex;
       ay += f * ey;
       az += f * ez;
-    });
+    }, tab);
     const T s = div_t(T(-2), rho_i);
     ax *= s;
     ay *= s;
@@ -1115,15 +1157,18 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
 
 template <int D, class T>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) k_pressure(Params P, DevBuffers B, KC<T> k) {
+  __shared__ ShiftTable tab;
+  if constexpr (Local<T>::kLocal) fill_shift_table(tab);
   pressure_range<D, T>(P, B, k, B.sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
-                       gridDim.x * blockDim.x);
+                       gridDim.x * blockDim.x, &tab);
 }
 
 // Riemann density relaxation: reads records of buffer 1; drho and rho (state).
 template <int D, class T>
 __device__ __forceinline__ void density_relax_range(const Params& P, const DevBuffers& B,
                                                     const KC<T>& k, DevScalars* sc, int i,
-                                                    int end, int stride) {
+                                                    int end, int stride,
+                                     const ShiftTable* tab) {
   using R = Rec<D, T>;
   const int par = sc->par;
   const double hdt = 0.5 * sc->dt_ac;
@@ -1146,7 +1191,8 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     const T p_i = R::pres(pi, si), rho_i = R::rho(pi, si);
     T sum = 0;
-    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
+    visit_neighbours<D, Local<T>::kLocal>(
+        P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w) {
       T rx, ry, rz;
       typename R::PV pj;
       typename R::SV sj;
@@ -1180,7 +1226,7 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
             k.half * (UL + UR) + k.riemann * div_t(p_i - R::pres(pj, sj), T(2) * rbar * k.c0);
         sum += div_t(k.m, rho_j) * wendland_dr(k, r) * (UL - Us);
       }
-    });
+    }, tab);
     const T dr = T(-2) * rho_i * sum;
     S.drho[i] = dr;
     double rho = S.rho[i] + hdt * (double)dr;
@@ -1195,9 +1241,11 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
 template <int D, class T>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) k_density_relax(Params P, DevBuffers B, KC<T> k) {
   DevScalars* sc = B.sc;
+  __shared__ ShiftTable tab;
+  if constexpr (Local<T>::kLocal) fill_shift_table(tab);
   if (blockIdx.x == 0 && threadIdx.x == 0) sc->vmax2_cur = sc->vmax2_next;
   density_relax_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
-                            gridDim.x * blockDim.x);
+                            gridDim.x * blockDim.x, &tab);
 }
 
 // Wall setup: gather sorted wall positions (double SoA for the parity kernel,

@@ -136,24 +136,25 @@ __global__ void kb_half1(BatchArgs A, DevBuffers B, const WorkList* wl) {
   });
 }
 
-template <int D, class T>
+template <int D, class T, bool kWallVel>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) kb_pressure(BatchArgs A, DevBuffers B,
                                                                   const WorkList* wl) {
   __shared__ ShiftTable tab;
   if constexpr (Local<T>::kLocal) fill_shift_table(tab);
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
-    pressure_range<D, T>(P, tank_buffers(A, B, t), tank_kc<T>(A, t), A.tsc + t, i, end,
+    pressure_range<D, T, kWallVel>(P, tank_buffers(A, B, t), tank_kc<T>(A, t), A.tsc + t, i, end,
                          blockDim.x, &tab);
   });
 }
 
-template <int D, class T>
+template <int D, class T, bool kWallVel>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) kb_density_relax(BatchArgs A, DevBuffers B,
                                                                        const WorkList* wl) {
   __shared__ ShiftTable tab;
   if constexpr (Local<T>::kLocal) fill_shift_table(tab);
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
-    density_relax_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x, &tab);
+    density_relax_range<D, T, kWallVel>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x,
+                                       &tab);
   });
 }
 
@@ -210,9 +211,16 @@ void enqueue_batch_step_t(const BatchStageArgs& a, cudaStream_t s, cudaEvent_t* 
   mark(ev, kStageHalf1, s);
   kb_half1<D, T><<<grid, blk, 0, s>>>(A, B, A.wl_all);
   mark(ev, kStagePressure, s);
-  kb_pressure<D, T><<<grid, blk, 0, s>>>(A, B, A.wl_all);
+  const bool wall_vel = wall_vel_code<D>(a.variants);
+  if (wall_vel)
+    kb_pressure<D, T, true><<<grid, blk, 0, s>>>(A, B, A.wl_all);
+  else
+    kb_pressure<D, T, false><<<grid, blk, 0, s>>>(A, B, A.wl_all);
   mark(ev, kStageDensityRelax, s);
-  kb_density_relax<D, T><<<grid, blk, 0, s>>>(A, B, A.wl_all);
+  if (wall_vel)
+    kb_density_relax<D, T, true><<<grid, blk, 0, s>>>(A, B, A.wl_all);
+  else
+    kb_density_relax<D, T, false><<<grid, blk, 0, s>>>(A, B, A.wl_all);
   mark(ev, kStages, s);
 }
 

@@ -64,6 +64,10 @@ def lib():
             L.osph_set_drho.restype = i; L.osph_set_drho.argtypes = [vp, vp]
             L.osph_set_wall_translation.restype = i
             L.osph_set_wall_translation.argtypes = [vp, vp]
+            L.osph_set_wall_motion.restype = i
+            L.osph_set_wall_motion.argtypes = [vp, vp, d, vp]
+            L.osph_set_time.restype = None
+            L.osph_set_time.argtypes = [vp, d]
             L.osph_set_variant.restype = None; L.osph_set_variant.argtypes = [vp, i, i]
             L.osph_set_transport_correction.restype = None
             L.osph_set_transport_correction.argtypes = [vp, i]
@@ -152,7 +156,8 @@ class Oracle:
             if case.wall is not None and len(case.wall):
                 o.set_wall(case.wall, case.wall_vel)
                 if getattr(case, "wall_moves", None) is not None:
-                    o.set_wall_translation(case.wall_moves)
+                    o.set_wall_motion(case.wall_moves, getattr(case, "wall_omega", 0.0),
+                                      getattr(case, "wall_amplitude", None))
             o.set_fluid(case.fluid, case.vel, case.rho)
         return o
 
@@ -184,6 +189,19 @@ class Oracle:
         if moves is not None:
             moves = np.ascontiguousarray(moves, dtype=np.uint8)
         lib().osph_set_wall_translation(self._s, _ptr(moves))
+
+    def set_wall_motion(self, moves, omega=0.0, amplitude=None):
+        """Translating walls (moves[u] != 0) that also oscillate with
+        amplitude[u] at angular frequency omega (None: uniform motion)."""
+        if moves is not None:
+            moves = np.ascontiguousarray(moves, dtype=np.uint8)
+        if amplitude is not None:
+            amplitude = np.ascontiguousarray(amplitude, dtype=np.float64)
+        lib().osph_set_wall_motion(self._s, _ptr(moves), float(omega), _ptr(amplitude))
+
+    def set_time(self, t):
+        """Sets the simulation time (translating walls placed at it)."""
+        lib().osph_set_time(self._s, float(t))
 
     def set_drho(self, drho):
         drho = np.ascontiguousarray(drho, dtype=np.float64)

@@ -53,17 +53,22 @@ struct osim {
   long* cb; /* cell_begin, ncell + 1 entries */
 
   /* wall, sorted by cell: once, or at every rebuild when some walls
-   * translate; vw = prescribed wall velocity (zero at rest).  A wall slides
-   * along itself (fixed position) unless it translates: then it moves with
-   * its velocity, x_w(t) = x_w(0) + v_w t.  xw0, vwu, wmoves keep the given
-   * positions, velocities and translation flags in user order. */
+   * translate; vw, aw = wall velocity and acceleration at the current time
+   * (zero at rest).  A wall slides along itself (fixed position, velocity
+   * vwu) unless it translates: then it follows
+   *   x_w(t) = x_w(0) + v t + A sin(omega t),
+   *   v_w(t) = v + A omega cos(omega t),  a_w(t) = -A omega^2 sin(omega t),
+   * v its given velocity, A its amplitude (zero: uniform motion).  xw0, vwu,
+   * awu, wmoves keep the given positions, velocities, amplitudes and
+   * translation flags in user order. */
   long nw;
-  double (*xw)[3], (*vw)[3];
+  double (*xw)[3], (*vw)[3], (*aw)[3];
   uint32_t *idw, *keyw;
   long* cbw;
-  double (*xw0)[3], (*vwu)[3];
+  double (*xw0)[3], (*vwu)[3], (*awu)[3];
   unsigned char* wmoves;
   int wtranslate; /* some wall translates */
+  double womega;  /* angular frequency of the wall oscillation */
 
   double t, tau, dt_ad, dt_ac;
   long n_ac, n_adv;
@@ -183,8 +188,8 @@ static void free_fluid(osim* s) {
 void osph_destroy(osim* s) {
   if (!s) return;
   free_fluid(s);
-  free(s->xw); free(s->vw); free(s->idw); free(s->keyw);
-  free(s->xw0); free(s->vwu); free(s->wmoves);
+  free(s->xw); free(s->vw); free(s->aw); free(s->idw); free(s->keyw);
+  free(s->xw0); free(s->vwu); free(s->awu); free(s->wmoves);
   free(s->cb); free(s->cbw);
   free(s);
 }
@@ -260,13 +265,29 @@ static void permute_u(uint32_t* a, const uint32_t* perm, long n) {
   free(t);
 }
 
-/* Wall positions at time t: x_w(0) + v_w t for translating walls, the given
- * position for the others (sorted slots, from the user-order copies). */
+/* Position, velocity and acceleration of wall u (user order) at time t. */
+static void wall_kinematics(const osim* s, uint32_t u, double t, double x[3], double v[3],
+                            double a[3]) {
+  const double sn = sin(s->womega * t), cs = cos(s->womega * t);
+  for (int c = 0; c < 3; ++c) {
+    if (s->wmoves[u]) {
+      x[c] = s->xw0[u][c] + t * s->vwu[u][c] + s->awu[u][c] * sn;
+      v[c] = s->vwu[u][c] + s->awu[u][c] * s->womega * cs;
+      a[c] = -s->awu[u][c] * s->womega * s->womega * sn;
+    } else {
+      x[c] = s->xw0[u][c];
+      v[c] = s->vwu[u][c];
+      a[c] = 0.0;
+    }
+  }
+}
+
+/* Translating walls to time t (sorted slots, from the user-order copies). */
 static void place_walls(osim* s, double t) {
   for (long k = 0; k < s->nw; ++k) {
     uint32_t u = s->idw[k];
     if (!s->wmoves[u]) continue;
-    for (int c = 0; c < 3; ++c) s->xw[k][c] = s->xw0[u][c] + t * s->vwu[u][c];
+    wall_kinematics(s, u, t, s->xw[k], s->vw[k], s->aw[k]);
   }
 }
 
@@ -277,9 +298,8 @@ static void bin_walls(osim* s, double t) {
   kv_t* a = (kv_t*)xcalloc((size_t)(n > 0 ? n : 1), sizeof(kv_t));
   int oob = 0;
   for (long u = 0; u < n; ++u) {
-    double xu[3];
-    for (int c = 0; c < 3; ++c)
-      xu[c] = s->wmoves[u] ? s->xw0[u][c] + t * s->vwu[u][c] : s->xw0[u][c];
+    double xu[3], vu[3], au[3];
+    wall_kinematics(s, (uint32_t)u, t, xu, vu, au);
     a[u].key = cell_key(s, xu, &oob);
     a[u].idx = (uint32_t)u;
   }
@@ -289,10 +309,7 @@ static void bin_walls(osim* s, double t) {
     uint32_t u = a[k].idx;
     s->idw[k] = u;
     s->keyw[k] = a[k].key;
-    for (int c = 0; c < 3; ++c) {
-      s->xw[k][c] = s->wmoves[u] ? s->xw0[u][c] + t * s->vwu[u][c] : s->xw0[u][c];
-      s->vw[k][c] = s->vwu[u][c];
-    }
+    wall_kinematics(s, u, t, s->xw[k], s->vw[k], s->aw[k]);
   }
   free(a);
   cell_offsets(s, s->keyw, n, s->cbw);
@@ -330,14 +347,27 @@ void osph_rebuild(osim* s) {
   if (s->wtranslate) bin_walls(s, s->t);
 }
 
-int osph_set_wall_translation(osim* s, const unsigned char* moves) {
+int osph_set_wall_motion(osim* s, const unsigned char* moves, double omega,
+                         const double* amplitude) {
+  const int d = s->dim;
   s->wtranslate = 0;
+  s->womega = omega;
   for (long u = 0; u < s->nw; ++u) {
     s->wmoves[u] = moves ? (moves[u] ? 1 : 0) : 0;
     if (s->wmoves[u]) s->wtranslate = 1;
+    for (int c = 0; c < 3; ++c) s->awu[u][c] = (amplitude && c < d) ? amplitude[u * d + c] : 0.0;
   }
   bin_walls(s, s->t);
   return 0;
+}
+
+void osph_set_time(osim* s, double t) {
+  s->t = t;
+  if (s->wtranslate) bin_walls(s, t);
+}
+
+int osph_set_wall_translation(osim* s, const unsigned char* moves) {
+  return osph_set_wall_motion(s, moves, 0.0, NULL);
 }
 
 int osph_set_particles(osim* s, int kind, long n, const double* pos,
@@ -377,17 +407,20 @@ int osph_set_particles(osim* s, int kind, long n, const double* pos,
     return 0;
   }
   if (kind == 1) {
-    free(s->xw); free(s->vw); free(s->idw); free(s->keyw);
-    free(s->xw0); free(s->vwu); free(s->wmoves);
+    free(s->xw); free(s->vw); free(s->aw); free(s->idw); free(s->keyw);
+    free(s->xw0); free(s->vwu); free(s->awu); free(s->wmoves);
     s->nw = n;
     s->xw = (double(*)[3])xcalloc((size_t)n, sizeof(double[3]));
     s->vw = (double(*)[3])xcalloc((size_t)n, sizeof(double[3]));
+    s->aw = (double(*)[3])xcalloc((size_t)n, sizeof(double[3]));
     s->idw = (uint32_t*)xcalloc((size_t)n, sizeof(uint32_t));
     s->keyw = (uint32_t*)xcalloc((size_t)n, sizeof(uint32_t));
     s->xw0 = (double(*)[3])xcalloc((size_t)n, sizeof(double[3]));
     s->vwu = (double(*)[3])xcalloc((size_t)n, sizeof(double[3]));
+    s->awu = (double(*)[3])xcalloc((size_t)n, sizeof(double[3]));
     s->wmoves = (unsigned char*)xcalloc((size_t)n, 1);
     s->wtranslate = 0;
+    s->womega = 0.0;
     for (long i = 0; i < n; ++i)
       for (int c = 0; c < 3; ++c) {
         s->xw0[i][c] = c < d ? pos[i * d + c] : 0.0;
@@ -592,12 +625,13 @@ void osph_half1(osim* s, double dt) {
  * For the pair (i, j): e_ij = (x_i - x_j) / r_ij, U_L = -v_i.e_ij,
  * U_R = -v_j.e_ij, and
  *   a_i = -(2 / rho_i) sum_j P*_ij V_j W'(r_ij) e_ij,   V_j = m / rho_j.
- * Wall particle w (fixed position, prescribed velocity v_w: 0 at rest, or
- * the velocity of a wall sliding along itself, so a_w = 0) supplies a
- * mirrored right state (reading: pressure extrapolated along gravity,
- * density from the inverse equation of state and volume from that density,
- * as in Adami, Hu & Adams, J. Comput. Phys. 231 (2012)):
- *   p_w = p_i + rho_i (x_w - x_i).g,  rho_w = rho0 + p_w / c0^2,
+ * Wall particle w (velocity v_w and acceleration a_w at the current time:
+ * zero at rest, v_w for a sliding wall, both for a translating one) supplies
+ * a mirrored right state (reading: pressure extrapolated along the effective
+ * gravity of the wall's frame, density from the inverse equation of state
+ * and volume from that density, as in Adami, Hu & Adams, J. Comput. Phys.
+ * 231 (2012)):
+ *   p_w = p_i + rho_i (x_w - x_i).(g - a_w),  rho_w = rho0 + p_w / c0^2,
  *   v_R = 2 v_w - v_i,  V_w = m / rho_w.
  * Then v_i += dt (a_i + a_prior_i). */
 /* Pressure acceleration of storage slot i with the given density and
@@ -638,7 +672,7 @@ static void pressure_acc_of(const osim* s, long i, const double* rho, const doub
       double e[3];
       for (int k = 0; k < 3; ++k) e[k] = (s->x[i][k] - s->xw[w][k]) / r;
       double gdot = 0.0;
-      for (int k = 0; k < 3; ++k) gdot += (s->xw[w][k] - s->x[i][k]) * s->g[k];
+      for (int k = 0; k < 3; ++k) gdot += (s->xw[w][k] - s->x[i][k]) * (s->g[k] - s->aw[w][k]);
       double pw = p[i] + rho[i] * gdot;
       double rhow = s->rho0 + pw / (c0 * c0);
       double UL = -(s->v[i][0] * e[0] + s->v[i][1] * e[1] + s->v[i][2] * e[2]);
@@ -711,7 +745,8 @@ void osph_half2(osim* s, double dt) {
         double e[3];
         for (int k = 0; k < 3; ++k) e[k] = (s->x[i][k] - s->xw[w][k]) / r;
         double gdot = 0.0;
-        for (int k = 0; k < 3; ++k) gdot += (s->xw[w][k] - s->x[i][k]) * s->g[k];
+        for (int k = 0; k < 3; ++k)
+          gdot += (s->xw[w][k] - s->x[i][k]) * (s->g[k] - s->aw[w][k]);
         double pw = s->p[i] + s->rho[i] * gdot;
         double rhow = s->rho0 + pw / (c0 * c0);
         double UL = -(s->v[i][0] * e[0] + s->v[i][1] * e[1] + s->v[i][2] * e[2]);

@@ -65,6 +65,14 @@ int osph_set_particles(osim* s, int kind, long n, const double* pos,
  * the fluid's half-drifts: at t + dt/2 for the pressure relaxation, at
  * t + dt for the density relaxation.  NULL clears.  Returns 0. */
 int osph_set_wall_translation(osim* s, const unsigned char* moves);
+/* translating walls that also oscillate: wall u with moves[u] != 0 follows
+ * x_w(t) = x_w(0) + v t + A sin(omega t) with A = amplitude[u * dim ..]
+ * (NULL: none), so v_w = v + A omega cos(omega t), a_w = -A omega^2
+ * sin(omega t); a_w enters the wall pressure p_w = p_i + rho_i
+ * (x_w - x_i).(g - a_w).  osph_set_wall_translation is this call with no
+ * amplitude.  Returns 0. */
+int osph_set_wall_motion(osim* s, const unsigned char* moves, double omega,
+                         const double* amplitude);
 /* method variants: density_riemann = 1 (default) takes the Riemann U* in the
  * density relaxation, 0 the average of the two states; reinit_blended = 0
  * (default) reinitialises the density with the free-surface clamp
@@ -85,6 +93,8 @@ int osph_set_drho(osim* s, const double* drho);
 int osph_step(osim* s, long n);
 
 /* individual stages, for tests */
+/* sets the simulation time (translating walls are placed and binned at it) */
+void osph_set_time(osim* s, double t);
 void osph_rebuild(osim* s);
 void osph_density_summation(osim* s);
 void osph_viscous(osim* s);

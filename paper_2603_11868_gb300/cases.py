@@ -30,6 +30,10 @@ Workloads:
                     whose left wall block translates into it at V = c0 / 20
                     from t = 0: a compression wave runs ahead at about c0
                     with p = rho0 c0 V and u = V behind it (linear acoustics).
+  shaken_tank_2d    closed 2D tank, completely filled, whose walls all oscillate
+                    along x with x = A sin(omega t) (no gravity): the fluid
+                    follows the tank and the pressure tilts with the
+                    tank's acceleration.
   dam_break_obstacle_3d
                     3D dam break whose surge hits a box obstacle on the floor
                     (the kind of test the paper's second workload is): tank
@@ -65,6 +69,8 @@ class Case:
     meta: dict = field(default_factory=dict)
     wall_vel: np.ndarray | None = None  # (nw, dim) prescribed wall velocity, or None (rest)
     wall_moves: np.ndarray | None = None  # (nw,) 1: the wall translates with its velocity
+    wall_omega: float = 0.0              # angular frequency of translating walls' oscillation
+    wall_amplitude: np.ndarray | None = None  # (nw, dim) oscillation amplitude, or None
 
     @property
     def n(self) -> int:
@@ -318,3 +324,31 @@ def piston_channel_2d(dp: float = 0.05, length: float = 4.0, height: float = 0.5
                 meta=dict(tank=tank, V=V, L=length, H=height, layers=layers),
                 wall_vel=np.ascontiguousarray(wall_vel),
                 wall_moves=piston.astype(np.uint8))
+
+
+def shaken_tank_2d(dp: float = 0.025, length: float = 1.0, height: float = 0.5,
+                   A: float = 0.01, omega: float = 2.0 * math.pi, c0: float = 20.0,
+                   compression: float = 1.005, layers: int = 4, rho0: float = 1.0) -> Case:
+    """Closed 2D tank filled with fluid (lattice `compression` times finer
+    than dp, so the pressure stays positive); every wall particle translates
+    with x_w(t) = x_w(0) + A sin(omega t) e_x, and the fluid starts with the
+    tank's velocity A omega e_x.  No gravity, inviscid.  The domain leaves
+    room for the walls' swing."""
+    nx, ny = int(round(length / dp)), int(round(height / dp))
+    dpf = dp / compression
+    xs = 0.5 * (length - nx * dpf) + (np.arange(nx) + 0.5) * dpf
+    ys = 0.5 * (height - ny * dpf) + (np.arange(ny) + 0.5) * dpf
+    Y, X = np.meshgrid(ys, xs, indexing="ij")
+    fluid = np.ascontiguousarray(np.stack([X.ravel(), Y.ravel()], axis=1))
+    tank = (length, height)
+    wall = tank_walls(2, tank, dp, layers, open_top=False)
+    lo, hi = _domain(2, tank, dp, layers, 0.0)
+    lo = (lo[0] - 2 * abs(A) - dp, lo[1])
+    hi = (hi[0] + 2 * abs(A) + dp, hi[1])
+    vel = np.tile([A * omega, 0.0], (len(fluid), 1))
+    amp = np.ascontiguousarray(np.tile([A, 0.0], (len(wall), 1)))
+    return Case("shaken_tank_2d", 2, dp, 1.3 * dp, rho0, c0, 0.0, c0 / 10.0, (0.0, 0.0), lo,
+                hi, fluid, wall, vel=np.ascontiguousarray(vel),
+                meta=dict(tank=tank, L=length, H=height, A=A, omega=omega, layers=layers),
+                wall_vel=np.zeros_like(wall), wall_moves=np.ones(len(wall), np.uint8),
+                wall_omega=omega, wall_amplitude=amp)

@@ -24,18 +24,22 @@ MUTATIONS = {
                               "double f = Ps * (s->m / rho[i])"),
     "pressure_direction": ("for (int k = 0; k < 3; ++k) out[k] = -2.0 / rho[i] * a[k];",
                            "for (int k = 0; k < 3; ++k) out[k] = 2.0 / rho[i] * a[k];"),
-    "wall_gravity_sign": ("gdot += (s->xw[w][k] - s->x[i][k]) * s->g[k];",
-                          "gdot += (s->x[i][k] - s->xw[w][k]) * s->g[k];"),
+    "wall_gravity_sign": ("gdot += (s->xw[w][k] - s->x[i][k]) * (s->g[k] - s->aw[w][k]);",
+                          "gdot += (s->x[i][k] - s->xw[w][k]) * (s->g[k] - s->aw[w][k]);"),
     "wall_mirror_velocity": ("d += (2.0 * vw[k] - vi[k]) * e[k];",
                              "d += (2.0 * vw[k] + vi[k]) * e[k];"),
     "wall_mirror_factor": ("d += (2.0 * vw[k] - vi[k]) * e[k];",
                            "d += (vw[k] - vi[k]) * e[k];"),
     "wall_viscous_mirror": ("a[k] += coef * (2.0 * (s->v[i][k] - s->vw[w][k]));",
                             "a[k] += coef * (s->v[i][k] - s->vw[w][k]);"),
+    "wall_accel_sign": ("gdot += (s->xw[w][k] - s->x[i][k]) * (s->g[k] - s->aw[w][k]);",
+                        "gdot += (s->xw[w][k] - s->x[i][k]) * (s->g[k] + s->aw[w][k]);"),
+    "wall_accel_law": ("a[c] = -s->awu[u][c] * s->womega * s->womega * sn;",
+                       "a[c] = -s->awu[u][c] * s->womega * sn;"),
     "translate_half_step_time": ("if (s->wtranslate) place_walls(s, s->t + 0.5 * dt);",
                                  "if (s->wtranslate) place_walls(s, s->t + dt);"),
-    "translate_speed": ("for (int c = 0; c < 3; ++c) s->xw[k][c] = s->xw0[u][c] + t * s->vwu[u][c];",
-                        "for (int c = 0; c < 3; ++c) s->xw[k][c] = s->xw0[u][c] + 0.5 * t * s->vwu[u][c];"),
+    "translate_speed": ("x[c] = s->xw0[u][c] + t * s->vwu[u][c] + s->awu[u][c] * sn;",
+                        "x[c] = s->xw0[u][c] + 0.5 * t * s->vwu[u][c] + s->awu[u][c] * sn;"),
     "translate_not_rebinned": ("if (s->wtranslate) bin_walls(s, s->t);",
                                "if (0) bin_walls(s, s->t);"),
     "wall_viscous_velocity_sign": ("a[k] += coef * (2.0 * (s->v[i][k] - s->vw[w][k]));",

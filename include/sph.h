@@ -210,6 +210,19 @@ int sph_checkpoint_load(sph_ctx* ctx, const void* buf, size_t bytes);
  * wall buffers cannot be allocated. */
 int sph_set_wall_translation(sph_ctx* ctx, const uint8_t* moves);
 
+/* Translating walls that may also oscillate: wall u with moves[u] != 0
+ * follows x_w(t) = x_w(0) + v t + A sin(omega t), A = amplitude[u * dim ..]
+ * (host, nw * dim doubles, user order; NULL = no oscillation), v its given
+ * velocity (zero for walls given none).  Its velocity is then
+ * v + A omega cos(omega t) and its acceleration a_w = -A omega^2
+ * sin(omega t), which enters the mirrored wall pressure
+ * p_w = p_i + rho_i (x_w - x_i).(g - a_w).  sph_set_wall_translation(ctx,
+ * moves) is this call with no amplitude.  The neighbour lists' drift bound
+ * takes |v| + |A| |omega| as the wall speed.  SPH_E_INVALID for a non-finite
+ * omega or amplitude; otherwise as sph_set_wall_translation. */
+int sph_set_wall_motion(sph_ctx* ctx, const uint8_t* moves, double omega,
+                        const double* amplitude);
+
 /* Queues n acoustic steps of the dual-criteria schedule.  Each step: when the
  * elapsed time of the current advection step has reached its length (or on
  * the first step), a new advection step begins (length 0.25 h / max(U_ref,

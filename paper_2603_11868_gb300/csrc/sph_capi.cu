@@ -41,6 +41,7 @@ struct sph_ctx {
   // trans_blocks: the buffers of translating walls (sph_set_wall_translation)
   std::vector<Block> fluid_blocks, wall_blocks, fixed_blocks, trans_blocks;
   std::vector<double> wall_vel_host;  // given wall velocities (n * dim), empty at rest
+  bool motion_owns_vel = false;  // wall velocity arrays allocated by sph_set_wall_motion
   std::string err;
   bool fluid_set = false;
 };
@@ -74,8 +75,17 @@ void clear_translation(sph_ctx* c) {
   c->B.wkeys[0] = c->B.wkeys[1] = nullptr;
   c->B.wvals[0] = c->B.wvals[1] = nullptr;
   c->B.wtile_hist = nullptr;
-  c->P.variant &= ~kVariantTranslatingWall;
+  c->B.wall_amp = nullptr;
+  c->B.wall_acc = nullptr;
+  c->P.variant &= ~(kVariantTranslatingWall | kVariantAccelWall);
   c->P.wall_vmax = 0.0;
+  c->P.wall_omega = 0.0;
+  if (c->motion_owns_vel) {
+    c->B.wall_vel = nullptr;
+    c->B.wall_v0 = nullptr;
+    c->P.variant &= ~kVariantMovingWall;
+    c->motion_owns_vel = false;
+  }
 }
 
 #define CK(call)                                  \
@@ -599,14 +609,14 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
 // setup it belongs to.
 namespace {
 constexpr char kCkptMagic[8] = {'S', 'P', 'H', 'C', 'K', 'P', 'T', '1'};
-constexpr int32_t kCkptVersion = 1;
+constexpr int32_t kCkptVersion = 2;
 
 struct CkptHeader {
   char magic[8];
   int32_t version, dim, precision, variant;
   int64_t n, nw, ncell;
   int32_t nx, ny, nz, pad_;
-  double h, cs, rho0, c0, mu, U_ref, m, V, wall_vmax;
+  double h, cs, rho0, c0, mu, U_ref, m, V, wall_vmax, wall_omega;
   double lo[3], g[3];
   uint64_t scalars_bytes;
 };
@@ -634,6 +644,7 @@ void ckpt_header(const sph_ctx* c, CkptHeader* hd) {
   hd->m = P.m;
   hd->V = P.V;
   hd->wall_vmax = P.wall_vmax;
+  hd->wall_omega = P.wall_omega;
   for (int k = 0; k < 3; ++k) {
     hd->lo[k] = P.lo[k];
     hd->g[k] = P.g[k];
@@ -709,6 +720,7 @@ int sph_checkpoint_load(sph_ctx* c, const void* buf, size_t bytes) {
                     hd.h == mine.h && hd.cs == mine.cs && hd.rho0 == mine.rho0 &&
                     hd.c0 == mine.c0 && hd.mu == mine.mu && hd.U_ref == mine.U_ref &&
                     hd.m == mine.m && hd.V == mine.V && hd.wall_vmax == mine.wall_vmax &&
+                    hd.wall_omega == mine.wall_omega &&
                     memcmp(hd.lo, mine.lo, sizeof(hd.lo)) == 0 &&
                     memcmp(hd.g, mine.g, sizeof(hd.g)) == 0;
   if (!same)
@@ -788,33 +800,44 @@ int sph_checkpoint_load(sph_ctx* c, const void* buf, size_t bytes) {
   return leave(c);
 }
 
-int sph_set_wall_translation(sph_ctx* c, const uint8_t* moves) {
-  TraceRange trace_("sph_set_wall_translation");
+int sph_set_wall_motion(sph_ctx* c, const uint8_t* moves, double omega,
+                        const double* amplitude) {
+  TraceRange trace_("sph_set_wall_motion");
   if (!c) return SPH_E_INVALID;
+  if (!std::isfinite(omega)) return set_err(c, SPH_E_INVALID, "omega is not finite");
+  const size_t n = (size_t)c->P.nw;
+  const int d = c->P.dim;
+  if (amplitude)
+    for (size_t q = 0; q < n * (size_t)d; ++q)
+      if (!std::isfinite(amplitude[q]))
+        return set_err(c, SPH_E_INVALID, "wall amplitude is not finite");
   int rc = enter(c);
   if (rc) return rc;
   CK(cudaStreamSynchronize(c->stream));
   drop_graph(c);
   dev_free_list(c, c->trans_blocks);
   clear_translation(c);
-  const size_t n = (size_t)c->P.nw;
   if (n == 0) return leave(c);
-  const int d = c->P.dim;
-  bool any = false;
+  bool any = false, osc = false;
   double vmax = 0.0;
   if (moves) {
     for (size_t u = 0; u < n; ++u) {
       if (!moves[u]) continue;
       any = true;
-      if (c->wall_vel_host.empty()) continue;
-      double v2 = 0.0;
-      for (int k = 0; k < d; ++k) v2 += c->wall_vel_host[u * d + k] * c->wall_vel_host[u * d + k];
-      vmax = std::max(vmax, std::sqrt(v2));
+      double v2 = 0.0, a2 = 0.0;
+      for (int k = 0; k < d; ++k) {
+        if (!c->wall_vel_host.empty())
+          v2 += c->wall_vel_host[u * d + k] * c->wall_vel_host[u * d + k];
+        if (amplitude) a2 += amplitude[u * d + k] * amplitude[u * d + k];
+      }
+      if (a2 > 0.0 && omega != 0.0) osc = true;
+      vmax = std::max(vmax, std::sqrt(v2) + std::sqrt(a2) * std::fabs(omega));
     }
   }
-  // walls given no velocity are at rest: nothing to translate
-  if (!c->B.wall_v0) any = false;
+  // walls given no velocity and no oscillation are at rest: nothing moves
+  if (!c->B.wall_v0 && !osc) any = false;
   auto A = [&](size_t bytes) { return dev_alloc(c, bytes, c->trans_blocks); };
+  const size_t rec = n * (d == 3 ? 4 : 2) * tsize(c);
   uint8_t* dm = any ? (uint8_t*)A(n) : nullptr;
   c->B.wall_io = (double*)A(n * 3 * 8);
   c->B.wall_key = (uint32_t*)A(n * 4);
@@ -824,8 +847,14 @@ int sph_set_wall_translation(sph_ctx* c, const uint8_t* moves) {
   }
   const size_t tiles = (n + kSortTile - 1) / kSortTile;
   c->B.wtile_hist = (uint32_t*)A(tiles * ((size_t)1 << kMaxRadixBits) * 4);
+  double* amp = osc ? (double*)A(n * 3 * 8) : nullptr;
+  void* acc = osc ? A(rec) : nullptr;
+  const bool need_vel = osc && !c->B.wall_vel;
+  void* vel = need_vel ? A(rec) : nullptr;
+  double* v0 = need_vel ? (double*)A(n * 3 * 8) : nullptr;
   const bool ok = (!any || dm) && c->B.wall_io && c->B.wall_key && c->B.wkeys[0] &&
-                  c->B.wkeys[1] && c->B.wvals[0] && c->B.wvals[1] && c->B.wtile_hist;
+                  c->B.wkeys[1] && c->B.wvals[0] && c->B.wvals[1] && c->B.wtile_hist &&
+                  (!osc || (amp && acc)) && (!need_vel || (vel && v0));
   if (!ok) {
     dev_free_list(c, c->trans_blocks);
     clear_translation(c);
@@ -837,6 +866,25 @@ int sph_set_wall_translation(sph_ctx* c, const uint8_t* moves) {
     c->P.variant |= kVariantTranslatingWall;
     c->P.wall_vmax = vmax;
   }
+  if (osc) {
+    // amplitudes: host AoS -> wall_io (scratch here) -> SoA
+    CK(cudaMemcpyAsync(c->B.wall_io, amplitude, n * d * 8, cudaMemcpyHostToDevice, c->stream));
+    double* soa[3] = {amp, amp + n, amp + 2 * n};
+    if (d == 2) CK(cudaMemsetAsync(amp + 2 * n, 0, n * 8, c->stream));
+    launch_deinterleave(c->B.wall_io, (int)n, d, soa, c->stream);
+    c->B.wall_amp = amp;
+    c->B.wall_acc = acc;
+    if (need_vel) {
+      // walls given without velocities: zero base velocity, records owned here
+      CK(cudaMemsetAsync(v0, 0, n * 3 * 8, c->stream));
+      c->B.wall_vel = vel;
+      c->B.wall_v0 = v0;
+      c->P.variant |= kVariantMovingWall;
+      c->motion_owns_vel = true;
+    }
+    c->P.variant |= kVariantAccelWall;
+    c->P.wall_omega = omega;
+  }
   // walls binned again where they are now (back at their given positions
   // when none translates)
   if (c->precision == SPH_FP64)
@@ -847,6 +895,10 @@ int sph_set_wall_translation(sph_ctx* c, const uint8_t* moves) {
   CK(invalidate_lists(c));
   CK(cudaStreamSynchronize(c->stream));
   return leave(c);
+}
+
+int sph_set_wall_translation(sph_ctx* c, const uint8_t* moves) {
+  return sph_set_wall_motion(c, moves, 0.0, nullptr);
 }
 
 int sph_step(sph_ctx* c, int n) {

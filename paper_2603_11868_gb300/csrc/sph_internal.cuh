@@ -58,6 +58,9 @@ constexpr int kVariantMovingWall = 8;  // walls with a prescribed (sliding) velo
 // some walls translate with their velocity: binned again at every rebuild,
 // moved with the fluid's half-drifts
 constexpr int kVariantTranslatingWall = 16;
+// some translating walls also oscillate: their acceleration enters the wall
+// pressure, p_w = p_i + rho_i (x_w - x_i).(g - a_w)
+constexpr int kVariantAccelWall = 32;
 
 // error flag bits (sticky, device)
 constexpr int kFlagOutOfDomain = 1;
@@ -90,9 +93,11 @@ struct Params {
   // blended free-surface density reinitialisation instead of the clamp;
   // kVariantTransport -> transport-velocity correction after the summation;
   // kVariantMovingWall -> the wall terms read the prescribed wall velocity;
-  // kVariantTranslatingWall -> some walls move with their velocity
+  // kVariantTranslatingWall -> some walls move with their velocity;
+  // kVariantAccelWall -> some of them oscillate (wall_omega, wall_amp)
   int variant;
-  double wall_vmax;  // largest speed of a translating wall (0 when none translates)
+  double wall_vmax;   // bound on a translating wall's speed (0 when none translates)
+  double wall_omega;  // angular frequency of the walls' oscillation
   // position of this tank in the arrays of a batch (all zero for one tank):
   // first fluid slot, first wall slot, first entry of its cell offsets
   int foff, woff;
@@ -187,6 +192,8 @@ struct DevBuffers {
   // placed at the binning time (user order SoA) and the wall sort's own
   // ping-pong and histogram buffers
   const uint8_t* wall_moves;
+  const double* wall_amp;  // oscillation amplitudes (user order SoA), null: none
+  void* wall_acc;          // wall accelerations (T4 / T2, sorted), null: none
   double* wall_io;
   uint32_t* wall_key;  // binned cell key of each sorted wall
   uint32_t* wkeys[2];

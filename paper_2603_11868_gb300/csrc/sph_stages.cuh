@@ -627,6 +627,15 @@ __device__ __forceinline__ T wall_vel_dot(const DevBuffers& B, int j, T ex, T ey
   return vw.x * ex + vw.y * ey + WR::z(vw) * ez;
 }
 
+// (x_i - x_w) . a_w for an oscillating wall particle j (kVariantAccelWall):
+// with it the mirrored wall pressure p_w = p_i + rho_i (x_w - x_i).(g - a_w).
+template <int D, class T>
+__device__ __forceinline__ T wall_acc_dot(const DevBuffers& B, int j, T rx, T ry, T rz) {
+  using WR = WallRec<D, T>;
+  const typename WR::WV aw = ((const typename WR::WV*)B.wall_acc)[j];
+  return aw.x * rx + aw.y * ry + WR::z(aw) * rz;
+}
+
 // List build (right after the rebuild, positions = binned positions): one
 // direct search per particle that records the candidates closer than
 // 2h + skin.  The membership test runs in the pair type on the loop records;
@@ -1050,7 +1059,7 @@ inline bool wall_vel_code(int variant) {
 // Reads records of buffer 0, writes records of buffer 1.  kWallVel compiles
 // in the (run-time checked) wall-velocity term of sliding walls
 // (kVariantMovingWall); see wall_vel_code() for when it is left out.
-template <int D, class T, bool kWallVel = true>
+template <int D, class T, bool kWallVel = true, bool kAccel = false>
 __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers& B, const KC<T>& k,
                                                DevScalars* sc, int i, int end, int stride,
                                      const ShiftTable* tab) {
@@ -1103,8 +1112,9 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
       const T UL = -(vxi * ex + vyi * ey + vzi * ez);
       T UR, p_j, rho_j;
       if (w) {
-        // mirrored state: p_w = p_i + rho_i (x_w - x_i).g, x_w - x_i = -r_vec
-        const T gdot = -(rx * k.g[0] + ry * k.g[1] + rz * k.g[2]);
+        // mirrored state: p_w = p_i + rho_i (x_w - x_i).(g - a_w), x_w - x_i = -r_vec
+        T gdot = -(rx * k.g[0] + ry * k.g[1] + rz * k.g[2]);
+        if constexpr (kAccel) gdot += wall_acc_dot<D, T>(B, j, rx, ry, rz);
         p_j = p_i + rho_i * gdot;
         rho_j = k.rho0 + p_j * k.inv_c0sq;
         UR = -UL;
@@ -1168,17 +1178,17 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
   }
 }
 
-template <int D, class T, bool kWallVel>
+template <int D, class T, bool kWallVel, bool kAccel = false>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) k_pressure(Params P, DevBuffers B, KC<T> k) {
   __shared__ ShiftTable tab;
   if constexpr (Local<T>::kLocal) fill_shift_table(tab);
-  pressure_range<D, T, kWallVel>(P, B, k, B.sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+  pressure_range<D, T, kWallVel, kAccel>(P, B, k, B.sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
                        gridDim.x * blockDim.x, &tab);
 }
 
 // Riemann density relaxation: reads records of buffer 1; drho and rho (state).
 // kWallVel as for the pressure relaxation.
-template <int D, class T, bool kWallVel = true>
+template <int D, class T, bool kWallVel = true, bool kAccel = false>
 __device__ __forceinline__ void density_relax_range(const Params& P, const DevBuffers& B,
                                                     const KC<T>& k, DevScalars* sc, int i,
                                                     int end, int stride,
@@ -1224,7 +1234,8 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
       const T ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
       const T UL = -(vxi * ex + vyi * ey + vzi * ez);
       if (w) {
-        const T gdot = -(rx * k.g[0] + ry * k.g[1] + rz * k.g[2]);
+        T gdot = -(rx * k.g[0] + ry * k.g[1] + rz * k.g[2]);
+        if constexpr (kAccel) gdot += wall_acc_dot<D, T>(B, j, rx, ry, rz);
         const T pw_ = p_i + rho_i * gdot;
         const T rho_w = k.rho0 + pw_ * k.inv_c0sq;
         const T rbar = k.half * (rho_i + rho_w);
@@ -1253,13 +1264,13 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
 
 // One tank: block 0 also publishes this step's velocity maximum for the next
 // step's schedule (a batch does that in its schedule kernel).
-template <int D, class T, bool kWallVel>
+template <int D, class T, bool kWallVel, bool kAccel = false>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) k_density_relax(Params P, DevBuffers B, KC<T> k) {
   DevScalars* sc = B.sc;
   __shared__ ShiftTable tab;
   if constexpr (Local<T>::kLocal) fill_shift_table(tab);
   if (blockIdx.x == 0 && threadIdx.x == 0) sc->vmax2_cur = sc->vmax2_next;
-  density_relax_range<D, T, kWallVel>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+  density_relax_range<D, T, kWallVel, kAccel>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
                             gridDim.x * blockDim.x, &tab);
 }
 
@@ -1314,45 +1325,101 @@ __global__ void k_wall_gather(Params P, DevBuffers B, const double* __restrict__
 // rebuild (kBinAtRebuild, when a saved state is restored).
 constexpr int kBinAtStepStart = 0, kBinNow = 1, kBinAtRebuild = 2;
 
+// Kinematics of translating wall u (user order) along axis c at time t:
+// x0 + v t + A sin(omega t), v + A omega cos(omega t), -A omega^2 sin(omega t).
+struct WallKin {
+  double sn, cs, w;
+  __device__ WallKin(const Params& P, double t)
+      : sn(sin(P.wall_omega * t)), cs(cos(P.wall_omega * t)), w(P.wall_omega) {}
+  __device__ double x(const DevBuffers& B, size_t nw, size_t u, int c, double t) const {
+    double x = B.wall_x0[c * nw + u] + t * B.wall_v0[c * nw + u];
+    if (B.wall_amp) x += B.wall_amp[c * nw + u] * sn;
+    return x;
+  }
+  __device__ double v(const DevBuffers& B, size_t nw, size_t u, int c) const {
+    double v = B.wall_v0[c * nw + u];
+    if (B.wall_amp) v += B.wall_amp[c * nw + u] * w * cs;
+    return v;
+  }
+  __device__ double a(const DevBuffers& B, size_t nw, size_t u, int c) const {
+    return B.wall_amp ? -B.wall_amp[c * nw + u] * w * w * sn : 0.0;
+  }
+};
+
 template <int D>
 __global__ void k_wall_place(Params P, DevBuffers B, int gated, int when) {
   DevScalars* sc = B.sc;
   if (gated && !sc->new_adv) return;
   const double t = when == kBinNow ? sc->t : (when == kBinAtRebuild ? sc->t_reb : sc->t0);
+  const WallKin K(P, t);
   const size_t nw = (size_t)P.nw;
   for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < nw;
        u += (size_t)gridDim.x * blockDim.x) {
     const bool moves = B.wall_moves && B.wall_moves[u] && B.wall_v0;
-    for (int c = 0; c < 3; ++c) {
-      const double x = B.wall_x0[c * nw + u];
-      B.wall_io[c * nw + u] = moves ? x + t * B.wall_v0[c * nw + u] : x;
-    }
+    for (int c = 0; c < 3; ++c)
+      B.wall_io[c * nw + u] = moves ? K.x(B, nw, u, c, t) : B.wall_x0[c * nw + u];
   }
 }
 
-// Moves the translating walls (sorted slots) to the fluid's time: t0 + dt/2
-// after the first half-drift (`half`), t0 + dt after the second; their
-// records stay relative to the cell they were binned in.
+// Moves the translating walls (sorted slots) to a time: the fluid's after
+// the first half-drift (kMoveHalf: t0 + dt/2) or the second (kMoveFull:
+// t0 + dt), the step's start (kMoveStepStart, after a rebuild) or now
+// (kMoveNow); their records stay relative to the cell they were binned in.
+// Oscillating walls also get their velocity and acceleration at that time.
+constexpr int kMoveHalf = 1, kMoveFull = 0, kMoveStepStart = 2, kMoveNow = 3;
+
 template <int D, class T>
-__global__ void k_wall_move(Params P, DevBuffers B, int half) {
+__global__ void k_wall_move(Params P, DevBuffers B, int when) {
   using WR = WallRec<D, T>;
   const DevScalars* sc = B.sc;
-  const double t = sc->t0 + (half ? 0.5 : 1.0) * sc->dt_ac;
+  const double t = when == kMoveHalf   ? sc->t0 + 0.5 * sc->dt_ac
+                   : when == kMoveFull ? sc->t0 + sc->dt_ac
+                   : when == kMoveNow  ? sc->t
+                                       : sc->t0;
+  const WallKin K(P, t);
   const size_t nw = (size_t)P.nw;
   typename WR::WV* out = (typename WR::WV*)B.wallP;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nw;
        k += (size_t)gridDim.x * blockDim.x) {
     const uint32_t u = B.wall_id[k];
     if (!B.wall_moves || !B.wall_v0 || !B.wall_moves[u]) continue;
-    const double x = B.wall_x0[u] + t * B.wall_v0[u];
-    const double y = B.wall_x0[nw + u] + t * B.wall_v0[nw + u];
-    const double z = D == 3 ? B.wall_x0[2 * nw + u] + t * B.wall_v0[2 * nw + u] : 0.0;
+    const double x = K.x(B, nw, u, 0, t);
+    const double y = K.x(B, nw, u, 1, t);
+    const double z = D == 3 ? K.x(B, nw, u, 2, t) : 0.0;
     B.wall_xyz[k] = x;
     B.wall_xyz[nw + k] = y;
     if (D == 3) B.wall_xyz[2 * nw + k] = z;
     T ox, oy, oz;
     Local<T>::enc(P, B.ctab, decode(B.wall_key[k], P), x, y, z, ox, oy, oz);
     out[k] = WR::make(ox, oy, oz);
+    if (B.wall_amp) {
+      ((typename WR::WV*)B.wall_vel)[k] =
+          WR::make((T)K.v(B, nw, u, 0), (T)K.v(B, nw, u, 1), D == 3 ? (T)K.v(B, nw, u, 2) : T(0));
+      ((typename WR::WV*)B.wall_acc)[k] =
+          WR::make((T)K.a(B, nw, u, 0), (T)K.a(B, nw, u, 1), D == 3 ? (T)K.a(B, nw, u, 2) : T(0));
+    }
+  }
+}
+
+// The same at the step's start, for the gated rebuild of the plain launch
+// sequence: runs only when the step begins an advection step.
+template <int D, class T>
+__global__ void k_wall_move_gated(Params P, DevBuffers B) {
+  if (!B.sc->new_adv) return;
+  // one block-uniform decision, then the same body
+  using WR = WallRec<D, T>;
+  const DevScalars* sc = B.sc;
+  const double t = sc->t0;
+  const WallKin K(P, t);
+  const size_t nw = (size_t)P.nw;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nw;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t u = B.wall_id[k];
+    if (!B.wall_moves || !B.wall_v0 || !B.wall_amp || !B.wall_moves[u]) continue;
+    ((typename WR::WV*)B.wall_vel)[k] =
+        WR::make((T)K.v(B, nw, u, 0), (T)K.v(B, nw, u, 1), D == 3 ? (T)K.v(B, nw, u, 2) : T(0));
+    ((typename WR::WV*)B.wall_acc)[k] =
+        WR::make((T)K.a(B, nw, u, 0), (T)K.a(B, nw, u, 1), D == 3 ? (T)K.a(B, nw, u, 2) : T(0));
   }
 }
 
@@ -1393,7 +1460,16 @@ void enqueue_wall_rebin_t(const StageArgs& a, cudaStream_t s, int gated, int whe
   k_wall_gather<D, T><<<gw, 256, 0, s>>>(P, W, xs[0], xs[1], xs[2], W.wall_xyz,
                                          W.wall_xyz + nw, W.wall_xyz + 2 * nw, W.wall_v0, gated);
   launch_cell_offsets(W.wkeys[cur], P.nw, P.ncell, W.wall_cb, W.sc, gated, 0, s);
-  if (when == kBinAtRebuild) k_wall_move<D, T><<<gw, 256, 0, s>>>(P, W, 0);
+  if (when == kBinAtRebuild) {
+    k_wall_move<D, T><<<gw, 256, 0, s>>>(P, W, kMoveFull);
+  } else if (P.variant & kVariantAccelWall) {
+    // velocities and accelerations of oscillating walls at the binning time
+    // (the gather wrote the constant part); gated like the rebuild
+    if (!gated || when != kBinAtStepStart)
+      k_wall_move<D, T><<<gw, 256, 0, s>>>(P, W, when == kBinNow ? kMoveNow : kMoveStepStart);
+    else
+      k_wall_move_gated<D, T><<<gw, 256, 0, s>>>(P, W);
+  }
 }
 
 template <int D, class T>
@@ -1451,16 +1527,21 @@ void enqueue_acoustic_t(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev = nu
   const int gw = grid_for(P.nw, 256, L.blocks_stream);
   mark(ev, kStageHalf1, s);
   k_half1<D, T><<<gs, L.block_stream, 0, s>>>(P, B);
-  if (translating) k_wall_move<D, T><<<gw, 256, 0, s>>>(P, B, 1);
+  if (translating) k_wall_move<D, T><<<gw, 256, 0, s>>>(P, B, kMoveHalf);
   mark(ev, kStagePressure, s);
   const bool wall_vel = wall_vel_code<D>(P.variant);
-  if (wall_vel)
+  const bool accel = (P.variant & kVariantAccelWall) != 0;
+  if (accel)
+    k_pressure<D, T, true, true><<<gl, L.block_loop, 0, s>>>(P, B, k);
+  else if (wall_vel)
     k_pressure<D, T, true><<<gl, L.block_loop, 0, s>>>(P, B, k);
   else
     k_pressure<D, T, false><<<gl, L.block_loop, 0, s>>>(P, B, k);
-  if (translating) k_wall_move<D, T><<<gw, 256, 0, s>>>(P, B, 0);
+  if (translating) k_wall_move<D, T><<<gw, 256, 0, s>>>(P, B, kMoveFull);
   mark(ev, kStageDensityRelax, s);
-  if (wall_vel)
+  if (accel)
+    k_density_relax<D, T, true, true><<<gl, L.block_loop, 0, s>>>(P, B, k);
+  else if (wall_vel)
     k_density_relax<D, T, true><<<gl, L.block_loop, 0, s>>>(P, B, k);
   else
     k_density_relax<D, T, false><<<gl, L.block_loop, 0, s>>>(P, B, k);

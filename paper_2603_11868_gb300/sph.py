@@ -51,7 +51,8 @@ EXPORTS = ("sph_create", "sph_set_particles", "sph_step", "sph_get_fields", "sph
            "sph_batch_profile_stages", "sph_batch_kernels_per_step", "sph_batch_set_option",
            "sph_batch_synchronize", "sph_batch_last_error", "sph_batch_destroy",
            "sph_autotune", "sph_batch_autotune", "sph_debug_list_lengths",
-           "sph_set_wall_translation", "sph_checkpoint_bytes", "sph_checkpoint_save",
+           "sph_set_wall_translation", "sph_set_wall_motion", "sph_checkpoint_bytes",
+           "sph_checkpoint_save",
            "sph_checkpoint_load")
 SPH_MAX_TANKS = 1024
 SPH_NOALLOC_MAX_PARTICLES = 1 << 20
@@ -118,6 +119,8 @@ def load(path: str | None = None):
         L.sph_set_particles.argtypes = [vp, i, sz, vp, vp, vp]
         L.sph_set_wall_translation.restype = i
         L.sph_set_wall_translation.argtypes = [vp, vp]
+        L.sph_set_wall_motion.restype = i
+        L.sph_set_wall_motion.argtypes = [vp, vp, d, vp]
         L.sph_checkpoint_bytes.restype = sz
         L.sph_checkpoint_bytes.argtypes = [vp]
         L.sph_checkpoint_save.restype = i
@@ -249,6 +252,13 @@ def sph_set_particles(ctx, kind, pos, vel=None, rho=None):
 def sph_set_wall_translation(ctx, moves=None):
     moves = None if moves is None else np.ascontiguousarray(moves, dtype=np.uint8)
     _check(ctx, load().sph_set_wall_translation(ctx, _ptr(moves)))
+
+
+def sph_set_wall_motion(ctx, moves, omega=0.0, amplitude=None):
+    moves = None if moves is None else np.ascontiguousarray(moves, dtype=np.uint8)
+    amplitude = None if amplitude is None else np.ascontiguousarray(amplitude,
+                                                                     dtype=np.float64)
+    _check(ctx, load().sph_set_wall_motion(ctx, _ptr(moves), float(omega), _ptr(amplitude)))
 
 
 def sph_checkpoint_save(ctx):
@@ -732,7 +742,8 @@ class Solver:
         if case.wall is not None and len(case.wall):
             sph_set_particles(self.ctx, SPH_WALL, case.wall, getattr(case, "wall_vel", None))
             if getattr(case, "wall_moves", None) is not None:
-                sph_set_wall_translation(self.ctx, case.wall_moves)
+                sph_set_wall_motion(self.ctx, case.wall_moves, getattr(case, "wall_omega", 0.0),
+                                    getattr(case, "wall_amplitude", None))
         sph_set_particles(self.ctx, SPH_FLUID, case.fluid, case.vel, case.rho)
 
     @property

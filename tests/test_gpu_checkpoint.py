@@ -76,6 +76,11 @@ def test_resume_with_translating_walls(sph, precision):
     _resume_equals_continuous(sph, cases.piston_channel_2d(V=2.0), precision, 37, 90)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_resume_with_oscillating_walls(sph, precision):
+    _resume_equals_continuous(sph, cases.shaken_tank_2d(), precision, 41, 100)
+
+
 def test_checkpoint_of_another_setup_is_refused(sph):
     a = sph.Solver(cases.dam_break_2d(), precision="mixed")
     a.step(3)

@@ -253,3 +253,44 @@ def test_clearing_the_translation_puts_the_walls_back(sph, O):
     o.step(5)
     assert rel(got["pos"], o.field(O.POS)) <= 1e-10
     assert rel(got["rho"], o.field(O.RHO)) <= 1e-10
+
+
+# --------------------------------------------------------------------------
+# oscillating walls (sph_set_wall_motion): the shaken tank, whose walls are
+# given no velocity (the motion call supplies the velocity records)
+def test_oscillating_fp64_parity(sph, O):
+    case = cases.shaken_tank_2d()
+    for steps, tol in ((1, 1e-10), (120, 1e-8)):
+        got, want = _run(sph, O, case, "fp64", steps)
+        for k in ("pos", "vel", "rho", "acc"):
+            assert rel(got[k], want[k]) <= tol, (steps, k, rel(got[k], want[k]))
+        # the pressure tilt is small against the background pressure: compare
+        # the deviation from the mean
+        dp_got, dp_want = got["p"] - want["p"].mean(), want["p"] - want["p"].mean()
+        assert np.abs(dp_got - dp_want).max() <= tol * 1e3 * np.abs(dp_want).max(), steps
+
+
+def test_oscillating_mixed_one_step(sph, O):
+    case = cases.shaken_tank_2d()
+    got, want = _run(sph, O, case, "mixed", 1)
+    for k in ("acc", "aprior"):
+        err = np.abs(got[k] - want[k]).max() / max(np.abs(want[k]).max(), 1.0)
+        assert err <= 1e-5, (k, err)
+    assert rel(got["rho"], want["rho"]) <= 1e-6
+
+
+def test_shaken_tank_on_the_gpu(sph):
+    from test_oracle_walls import shaken_lockin  # same folder (pytest prepends it)
+    c = cases.shaken_tank_2d()
+    s = sph.Solver(c, precision="mixed")
+
+    def step_fields():
+        s.step(1)
+        sc = s.scalars()
+        f = s.fields("pos", "vel", "p", "rho")
+        return sc["t"], sc["dt_ac"], f["pos"], f["vel"], f["p"], f["rho"]
+
+    slope_ratio, vel_ratio = shaken_lockin(step_fields, c)
+    s.close()
+    assert abs(slope_ratio - 1) < 0.10, slope_ratio
+    assert abs(vel_ratio - 1) < 0.10, vel_ratio

@@ -78,21 +78,44 @@ MUTATIONS = {
 }
 
 
-@pytest.mark.slow
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
-def test_planted_mistake_is_caught(name, tmp_path):
+def _run_mutation(name, workdir):
+    """Compile the oracle with mutation `name` planted and run the pin files
+    against it; returns (anchor found, pytest return code, output tail)."""
     src = open(SRC).read()
     old, new = MUTATIONS[name]
-    assert src.count(old) >= 1, f"mutation anchor for {name} not found"
+    if src.count(old) < 1:
+        return False, None, ""
     mutated = src.replace(old, new, 1).replace(
         '#include "sph_oracle.h"', '#include "%s"' % os.path.join(ROOT, "oracle", "sph_oracle.h"))
-    c = tmp_path / "sph_oracle.c"
-    c.write_text(mutated)
-    so = tmp_path / "liboracle.so"
+    c = os.path.join(workdir, "sph_oracle.c")
+    with open(c, "w") as fh:
+        fh.write(mutated)
+    so = os.path.join(workdir, "liboracle.so")
     subprocess.run(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared", "-o",
-                    str(so), str(c), "-lm"], check=True)
-    env = dict(os.environ, ORACLE_LIB_OVERRIDE=str(so))
+                    so, c, "-lm"], check=True)
+    env = dict(os.environ, ORACLE_LIB_OVERRIDE=so)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         "-m", "not gpu", *PIN_FILES], cwd=ROOT, env=env,
-                       capture_output=True, text=True, timeout=600)
-    assert r.returncode == 1, f"pins did not catch {name}:\n{r.stdout[-2000:]}"
+                       capture_output=True, text=True, timeout=900)
+    return True, r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def mutation_results(tmp_path_factory):
+    """Every planted mistake, run concurrently (each a compiler and a pytest
+    child process of its own)."""
+    import concurrent.futures as cf
+    names = sorted(MUTATIONS)
+    dirs = {n: str(tmp_path_factory.mktemp("mut_" + n)) for n in names}
+    workers = max(1, min(8, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {n: ex.submit(_run_mutation, n, dirs[n]) for n in names}
+        return {n: f.result() for n, f in futs.items()}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, mutation_results):
+    found, code, tail = mutation_results[name]
+    assert found, f"mutation anchor for {name} not found"
+    assert code == 1, f"pins did not catch {name}:\n{tail}"

@@ -232,7 +232,12 @@ int alloc_fluid(sph_batch* b, size_t n) {
   }
   B.sigma = Al(nn * ts);
   B.sigma64 = (double*)Al(nn * 8);
-  ok &= B.sigma64 != nullptr;
+  for (int k = 0; k < 3; ++k) {
+    B.xreb[k] = k < d ? Al(nn * ts) : nullptr;
+    ok &= k >= d || B.xreb[k];
+  }
+  B.bud = (float*)Al(nn * 4);
+  ok &= B.sigma64 != nullptr && B.bud != nullptr;
   const size_t pbytes = 4 * ts;
   const size_t sbytes = (d == 3 ? 4 : 2) * ts;
   for (int p = 0; p < 2; ++p) {

@@ -53,11 +53,12 @@ __global__ void kb_reorder(BatchArgs A, DevBuffers B, const WorkList* wl) {
     const DevBuffers Bt = tank_buffers(A, B, t);
     const int base = wl->cbase[a];
     const int end = min(off + tile, P.n);
+    const BudgetArgs ba = budget_args(P, A.tsc[t]);
     for (int q = off + (int)threadIdx.x; q < end; q += blockDim.x) {
       const uint32_t key = keys[base + q] - P.cell_base;
       const int k = P.foff + q;
       A.bkey[k] = key;
-      reorder_slot<D, T>(P, Bt, S, Dd, k, perm[base + q], key);
+      reorder_slot<D, T>(P, Bt, S, Dd, k, perm[base + q], key, ba);
     }
   });
 }
@@ -84,7 +85,8 @@ template <int D, class T>
 __global__ void __launch_bounds__(256, kMinBlocks<T>) kb_build_lists(BatchArgs A, DevBuffers B,
                                                                      const WorkList* wl) {
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
-    if (P.use_list) build_lists_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x);
+    if (P.use_list)
+      build_lists_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x, B.bud);
   });
 }
 

@@ -310,6 +310,12 @@ int alloc_fluid(sph_ctx* c, size_t n) {
   }
   B.sigma = A(nn * ts);
   B.sigma64 = (double*)A(nn * 8);
+  for (int k = 0; k < 3; ++k) {
+    B.xreb[k] = k < d ? A(nn * ts) : nullptr;
+    ok &= k >= d || B.xreb[k];
+  }
+  B.bud = (float*)A(nn * 4);
+  ok &= B.bud != nullptr;
   ok &= B.sigma64 != nullptr;
   const size_t pbytes = 4 * ts;
   const size_t sbytes = (d == 3 ? 4 : 2) * ts;
@@ -609,7 +615,7 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
 // setup it belongs to.
 namespace {
 constexpr char kCkptMagic[8] = {'S', 'P', 'H', 'C', 'K', 'P', 'T', '1'};
-constexpr int32_t kCkptVersion = 2;
+constexpr int32_t kCkptVersion = 3;
 
 struct CkptHeader {
   char magic[8];
@@ -653,10 +659,11 @@ void ckpt_header(const sph_ctx* c, CkptHeader* hd) {
 }
 
 // bytes per fluid particle: x, v (double), rho (double), drho (pair type),
-// a_prior (pair type), id, binned key
+// a_prior (pair type), position at the rebuild (record frame, pair type),
+// drift budget (float), id, binned key
 size_t ckpt_per_particle(const sph_ctx* c) {
   const size_t d = (size_t)c->P.dim, ts = tsize(c);
-  return 2 * d * 8 + 8 + ts + d * ts + 4 + 4;
+  return 2 * d * 8 + 8 + ts + d * ts + d * ts + 4 + 4 + 4;
 }
 }  // namespace
 
@@ -696,6 +703,8 @@ int sph_checkpoint_save(sph_ctx* c, void* buf, size_t bytes) {
   CK(D2H(B.rho[par], n * 8));
   CK(D2H(B.drho[par], n * ts));
   for (int k = 0; k < d; ++k) CK(D2H(B.aprior[k], n * ts));
+  for (int k = 0; k < d; ++k) CK(D2H(B.xreb[k], n * ts));
+  CK(D2H(B.bud, n * 4));
   CK(D2H(B.id[par], n * 4));
   CK(D2H(B.keys[B.sorted_buf], n * 4));
   CK(cudaStreamSynchronize(c->stream));
@@ -772,6 +781,8 @@ int sph_checkpoint_load(sph_ctx* c, const void* buf, size_t bytes) {
   CK(H2D(B.rho[0], n * 8));
   CK(H2D(B.drho[0], n * ts));
   for (int k = 0; k < d; ++k) CK(H2D(B.aprior[k], n * ts));
+  for (int k = 0; k < d; ++k) CK(H2D(B.xreb[k], n * ts));
+  CK(H2D(B.bud, n * 4));
   CK(H2D(B.id[0], n * 4));
   CK(H2D(B.keys[B.sorted_buf], n * 4));
   for (int k = 0; k < d; ++k) CK(cudaMemsetAsync(B.acc[k], 0, n * ts, c->stream));

@@ -126,6 +126,11 @@ struct DevScalars {
   unsigned long long shift_bits;
   double t0;     // start time of the current acoustic step
   double t_reb;  // time of the last rebuild (translating walls were binned then)
+  // neighbour-list validity since the rebuild: some particle has left its
+  // drift budget at the positions the pressure loop (and, at the rebuild, the
+  // viscous loop) reads / at those the density relaxation reads
+  int drift_bad_p, drift_bad_r;
+  double wall_budget;  // drift budget of every wall particle (translating walls)
 };
 
 template <class T>
@@ -165,6 +170,8 @@ struct DevBuffers {
   void* recI;       // mixed mode: int4 (3D) / int2 (2D) fixed-point offsets at the rebuild
   uint32_t* nl;     // neighbour lists: entry k of particle i at ((i/32) cap + k) 32 + i%32
   uint32_t* nl_cnt; // list length per particle
+  void* xreb[3];  // position of every slot at the last rebuild, record frame (T)
+  float* bud;     // drift budget of every slot since the last rebuild
   uint32_t* keys[2];  // sort ping-pong; keys[sorted_buf] holds the sorted keys
   uint32_t* vals[2];
   int sorted_buf;

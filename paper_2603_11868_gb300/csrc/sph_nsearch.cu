@@ -359,6 +359,11 @@ __device__ __forceinline__ void control_one(const Params& P, DevScalars* sc) {
     sc->list_bad = 0;
     sc->shift_bits = 0ull;
     sc->t_reb = sc->t;
+    // per-particle drift budgets are set by the reorder from each particle's
+    // speed; walls all get the translating walls' one
+    sc->drift_bad_p = 0;
+    sc->drift_bad_r = 0;
+    sc->wall_budget = 1.25 * P.wall_vmax * span;
     disp = 0.0;
   }
   sc->new_adv = adv;

@@ -385,10 +385,31 @@ __device__ __forceinline__ double warp_max(double v) {
 // Reorder after the sort: gather slot j of the live state copy into slot k of
 // the other copy and write the loop records of buffer 0 (positions; velocity;
 // old p; old rho) for binned cell key `key` (in the tank's grid).
+// Drift budget of a particle for the lists of the advection step that
+// begins: its own speed (plus what gravity adds) over the step and one
+// overshooting acoustic step, with margin, and a floor; at most bmax (half
+// the step's skin).  Any value is valid (the lists and the checks use the
+// same one); this one is sized so that it is rarely left.
+__device__ __forceinline__ float drift_budget(float speed, float gspan, float span, float floor_,
+                                             float bmax) {
+  const float b = 1.25f * (speed + gspan) * span + floor_;
+  return b < bmax ? b : bmax;
+}
+
+// Budget constants of an advection step, computed once per launch or tile.
+struct BudgetArgs {
+  float span, gspan, floor_, bmax;
+};
+__device__ __forceinline__ BudgetArgs budget_args(const Params& P, const DevScalars& sc) {
+  const double span = sc.dt_ad + 1.5 * sc.dt_ac;
+  const double g = sqrt(P.g[0] * P.g[0] + P.g[1] * P.g[1] + P.g[2] * P.g[2]);
+  return BudgetArgs{(float)span, (float)(g * span), (float)(0.01 * P.h), (float)(0.5 * sc.skin)};
+}
+
 template <int D, class T>
 __device__ __forceinline__ void reorder_slot(const Params& P, const DevBuffers& B,
                                              const Live<T>& S, const Live<T>& Dd, int k,
-                                             uint32_t j, uint32_t key) {
+                                             uint32_t j, uint32_t key, const BudgetArgs& ba) {
   using R = Rec<D, T>;
   typename R::PV* recP = (typename R::PV*)B.recP[0];
   typename R::SV* recS = (typename R::SV*)B.recS[0];
@@ -408,9 +429,15 @@ __device__ __forceinline__ void reorder_slot(const Params& P, const DevBuffers& 
     Dd.rho[k] = rho;
     Dd.drho[k] = S.drho[j];
     Dd.id[k] = S.id[j];
+    const float fvx = (float)vx, fvy = (float)vy, fvz = (float)vz;
+    B.bud[k] = drift_budget(sqrtf(fvx * fvx + fvy * fvy + fvz * fvz), ba.gspan, ba.span,
+                            ba.floor_, ba.bmax);
     T ox, oy, oz;
     const Cell ck = decode(key, P);
     Local<T>::enc(P, B.ctab, ck, x, y, z, ox, oy, oz);
+    ((T*)B.xreb[0])[k] = ox;
+    ((T*)B.xreb[1])[k] = oy;
+    if (D == 3) ((T*)B.xreb[2])[k] = oz;
     T p = (T)(P.c0sq * (rho - P.rho0));
     recP[k] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p);
     recS[k] = R::makeS((T)vx, (T)vy, (T)vz, (T)rho, p);
@@ -447,27 +474,33 @@ __global__ void k_reorder(Params P, DevBuffers B, int gated) {
   const Live<T> S = live<T>(B, par), Dd = live<T>(B, par ^ 1);
   const uint32_t* __restrict__ perm = B.vals[B.sorted_buf];
   const uint32_t* __restrict__ keys = B.keys[B.sorted_buf];
+  const BudgetArgs ba = budget_args(P, *sc);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < P.n; k += gridDim.x * blockDim.x)
-    reorder_slot<D, T>(P, B, S, Dd, k, perm[k], keys[k]);
+    reorder_slot<D, T>(P, B, S, Dd, k, perm[k], keys[k], ba);
 }
 
 // ---------------------------------------------------------------------------
 // Neighbour lists.  Direct search tests every particle of the 3^D cells
 // (about 475 in 3D) for about 81 accepted neighbours, and the pair arithmetic
-// then runs with few lanes of a warp active.  The density summation, which
-// runs right after each rebuild and walks all candidates anyway, also records
-// for every particle the candidates closer than 2h + skin, in candidate order
-// (cells dz, dy, dx; fluid then wall particles of each cell).  The other loops
-// of the advection step walk that list instead of the cells.
+// then runs with few lanes of a warp active.  Right after each rebuild every
+// particle i records the candidates j closer than 2h + b_i + b_j, in
+// candidate order (cells dz, dy, dx; fluid then wall particles of each
+// cell); the other loops of the advection step walk that list instead of the
+// cells.  b_k is particle k's drift budget, set by the reorder from its own
+// speed (walls: the translating walls' speed bound, 0 at rest).
 //
-// Exactness: a candidate left out was at least 2h + skin away at the rebuild;
-// if no particle has moved more than D since then and 2D < skin, it is still
-// farther than 2h, so the accepted set -- and, since the list keeps candidate
-// order, every sum -- is the same as with direct search.  The schedule kernel
-// keeps D as the sum of dt/2 * (largest speed) over the half-drifts since the
-// rebuild; a loop uses the list only while 2D stays below the skin (with a
-// small margin) and no list overflowed, and falls back to direct search
-// otherwise.
+// Exactness: a candidate left out was at least 2h + b_i + b_j away at the
+// rebuild; while neither particle has moved more than its budget since then,
+// it is still farther than 2h, so the accepted set -- and, since the list
+// keeps candidate order, every sum -- is the same as with direct search.
+// The kernels that move particles (first half-step, pressure kick and drift,
+// transport shift) test every particle against its budget at the positions
+// the next loop reads and set a flag for that loop (drift_bad_p: pressure
+// and, at the rebuild, viscous; drift_bad_r: density relaxation); a loop uses
+// the list only while its flag is clear and no list overflowed, and falls
+// back to direct search otherwise, until the next rebuild.  A budget follows
+// the particle's own speed rather than the fastest particle's, so the lists
+// carry few more entries than the pairs within 2h.
 //
 // Entry: neighbour index in bits 0..24, dx+1 / dy+1 / dz+1 in bits 25..30,
 // wall flag in bit 31 (particle and wall counts below 2^25).  Entry k of
@@ -571,11 +604,32 @@ __device__ __forceinline__ T shifted(T x, float d, T cs) {
   return fmaf(-d, cs, x);
 }
 
-// whether this launch may use the lists: disp is the displacement bound of the
-// positions the loop reads
-__device__ __forceinline__ bool list_ok(const Params& P, const DevScalars* sc, double disp) {
-  disp += __longlong_as_double((long long)sc->shift_bits);  // transport shifts, if any
-  return P.use_list && !sc->list_bad && 2.0 * disp < 0.999 * sc->skin - 1e-6 * P.h;
+// Whether this launch may use the lists: no list overflowed, no particle has
+// left its drift budget at the positions the loop reads (drift_bad: the flag
+// for those positions), and the translating walls, at the loop's time
+// t_eval, are within theirs.
+__device__ __forceinline__ bool list_ok(const Params& P, const DevScalars* sc, int drift_bad,
+                                        double t_eval) {
+  return P.use_list && !sc->list_bad && !drift_bad &&
+         P.wall_vmax * (t_eval - sc->t_reb) <= sc->wall_budget;
+}
+
+// Whether particle i, at record-frame position (ox, oy, oz) (relative to the
+// cell it was binned in, as at the rebuild), has moved farther than its
+// budget since the rebuild.  In float the offsets carry errors of a few
+// 1e-7 of a cell edge, far below the budgets' floor of 0.01 h, so the test
+// at 0.999 b is conservative; flag_drift records it block-wide.
+template <int D, class T>
+__device__ __forceinline__ bool drifted(const DevBuffers& B, int i, T ox, T oy, T oz) {
+  const T dx = ox - ((const T*)B.xreb[0])[i], dy = oy - ((const T*)B.xreb[1])[i];
+  const T dz = D == 3 ? oz - ((const T*)B.xreb[2])[i] : T(0);
+  const T b = T(0.999) * (T)B.bud[i];
+  return dx * dx + dy * dy + dz * dz > b * b;
+}
+// (a warp vote, no block barrier: the batched kernels call the bodies once
+// per tile; the atomic runs only where a particle has drifted out)
+__device__ __forceinline__ void flag_drift(int* flag, int any) {
+  if (__any_sync(kFullMask, any) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
 // Pair geometry shared by the loops: r_ij = x_i - x_j of neighbour j.
@@ -645,15 +699,19 @@ __device__ __forceinline__ T wall_acc_dot(const DevBuffers& B, int j, T rx, T ry
 // Every loop below is a body over the slots i, i + stride, ... < end of one
 // tank (the whole fluid for one tank; one tile of a batch), ending with the
 // block-wide reductions; k_* are the one-tank kernels around them.
+// A candidate j enters i's list when closer than 2h + b_i + b_j (b the drift
+// budgets of the rebuild; bud, normally B.bud, may be larger ones): while no
+// particle leaves its budget, a pair left out stays farther than 2h.
 template <int D, class T>
 __device__ __forceinline__ void build_lists_range(const Params& P, const DevBuffers& B,
                                                   const KC<T>& k, DevScalars* sc, int i, int end,
-                                                  int stride) {
+                                                  int stride, const float* __restrict__ bud) {
   using R = Rec<D, T>;
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
   const uint32_t* __restrict__ keys = B.binned;
-  const double rl = (2.0 * P.h + sc->skin) * (1.0 + 1e-6);
-  const T rl2 = (T)(rl * rl);
+  const T two_h = (T)(2.0 * P.h);
+  const T bw = (T)sc->wall_budget;
+  const T grow = (T)(1.0 + 1e-6);
   int overflow = 0;
   for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
@@ -661,10 +719,13 @@ __device__ __forceinline__ void build_lists_range(const Params& P, const DevBuff
     PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
                     R::pz(pi), k.cs};
     ListWriter L{B.nl, P.list_cap, i, 0, true};
+    const T ri = two_h + (T)bud[i];
     visit_neighbours<D>(P, B, ci, i, false, [&](int j, int dx, int dy, int dz, bool w) {
       T rx, ry, rz;
       G.rel(j, dx, dy, dz, w, rx, ry, rz);
-      if (r2_of(rx, ry, rz) < rl2 && (w || j != i)) L.add((uint32_t)j | nl_code(dx, dy, dz, w));
+      const T rl = (ri + (w ? bw : (T)bud[j])) * grow;
+      if (r2_of(rx, ry, rz) < rl * rl && (w || j != i))
+        L.add((uint32_t)j | nl_code(dx, dy, dz, w));
     });
     B.nl_cnt[i] = (uint32_t)min(L.cnt, P.list_cap);
     if (L.cnt > P.list_cap) overflow = 1;
@@ -674,11 +735,12 @@ __device__ __forceinline__ void build_lists_range(const Params& P, const DevBuff
 
 template <int D, class T>
 __global__ void __launch_bounds__(256, kMinBlocks<T>) k_build_lists(Params P, DevBuffers B, KC<T> k,
-                                                                    int gated) {
+                                                                    int gated,
+                                                                    const float* bud = nullptr) {
   DevScalars* sc = B.sc;
   if (!P.use_list || (gated && !sc->new_adv)) return;
   build_lists_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
-                          gridDim.x * blockDim.x);
+                          gridDim.x * blockDim.x, bud ? bud : B.bud);
 }
 
 // Density from the kernel sum: the free-surface clamp rho0 max(sigma/sigma0, 1),
@@ -712,7 +774,7 @@ __device__ __forceinline__ void density_summation_range(const Params& P, const D
                                                         const KC<T>& k, DevScalars* sc, int i,
                                                         int end, int stride) {
   using R = Rec<D, T>;
-  const bool use_list = list_ok(P, sc, 0.0);
+  const bool use_list = list_ok(P, sc, sc->drift_bad_p, sc->t_reb);
   double* rho_live = sc->par ? B.rho[1] : B.rho[0];
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
   typename R::SV* recS = (typename R::SV*)B.recS[0];
@@ -779,7 +841,7 @@ __device__ __forceinline__ void density_summation_fx_range(const Params& P, cons
                                                            int stride) {
   using R = Rec<D, float>;
   using FV = typename FxRec<D>::V;
-  const bool use_list = list_ok(P, sc, 0.0);
+  const bool use_list = list_ok(P, sc, sc->drift_bad_p, sc->t_reb);
   double* rho_live = sc->par ? B.rho[1] : B.rho[0];
   const FV* __restrict__ rec = (const FV*)B.recI;
   const FV* __restrict__ wrec = (const FV*)B.wallI;
@@ -836,7 +898,7 @@ __device__ __forceinline__ void transport_range(const Params& P, const DevBuffer
                                                 int stride,
                                      const ShiftTable* tab) {
   using R = Rec<D, T>;
-  const bool use_list = list_ok(P, sc, 0.0);
+  const bool use_list = list_ok(P, sc, sc->drift_bad_p, sc->t_reb);
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
   const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
   const uint32_t* __restrict__ keys = B.binned;
@@ -902,6 +964,7 @@ __device__ __forceinline__ void transport_apply_range(const Params& P, const Dev
   const T* d1 = (const T*)B.aprior[1];
   const T* d2 = (const T*)B.aprior[2];
   double m = 0.0;
+  int drift = 0;
   for (; i < end; i += stride) {
     const double sx = (double)d0[i], sy = (double)d1[i], sz = D == 3 ? (double)d2[i] : 0.0;
     const double x = S.x0[i] + sx, y = S.x1[i] + sy, z = D == 3 ? S.x2[i] + sz : 0.0;
@@ -910,12 +973,15 @@ __device__ __forceinline__ void transport_apply_range(const Params& P, const Dev
     if (D == 3) S.x2[i] = z;
     T ox, oy, oz;
     Local<T>::enc(P, B.ctab, decode(keys[i], P), x, y, z, ox, oy, oz);
+    drift |= drifted<D, T>(B, i, ox, oy, oz);
     typename R::PV p = recP[i];
     R::set_pos(p, ox, oy, oz);
     recP[i] = p;
     const double s2 = sx * sx + sy * sy + sz * sz;
     m = s2 > m ? s2 : m;
   }
+  // shifted positions, read by the viscous loop: outside a budget -> no lists
+  flag_drift(&sc->drift_bad_p, drift);
   m = sqrt(warp_max(m));
   __shared__ double wm[32];
   __syncthreads();
@@ -945,7 +1011,7 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
                                               DevScalars* sc, int i, int end, int stride,
                                      const ShiftTable* tab) {
   using R = Rec<D, T>;
-  const bool use_list = list_ok(P, sc, 0.0);
+  const bool use_list = list_ok(P, sc, sc->drift_bad_p, sc->t_reb);
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
   const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
   const uint32_t* __restrict__ keys = B.binned;
@@ -1012,7 +1078,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_viscous(Params P, DevBuf
 // First half of the acoustic step; writes records of buffer 0.
 template <int D, class T>
 __device__ __forceinline__ void half1_range(const Params& P, const DevBuffers& B,
-                                            const DevScalars* sc, int i, int end, int stride) {
+                                            DevScalars* sc, int i, int end, int stride) {
   using R = Rec<D, T>;
   const int par = sc->par;
   const double dt = sc->dt_ac;
@@ -1021,6 +1087,7 @@ __device__ __forceinline__ void half1_range(const Params& P, const DevBuffers& B
   typename R::PV* recP = (typename R::PV*)B.recP[0];
   typename R::SV* recS = (typename R::SV*)B.recS[0];
   const Live<T> S = live<T>(B, par);
+  int drift = 0;
   for (; i < end; i += stride) {
     double rho = S.rho[i] + hdt * (double)S.drho[i];
     double p = P.c0sq * (rho - P.rho0);
@@ -1036,7 +1103,10 @@ __device__ __forceinline__ void half1_range(const Params& P, const DevBuffers& B
     Local<T>::enc(P, B.ctab, decode(keys[i], P), x, y, z, ox, oy, oz);
     recP[i] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, (T)p);
     recS[i] = R::makeS((T)vx, (T)vy, (T)vz, (T)rho, (T)p);
+    drift |= drifted<D, T>(B, i, ox, oy, oz);
   }
+  // positions the pressure loop reads: outside a budget -> no lists for it
+  flag_drift(&sc->drift_bad_p, drift);
 }
 
 template <int D, class T>
@@ -1067,11 +1137,8 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
   const int par = sc->par;
   const double dt = sc->dt_ac;
   const double hdt = 0.5 * dt;
-  // translating walls have moved by at most wall_vmax times the time since
-  // their binning; a wall pair needs the sum of both drifts below the skin,
-  // which 2 max(fluid, wall) bounds
   const bool use_list =
-      list_ok(P, sc, fmax(sc->disp_p, P.wall_vmax * (sc->t0 + hdt - sc->t_reb)));
+      list_ok(P, sc, sc->drift_bad_p, sc->t0 + hdt);
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
   const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
   typename R::PV* outP = (typename R::PV*)B.recP[1];
@@ -1082,7 +1149,7 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
   const T* ap2 = (const T*)B.aprior[2];
   const Live<T> S = live<T>(B, par);
   double vmax2 = 0.0;
-  int bad = 0;
+  int bad = 0, drift = 0;
   for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
     const typename R::PV pi = recP[i];
@@ -1165,12 +1232,15 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
     Local<T>::enc(P, B.ctab, ci, x, y, z, ox, oy, oz);
     outP[i] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p_i);
     outS[i] = R::makeS((T)vx, (T)vy, (T)vz, rho_i, p_i);
+    drift |= drifted<D, T>(B, i, ox, oy, oz);
   }
   vmax2 = warp_max(vmax2);
   __shared__ double wm[32];
   __syncthreads();  // the previous body call of this block has read wm
   if (threadIdx.x % 32 == 0) wm[threadIdx.x / 32] = vmax2;
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&sc->flags, kFlagNonFinite);
+  // positions the density relaxation reads: outside a budget -> no lists for it
+  flag_drift(&sc->drift_bad_r, drift);
   if (threadIdx.x == 0) {
     for (int q = 1; q < (int)(blockDim.x / 32); ++q) vmax2 = fmax(vmax2, wm[q]);
     if (!(vmax2 <= 1e300)) vmax2 = 1e300;
@@ -1196,11 +1266,8 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
   using R = Rec<D, T>;
   const int par = sc->par;
   const double hdt = 0.5 * sc->dt_ac;
-  // positions after the second half-drift: bound grows by dt/2 * top speed after the kick
-  const double disp2 =
-      sc->disp_p + hdt * sqrt(__longlong_as_double((long long)sc->vmax2_next));
   const bool use_list =
-      list_ok(P, sc, fmax(disp2, P.wall_vmax * (sc->t0 + 2.0 * hdt - sc->t_reb)));
+      list_ok(P, sc, sc->drift_bad_r, sc->t0 + 2.0 * hdt);
   const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[1];
   const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[1];
   const uint32_t* __restrict__ keys = B.binned;
@@ -1565,21 +1632,40 @@ void enqueue_advection_t(const StageArgs& a, cudaStream_t s) {
   enqueue_advection_loops<D, T>(a, s, 0, nullptr);
 }
 
-// Lists for a restored state: built from the positions as they stand with
-// the stored skin.  Every pair that comes within 2h before the next rebuild
-// is in them while the stored displacement bound holds (it counts the drift
-// since the rebuild, which covers the drift since now), and a list's sums
-// depend only on the pairs within 2h, visited in candidate order: the same
-// sums as the lists of the rebuild.
+// Lists for a restored state: built from the positions as they stand, with
+// budgets b_k + d_k, d_k the drift since the rebuild so far.  A pair left out
+// is farther than 2h + b_i + d_i + b_j + d_j now; a particle moves at most
+// d_k + b_k from here before it leaves its budget, so the pair stays farther
+// than 2h while the stored budgets hold -- the condition the loops check.
+// A list's sums depend only on the pairs within 2h, visited in candidate
+// order: the same sums as the lists of the rebuild.
+template <int D, class T>
+__global__ void k_restore_budgets(Params P, DevBuffers B, float* grown) {
+  const Live<T> S = live<T>(B, B.sc->par);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    T ox, oy, oz;
+    Local<T>::enc(P, B.ctab, decode(B.binned[i], P), S.x0[i], S.x1[i],
+                  D == 3 ? S.x2[i] : 0.0, ox, oy, oz);
+    const double dx = (double)ox - (double)((const T*)B.xreb[0])[i];
+    const double dy = (double)oy - (double)((const T*)B.xreb[1])[i];
+    const double dz = D == 3 ? (double)oz - (double)((const T*)B.xreb[2])[i] : 0.0;
+    // b + d with a margin for the record frame's rounding, rounded up
+    grown[i] = __double2float_ru(1.001 * ((double)B.bud[i] + sqrt(dx * dx + dy * dy + dz * dz)));
+  }
+}
+
 template <int D, class T>
 void enqueue_restore_lists_t(const StageArgs& a, cudaStream_t s) {
   const Params& P = a.P;
   const LaunchCfg& L = a.L;
   if (!P.use_list || P.n <= 0) return;
-  k_encode_records<D, T><<<grid_for(P.n, L.block_stream, L.blocks_stream), L.block_stream, 0,
-                           s>>>(P, a.B);
+  const int gs = grid_for(P.n, L.block_stream, L.blocks_stream);
+  k_encode_records<D, T><<<gs, L.block_stream, 0, s>>>(P, a.B);
+  // budgets b + (drift so far) in the summation scratch
+  float* grown = (float*)a.B.sigma;
+  k_restore_budgets<D, T><<<gs, L.block_stream, 0, s>>>(P, a.B, grown);
   k_build_lists<D, T><<<grid_for(P.n, L.block_loop, L.blocks_loop), L.block_loop, 0, s>>>(
-      P, a.B, make_kc<T>(P), 0);
+      P, a.B, make_kc<T>(P), 0, grown);
 }
 
 template <int D, class T>

@@ -615,7 +615,7 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
 // setup it belongs to.
 namespace {
 constexpr char kCkptMagic[8] = {'S', 'P', 'H', 'C', 'K', 'P', 'T', '1'};
-constexpr int32_t kCkptVersion = 3;
+constexpr int32_t kCkptVersion = 4;
 
 struct CkptHeader {
   char magic[8];

@@ -115,15 +115,9 @@ struct DevScalars {
   int par;      // live state copy
   int flags;    // sticky error bits
   // neighbour-list bookkeeping (see the list section of sph_stages.cuh)
-  double skin;     // list radius is 2h + skin for the current advection step
-  double disp;     // bound on any particle's displacement since the rebuild, at step start
-  double disp_p;   // the same bound after this step's first half-drift
-  double dt_prev;  // length of the previous acoustic step
-  int list_bad;    // a list overflowed its capacity in this advection step
+  double skin;   // twice the largest drift budget of the current advection step
+  int list_bad;  // a list overflowed its capacity in this advection step
   int pad_;
-  // bit pattern of the largest transport-velocity shift of this advection step
-  // (part of every particle's displacement since the rebuild)
-  unsigned long long shift_bits;
   double t0;     // start time of the current acoustic step
   double t_reb;  // time of the last rebuild (translating walls were binned then)
   // neighbour-list validity since the rebuild: some particle has left its

@@ -332,14 +332,11 @@ __global__ void k_cell_offsets(const uint32_t* __restrict__ keys, int n, uint32_
 
 // ---------------------------------------------------------------------------
 // Dual-criteria schedule, one thread.  vmax2_cur holds max |v|^2 of the
-// current velocities.
-// Also keeps the neighbour-list displacement bound: every half-drift moves a
-// particle by at most dt/2 times the largest speed of the velocities it uses
-// (vmax2_cur holds the maximum after the last kick).
+// current velocities.  At an advection step it also sizes the skin (the cap
+// of the particles' drift budgets) and clears the lists' validity flags.
 __device__ __forceinline__ void control_one(const Params& P, DevScalars* sc) {
   double vmax = sqrt(__longlong_as_double((long long)sc->vmax2_cur));
   int adv = (!sc->started || sc->tau >= sc->dt_ad) ? 1 : 0;
-  double disp = sc->started ? sc->disp_p + 0.5 * sc->dt_prev * vmax : 0.0;
   double dt = 0.6 * P.h / (P.c0 + vmax);
   if (adv) {
     sc->dt_ad = 0.25 * P.h / (P.U_ref > vmax ? P.U_ref : vmax);
@@ -349,22 +346,19 @@ __device__ __forceinline__ void control_one(const Params& P, DevScalars* sc) {
     // skin for this advection step: twice the distance covered at the current
     // top speed (plus what gravity can add; at least the speed of a
     // translating wall) over the step and one overshooting acoustic step, with
-    // margin; the loops check the bound and fall back to direct search if it
-    // is ever exceeded
+    // margin; no particle's drift budget exceeds half of it
     const double gmag = sqrt(P.g[0] * P.g[0] + P.g[1] * P.g[1] + P.g[2] * P.g[2]);
     const double span = sc->dt_ad + 1.5 * dt;
     const double vs = vmax > P.wall_vmax ? vmax : P.wall_vmax;
     double skin = 2.5 * (vs + gmag * span) * span + 0.02 * P.h;
     sc->skin = skin < P.skin_max ? skin : P.skin_max;
     sc->list_bad = 0;
-    sc->shift_bits = 0ull;
     sc->t_reb = sc->t;
     // per-particle drift budgets are set by the reorder from each particle's
     // speed; walls all get the translating walls' one
     sc->drift_bad_p = 0;
     sc->drift_bad_r = 0;
     sc->wall_budget = 1.25 * P.wall_vmax * span;
-    disp = 0.0;
   }
   sc->new_adv = adv;
   sc->dt_ac = dt;
@@ -373,9 +367,6 @@ __device__ __forceinline__ void control_one(const Params& P, DevScalars* sc) {
   sc->t += dt;
   sc->n_ac += 1;
   sc->vmax2_next = 0ull;
-  sc->disp = disp;
-  sc->disp_p = disp + 0.5 * dt * vmax;
-  sc->dt_prev = dt;
 }
 
 // use_cond: the step runs as a CUDA graph whose rebuild stages sit in a

@@ -951,7 +951,8 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_transport(Params P, DevB
 }
 
 // Apply the shifts: positions (FP64 state) and the position records of
-// buffer 0; the largest shift joins the displacement bound of the lists.
+// buffer 0; a particle shifted out of its drift budget clears the lists for
+// the viscous loop and the rest of the advection step.
 template <int D, class T>
 __device__ __forceinline__ void transport_apply_range(const Params& P, const DevBuffers& B,
                                                       DevScalars* sc, int i, int end,
@@ -963,7 +964,6 @@ __device__ __forceinline__ void transport_apply_range(const Params& P, const Dev
   const T* d0 = (const T*)B.aprior[0];
   const T* d1 = (const T*)B.aprior[1];
   const T* d2 = (const T*)B.aprior[2];
-  double m = 0.0;
   int drift = 0;
   for (; i < end; i += stride) {
     const double sx = (double)d0[i], sy = (double)d1[i], sz = D == 3 ? (double)d2[i] : 0.0;
@@ -977,20 +977,9 @@ __device__ __forceinline__ void transport_apply_range(const Params& P, const Dev
     typename R::PV p = recP[i];
     R::set_pos(p, ox, oy, oz);
     recP[i] = p;
-    const double s2 = sx * sx + sy * sy + sz * sz;
-    m = s2 > m ? s2 : m;
   }
   // shifted positions, read by the viscous loop: outside a budget -> no lists
   flag_drift(&sc->drift_bad_p, drift);
-  m = sqrt(warp_max(m));
-  __shared__ double wm[32];
-  __syncthreads();
-  if (threadIdx.x % 32 == 0) wm[threadIdx.x / 32] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int q = 1; q < (int)(blockDim.x / 32); ++q) m = fmax(m, wm[q]);
-    atomicMax(&sc->shift_bits, (unsigned long long)__double_as_longlong(m));
-  }
 }
 
 template <int D, class T>

@@ -143,9 +143,21 @@ __host__ KC<T> make_kc(const Params& P) {
 }
 
 // pair-type helpers
-__device__ __forceinline__ float inv_sqrt_t(float a) { return rsqrtf(a); }
+// The float forms are the PTX approximations with subnormals flushed: the
+// loops never meet a subnormal distance or density, and for normal operands
+// they give the same values as rsqrtf / __fdividef without the subnormal
+// range handling around them.
+__device__ __forceinline__ float inv_sqrt_t(float a) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
 __device__ __forceinline__ double inv_sqrt_t(double a) { return 1.0 / sqrt(a); }
-__device__ __forceinline__ float div_t(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float div_t(float a, float b) {
+  float r;
+  asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
 __device__ __forceinline__ double div_t(double a, double b) { return a / b; }
 
 // r^2 of the pair: FP64 uses an uncontracted sum (bit-identical acceptance with

@@ -162,7 +162,7 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
  *     density relaxation and the viscous force, which takes v_i - v_R =
  *     2 (v_i - v_w) for a wall neighbour; the wall pressure extrapolation is
  *     unchanged (no wall acceleration).  rho must be NULL.
- * n may be 0 and must be below 2^25.  Fails with SPH_E_INVALID on a NULL pos
+ * n may be 0 and must be below 2^26.  Fails with SPH_E_INVALID on a NULL pos
  * with n > 0, on too many particles, on a wall density or on a non-finite
  * wall velocity. */
 int sph_set_particles(sph_ctx* ctx, int kind, size_t n, const double* pos, const double* vel,
@@ -264,8 +264,8 @@ int sph_debug_neighbour_stats(sph_ctx* ctx, uint32_t* cnt_fluid, uint32_t* cnt_w
                               uint64_t* hash);
 
 /* Length of every fluid particle's neighbour list (storage order, n entries)
- * as built at the last rebuild: the candidates closer than 2h + skin.  All 0
- * when lists are off. */
+ * as built at the last rebuild: the fluid and wall candidates closer than 2h
+ * plus both particles' drift budgets.  All 0 when lists are off. */
 int sph_debug_list_lengths(sph_ctx* ctx, uint32_t* lengths);
 
 /* Stages of one acoustic step, in launch order (sph_profile_stages). */
@@ -429,7 +429,7 @@ int sph_create_batch(int n_tanks, const sph_tank* tanks, int precision,
  * sum(counts) * dim doubles, tank 0's particles first (vel, rho as
  * sph_set_particles: NULL = zero velocity / the tank's rho0; walls may take
  * prescribed sliding velocities, no density).  The total of each kind must
- * stay below 2^25. */
+ * stay below 2^26. */
 int sph_batch_set_particles(sph_batch* b, int kind, const size_t* counts, const double* pos,
                             const double* vel, const double* rho);
 

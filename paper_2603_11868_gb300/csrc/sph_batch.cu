@@ -495,10 +495,10 @@ int sph_batch_set_particles(sph_batch* b, int kind, const size_t* counts, const 
   if (!counts) return set_err(b, SPH_E_INVALID, "counts is NULL");
   size_t total = 0;
   for (int t = 0; t < b->T; ++t) {
-    if (counts[t] >= (1ull << 25)) return set_err(b, SPH_E_INVALID, "tank count too large");
+    if (counts[t] >= (1ull << 26)) return set_err(b, SPH_E_INVALID, "tank count too large");
     total += counts[t];
   }
-  if (total >= (1ull << 25)) return set_err(b, SPH_E_INVALID, "at most 2^25 - 1 particles per kind");
+  if (total >= (1ull << 26)) return set_err(b, SPH_E_INVALID, "at most 2^26 - 1 particles per kind");
   if (total > 0 && !pos) return set_err(b, SPH_E_INVALID, "pos is NULL");
   if (kind != SPH_FLUID && kind != SPH_WALL)
     return set_err(b, SPH_E_INVALID, "unknown particle kind");

@@ -467,7 +467,7 @@ int sph_set_particles(sph_ctx* c, int kind, size_t n, const double* pos, const d
   TraceRange trace_("sph_set_particles");
   if (!c) return SPH_E_INVALID;
   if (n > 0 && !pos) return set_err(c, SPH_E_INVALID, "pos is NULL");
-  if (n >= (1ull << 25)) return set_err(c, SPH_E_INVALID, "at most 2^25 - 1 particles per kind");
+  if (n >= (1ull << 26)) return set_err(c, SPH_E_INVALID, "at most 2^26 - 1 particles per kind");
   const int d = c->P.dim;
   if (kind == SPH_FLUID) {
     int rc = enter(c);
@@ -1101,6 +1101,9 @@ int sph_debug_list_lengths(sph_ctx* c, uint32_t* lengths) {
     CK(cudaMemcpyAsync(lengths, c->B.nl_cnt, n * 4, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (!c->P.use_list) memset(lengths, 0, n * 4);
+  // a count word packs the fluid run (bits 0..15) and the wall run (16..31)
+  for (size_t k = 0; k < n && c->P.use_list; ++k)
+    lengths[k] = (lengths[k] & 0xFFFFu) + (lengths[k] >> 16);
   rc = leave(c);
   if (rc) return rc;
   return sync_status(c);

@@ -496,8 +496,8 @@ __global__ void k_reorder(Params P, DevBuffers B, int gated) {
 // (about 475 in 3D) for about 81 accepted neighbours, and the pair arithmetic
 // then runs with few lanes of a warp active.  Right after each rebuild every
 // particle i records the candidates j closer than 2h + b_i + b_j, in
-// candidate order (cells dz, dy, dx; fluid then wall particles of each
-// cell); the other loops of the advection step walk that list instead of the
+// candidate order (fluid particles by cells dz, dy, dx, then wall particles
+// in the same cell order); the other loops of the advection step walk that list instead of the
 // cells.  b_k is particle k's drift budget, set by the reorder from its own
 // speed (walls: the translating walls' speed bound, 0 at rest).
 //
@@ -514,31 +514,42 @@ __global__ void k_reorder(Params P, DevBuffers B, int gated) {
 // the particle's own speed rather than the fastest particle's, so the lists
 // carry few more entries than the pairs within 2h.
 //
-// Entry: neighbour index in bits 0..24, dx+1 / dy+1 / dz+1 in bits 25..30,
-// wall flag in bit 31 (particle and wall counts below 2^25).  Entry k of
-// particle i lives at ((i / 32) cap + k) 32 + i % 32, so a warp's k-th entries
-// are one coalesced 128-byte line.
-constexpr uint32_t kIdxMask = (1u << 25) - 1u;
+// Entry: neighbour index in bits 0..25 and (dx + 1) | (dy + 1) << 2 |
+// (dz + 1) << 4 in bits 26..31 (particle and wall counts below 2^26).  A list
+// holds the fluid neighbours first and the wall neighbours after them, so a
+// loop walks two runs of one kind each instead of testing a flag per entry;
+// nl_cnt packs the two run lengths (fluid in bits 0..15, wall in bits 16..31).
+// Entry k of particle i lives at ((i / 32) cap + k) 32 + i % 32, so a warp's
+// k-th entries are one coalesced 128-byte line.
+constexpr int kIdxBits = 26;
+constexpr uint32_t kIdxMask = (1u << kIdxBits) - 1u;
 
-__device__ __forceinline__ uint32_t nl_code(int dx, int dy, int dz, bool w) {
-  return ((uint32_t)(dx + 1) << 25) | ((uint32_t)(dy + 1) << 27) | ((uint32_t)(dz + 1) << 29) |
-         (w ? 0x80000000u : 0u);
+__device__ __forceinline__ uint32_t nl_code(int dx, int dy, int dz) {
+  return (uint32_t)((dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4)) << kIdxBits;
 }
 __device__ __forceinline__ size_t nl_slot(int i, int k, int cap) {
   return ((size_t)(i >> 5) * (size_t)cap + (size_t)k) * 32u + (size_t)(i & 31);
 }
 
+// Appends the entries of one particle in visiting order (every fluid
+// candidate before any wall candidate); counts past the capacity are kept so
+// the caller can flag the overflow.
 struct ListWriter {
   uint32_t* nl;
-  int cap, i, cnt;
-  bool on;
-  __device__ __forceinline__ void add(uint32_t entry) {
-    if (on && cnt < cap) nl[nl_slot(i, cnt, cap)] = entry;
-    ++cnt;
+  int cap, i, nf, nw;
+  __device__ __forceinline__ void add(uint32_t entry, bool w) {
+    const int k = nf + nw;
+    if (k < cap) nl[nl_slot(i, k, cap)] = entry;
+    if (w) ++nw; else ++nf;
+  }
+  __device__ __forceinline__ bool overflowed() const { return nf + nw > cap; }
+  __device__ __forceinline__ uint32_t packed() const {
+    const int f = min(nf, cap);
+    return (uint32_t)f | ((uint32_t)min(nw, cap - f) << 16);
   }
 };
 
-// The cell offsets of a list entry as floats: bits 25..30 of an entry hold
+// The cell offsets of a list entry as floats: bits 26..31 of an entry hold
 // (dx + 1) | (dy + 1) << 2 | (dz + 1) << 4, so the float loops read
 // (dx, dy, dz) from this 64-entry table in shared memory (one load) instead
 // of decoding and converting three fields.  Every block fills it once.
@@ -552,10 +563,37 @@ __device__ __forceinline__ void fill_shift_table(ShiftTable& t) {
   __syncthreads();
 }
 
+// One run of list entries [k0, k1) of one kind; entries are prefetched two
+// ahead, so the list streams from DRAM while the previous pairs are computed.
+template <bool kTab, bool kWall, class V>
+__device__ __forceinline__ void walk_list(const Params& P, const DevBuffers& B,
+                                          const uint32_t* __restrict__ e, int k0, int k1, V& v,
+                                          const ShiftTable* tab) {
+  uint32_t x0 = k0 < k1 ? __ldcs(e + (size_t)k0 * 32u) : 0u;
+  uint32_t x1 = k0 + 1 < k1 ? __ldcs(e + (size_t)(k0 + 1) * 32u) : 0u;
+  for (int k = k0; k < k1; ++k) {
+    const uint32_t x = x0;
+    x0 = x1;
+    x1 = k + 2 < k1 ? __ldcs(e + (size_t)(k + 2) * 32u) : 0u;
+    const int j = (int)(x & kIdxMask);
+    if (!SPH_DBG_IN(B, j, kWall ? P.woff : P.foff, kWall ? P.woff + P.nw : P.foff + P.n))
+      continue;
+    if constexpr (kTab) {
+      const float4 d = tab->d[x >> kIdxBits];
+      v(j, d.x, d.y, d.z, kWall);
+    } else {
+      const uint32_t c = x >> kIdxBits;
+      v(j, (int)(c & 3u) - 1, (int)((c >> 2) & 3u) - 1, (int)(c >> 4) - 1, kWall);
+    }
+  }
+}
+
 // Visit the candidates of target i either through its list or through the
-// 3^D cells; v(j, dx, dy, dz, wall) does the test and the arithmetic.  With
-// kTab the list path passes the offsets as floats from `tab` (the same
-// values; direct search passes ints).
+// 3^D cells: every fluid candidate (cells dz, dy, dx; ascending index), then
+// every wall candidate in the same cell order.  v(j, dx, dy, dz, wall) does
+// the test and the arithmetic; the wall argument is a constant at each call
+// site.  With kTab the list path passes the offsets as floats from `tab`
+// (the same values; direct search passes ints).
 template <int D, bool kTab = false, class V>
 __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffers& B, Cell ci,
                                                  int i, bool use_list, V&& v,
@@ -564,43 +602,30 @@ __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffe
       !SPH_DBG_IN(B, ci.z, 0, D == 3 ? P.nz : 1))
     return;
   if (use_list) {
-    const int cnt = (int)B.nl_cnt[i];
+    const uint32_t c = B.nl_cnt[i];
+    const int nf = (int)(c & 0xFFFFu);
+    const int nt = nf + (int)(c >> 16);
     const uint32_t* __restrict__ e = B.nl + nl_slot(i, 0, P.list_cap);
-    // entries are prefetched two ahead: the list streams from DRAM while the
-    // previous pairs are computed
-    uint32_t x0 = cnt > 0 ? __ldcs(e) : 0u;
-    uint32_t x1 = cnt > 1 ? __ldcs(e + 32) : 0u;
-    for (int k = 0; k < cnt; ++k) {
-      const uint32_t x = x0;
-      x0 = x1;
-      x1 = k + 2 < cnt ? __ldcs(e + (size_t)(k + 2) * 32u) : 0u;
-      const int j = (int)(x & kIdxMask);
-      const bool w = (x >> 31) != 0u;
-      if (!SPH_DBG_IN(B, j, w ? P.woff : P.foff, w ? P.woff + P.nw : P.foff + P.n)) continue;
-      if constexpr (kTab) {
-        const float4 d = tab->d[(x >> 25) & 63u];
-        v(j, d.x, d.y, d.z, w);
-      } else {
-        v(j, (int)((x >> 25) & 3u) - 1, (int)((x >> 27) & 3u) - 1, (int)((x >> 29) & 3u) - 1,
-          w);
-      }
-    }
+    walk_list<kTab, false>(P, B, e, 0, nf, v, tab);
+    walk_list<kTab, true>(P, B, e, nf, nt, v, tab);
     return;
   }
   const uint32_t* __restrict__ cb = B.cell_begin + P.cell_base;
-  const uint32_t* __restrict__ wcb = B.wall_cb + P.cell_base;
   for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
     const uint32_t e = cb[c + 1];
     if (SPH_DBG_IN(B, cb[c], P.foff, P.foff + P.n + 1) &&
         SPH_DBG_IN(B, e, cb[c], P.foff + P.n + 1))
       for (uint32_t j = cb[c]; j < e; ++j) v((int)j, dx, dy, dz, false);
-    if (P.nw > 0) {
+  });
+  if (P.nw > 0) {
+    const uint32_t* __restrict__ wcb = B.wall_cb + P.cell_base;
+    for_each_cell<D>(P, ci, [&](uint32_t c, int dx, int dy, int dz) {
       const uint32_t we = wcb[c + 1];
       if (SPH_DBG_IN(B, wcb[c], P.woff, P.woff + P.nw + 1) &&
           SPH_DBG_IN(B, we, wcb[c], P.woff + P.nw + 1))
         for (uint32_t w = wcb[c]; w < we; ++w) v((int)w, dx, dy, dz, true);
-    }
-  });
+    });
+  }
 }
 
 // x - d * cs in the record frame (x itself for absolute positions); d is the
@@ -730,17 +755,17 @@ __device__ __forceinline__ void build_lists_range(const Params& P, const DevBuff
     const typename R::PV pi = recP[i];
     PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
                     R::pz(pi), k.cs};
-    ListWriter L{B.nl, P.list_cap, i, 0, true};
+    ListWriter L{B.nl, P.list_cap, i, 0, 0};
     const T ri = two_h + (T)bud[i];
     visit_neighbours<D>(P, B, ci, i, false, [&](int j, int dx, int dy, int dz, bool w) {
       T rx, ry, rz;
       G.rel(j, dx, dy, dz, w, rx, ry, rz);
       const T rl = (ri + (w ? bw : (T)bud[j])) * grow;
       if (r2_of(rx, ry, rz) < rl * rl && (w || j != i))
-        L.add((uint32_t)j | nl_code(dx, dy, dz, w));
+        L.add((uint32_t)j | nl_code(dx, dy, dz), w);
     });
-    B.nl_cnt[i] = (uint32_t)min(L.cnt, P.list_cap);
-    if (L.cnt > P.list_cap) overflow = 1;
+    B.nl_cnt[i] = L.packed();
+    if (L.overflowed()) overflow = 1;
   }
   if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(&sc->list_bad, 1);
 }
@@ -768,13 +793,14 @@ __device__ __forceinline__ double reinit_density(const Params& P, double sigma, 
 }
 
 // Whether candidate (dx, dy, dz, wall, j) comes after particle i itself in the
-// candidate order of direct search (cells dz, dy, dx; fluid before wall
-// particles of a cell; ascending index).
+// candidate order of direct search (every fluid candidate by cells dz, dy, dx
+// and ascending index, then every wall candidate).
 __device__ __forceinline__ bool after_self(int dx, int dy, int dz, bool w, int j, int i) {
+  if (w) return true;
   if (dz != 0) return dz > 0;
   if (dy != 0) return dy > 0;
   if (dx != 0) return dx > 0;
-  return w || j > i;
+  return j > i;
 }
 
 // Density summation (FP64 path): reads records P of buffer 0; writes rho

@@ -196,6 +196,11 @@ def make_workload(name: str, dp: float | None = None):
         return cases.dam_break_3d(dp=0.01, seed=1), "3D dam break, dp=0.01"
     if name == "dam_break_2d":
         return cases.dam_break_2d(), "2D dam break, dp=0.025"
+    if name == "dam_break_obstacle_3d_56m":
+        # the largest particle count of the paper's runs (dam break with an
+        # obstacle, 56 M particles): 56.3 M fluid + 8.4 M wall particles
+        return (cases.dam_break_obstacle_3d(dp=0.0022),
+                "3D dam break with obstacle, dp=0.0022")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -559,7 +564,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="dam_break_3d_5m",
                     choices=["dam_break_3d_5m", "dam_break_3d_80k", "dam_break_2d",
-                             "nsearch_16m", "batched_256"])
+                             "dam_break_obstacle_3d_56m", "nsearch_16m", "batched_256"])
     ap.add_argument("--dp", type=float, default=None,
                     help="3D dam break at this spacing instead of the named workload")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")

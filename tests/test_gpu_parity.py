@@ -362,3 +362,30 @@ def test_full_size_sampled_density(sph, O):
     assert np.isfinite(f["pos"]).all() and np.isfinite(f["vel"]).all()
     assert f["rho"].min() > 0.98 * case.rho0 and f["rho"].max() < 1.05 * case.rho0
     s.close()
+
+
+def test_beyond_2_25_fluid_particles_sampled(sph, O):
+    """A 3D dam break with more fluid particles than 2^25 (34.3 M at dp =
+    0.00133): list entries of the particles stored at slots >= 2^25 carry
+    neighbour indices with bit 25 set.  The first step's kernel sums and
+    accelerations of 600 / 300 of those particles against the oracle, with
+    the lists in use there."""
+    case = cases.dam_break_3d(dp=0.00133, seed=3)
+    assert case.n > 2 ** 25
+    s = sph.Solver(case, precision="mixed")
+    s.set_option(sph.SPH_OPT_RECORD_DIAGNOSTICS, 1)
+    s.step(1)
+    high = s.neighbour_state()["ids"][2 ** 25:]
+    assert s.list_lengths()[2 ** 25:].min() > 0
+    sig, acc = s.field("sigma"), s.field("acc")
+    # 2^26 particles of a kind are refused before the positions are read
+    tiny = np.zeros(3)
+    rc = sph.load().sph_set_particles(s.ctx, sph.SPH_FLUID, 2 ** 26, tiny.ctypes.data, None, None)
+    assert rc == sph.SPH_E_INVALID
+    s.close()
+    ids = np.random.default_rng(1).choice(high, 600, replace=False).astype(np.uint32)
+    o = O.Oracle.from_case(case)
+    assert rel(sig[ids], o.sample_sigma(ids)) <= 1e-6
+    err = _acc_err(acc[ids[:300]], o.sample_first_step_acc(ids[:300]), 9.81)
+    print(f"\nmixed first-step acceleration error beyond 2^25 (300 samples): {err:.2e}")
+    assert err <= 1e-5

@@ -35,7 +35,9 @@ struct Rec;
 
 template <class T>
 struct Rec<3, T> {
-  using PV = typename Vec4<T>::type;  // (x, y, z, p)
+  // (x, y, z, p); in buffer 0 from the reorder to the next first half-step
+  // the w slot holds the drift budget instead, which the list build reads
+  using PV = typename Vec4<T>::type;
   using SV = typename Vec4<T>::type;  // (vx, vy, vz, rho)
   __device__ static PV makeP(T x, T y, T z, T vx, T vy, T vz, T p) {
     PV r;
@@ -442,8 +444,9 @@ __device__ __forceinline__ void reorder_slot(const Params& P, const DevBuffers& 
     Dd.drho[k] = S.drho[j];
     Dd.id[k] = S.id[j];
     const float fvx = (float)vx, fvy = (float)vy, fvz = (float)vz;
-    B.bud[k] = drift_budget(sqrtf(fvx * fvx + fvy * fvy + fvz * fvz), ba.gspan, ba.span,
-                            ba.floor_, ba.bmax);
+    const float bk = drift_budget(sqrtf(fvx * fvx + fvy * fvy + fvz * fvz), ba.gspan, ba.span,
+                                  ba.floor_, ba.bmax);
+    B.bud[k] = bk;
     T ox, oy, oz;
     const Cell ck = decode(key, P);
     Local<T>::enc(P, B.ctab, ck, x, y, z, ox, oy, oz);
@@ -451,7 +454,7 @@ __device__ __forceinline__ void reorder_slot(const Params& P, const DevBuffers& 
     ((T*)B.xreb[1])[k] = oy;
     if (D == 3) ((T*)B.xreb[2])[k] = oz;
     T p = (T)(P.c0sq * (rho - P.rho0));
-    recP[k] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p);
+    recP[k] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, D == 3 ? (T)bk : p);
     recS[k] = R::makeS((T)vx, (T)vy, (T)vz, (T)rho, p);
     if constexpr (Local<T>::kLocal)
       ((typename FxRec<D>::V*)B.recI)[k] = fx_encode<D>(P, ck, x, y, z);
@@ -727,6 +730,18 @@ __device__ __forceinline__ T wall_acc_dot(const DevBuffers& B, int j, T rx, T ry
   return aw.x * rx + aw.y * ry + WR::z(aw) * rz;
 }
 
+// Drift budget of fluid slot j for the list build.  In 3D it is the w slot of
+// j's buffer-0 position record (written there by the reorder, or by the list
+// restore with its grown budgets, in place of the pressure that the next
+// first half-step writes), so a candidate costs one gather; 2D position
+// records have no free slot and read the budget array.
+template <int D, class T>
+__device__ __forceinline__ T build_budget(const typename Rec<D, T>::PV& pj,
+                                          const float* __restrict__ bud, int j) {
+  if constexpr (D == 3) return pj.w;
+  else return (T)bud[j];
+}
+
 // List build (right after the rebuild, positions = binned positions): one
 // direct search per particle that records the candidates closer than
 // 2h + skin.  The membership test runs in the pair type on the loop records;
@@ -737,8 +752,9 @@ __device__ __forceinline__ T wall_acc_dot(const DevBuffers& B, int j, T rx, T ry
 // tank (the whole fluid for one tank; one tile of a batch), ending with the
 // block-wide reductions; k_* are the one-tank kernels around them.
 // A candidate j enters i's list when closer than 2h + b_i + b_j (b the drift
-// budgets of the rebuild; bud, normally B.bud, may be larger ones): while no
-// particle leaves its budget, a pair left out stays farther than 2h.
+// budgets of the rebuild, or larger ones when lists are restored: 3D reads
+// them from the position records, 2D from bud): while no particle leaves its
+// budget, a pair left out stays farther than 2h.
 template <int D, class T>
 __device__ __forceinline__ void build_lists_range(const Params& P, const DevBuffers& B,
                                                   const KC<T>& k, DevScalars* sc, int i, int end,
@@ -756,11 +772,18 @@ __device__ __forceinline__ void build_lists_range(const Params& P, const DevBuff
     PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
                     R::pz(pi), k.cs};
     ListWriter L{B.nl, P.list_cap, i, 0, 0};
-    const T ri = two_h + (T)bud[i];
+    const T ri = two_h + build_budget<D, T>(pi, bud, i);
     visit_neighbours<D>(P, B, ci, i, false, [&](int j, int dx, int dy, int dz, bool w) {
-      T rx, ry, rz;
-      G.rel(j, dx, dy, dz, w, rx, ry, rz);
-      const T rl = (ri + (w ? bw : (T)bud[j])) * grow;
+      T rx, ry, rz, bj;
+      if (w) {
+        G.rel_wall(G.wall[j], dx, dy, dz, rx, ry, rz);
+        bj = bw;
+      } else {
+        const typename R::PV pj = recP[j];
+        G.rel_rec(pj, dx, dy, dz, rx, ry, rz);
+        bj = build_budget<D, T>(pj, bud, j);
+      }
+      const T rl = (ri + bj) * grow;
       if (r2_of(rx, ry, rz) < rl * rl && (w || j != i))
         L.add((uint32_t)j | nl_code(dx, dy, dz), w);
     });
@@ -1678,6 +1701,7 @@ __global__ void k_restore_budgets(Params P, DevBuffers B, float* grown) {
     const double dz = D == 3 ? (double)oz - (double)((const T*)B.xreb[2])[i] : 0.0;
     // b + d with a margin for the record frame's rounding, rounded up
     grown[i] = __double2float_ru(1.001 * ((double)B.bud[i] + sqrt(dx * dx + dy * dy + dz * dz)));
+    if constexpr (D == 3) ((typename Rec<D, T>::PV*)B.recP[0])[i].w = (T)grown[i];
   }
 }
 

@@ -114,12 +114,12 @@ enum sph_option {
   SPH_OPT_BLOCK = 3,              /* threads per block of the neighbour loops: 64..256,
                                      multiple of 32 (default 128)                      */
   SPH_OPT_RADIX_BITS = 4,         /* digit width of the radix sort: 4..11 (default 8)  */
-  SPH_OPT_NEIGHBOUR_LIST = 5,     /* 0/1 (default 1): loops after the density summation
-                                     walk per-particle neighbour lists (candidates within
-                                     2h plus both particles' drift budgets at the
-                                     rebuild) instead of the cells while every particle
-                                     stays within its budget; results are identical
-                                     either way                                         */
+  SPH_OPT_NEIGHBOUR_LIST = 5,     /* 0/1 (default 1): the neighbour loops of an
+                                     advection step walk per-particle neighbour lists
+                                     built at its rebuild (candidates within 2h plus
+                                     both particles' drift budgets) instead of the
+                                     cells while every particle stays within its
+                                     budget; results are identical either way          */
   SPH_OPT_DENSITY_RIEMANN = 6,    /* 1 (default): the density relaxation uses the
                                      Riemann interface velocity U*; 0: the plain average
                                      (U_L + U_R)/2, the dissipation-free variant, which is

@@ -566,9 +566,24 @@ __device__ __forceinline__ void fill_shift_table(ShiftTable& t) {
   __syncthreads();
 }
 
+// The float c - 1 of a shift code c in {0, 1, 2} without a table or a
+// conversion: its two high bytes (0xBF80, 0x0000, 0x3F80) picked out of two
+// constants by one byte permute.
+__device__ __forceinline__ float shift_f(uint32_t c) {
+  return __uint_as_float(__byte_perm(0x003F00BFu, 0x00800080u, c * 0x1100u + 0x0433u));
+}
+
+// Which float loops take the shifts from the entry bits (shift_f) rather than
+// the shared-memory table: measured per loop on the 5.1 M 3D dam break and the
+// 256 2D tanks (same values either way), the 3D density relaxation and viscous
+// loops ran faster without the table's shared-memory reads, the pressure loop
+// and every 2D loop slower.
+template <int D>
+constexpr bool kShiftBitsRV = D == 3;
+
 // One run of list entries [k0, k1) of one kind; entries are prefetched two
 // ahead, so the list streams from DRAM while the previous pairs are computed.
-template <bool kTab, bool kWall, class V>
+template <bool kTab, bool kBits, bool kWall, class V>
 __device__ __forceinline__ void walk_list(const Params& P, const DevBuffers& B,
                                           const uint32_t* __restrict__ e, int k0, int k1, V& v,
                                           const ShiftTable* tab) {
@@ -581,7 +596,10 @@ __device__ __forceinline__ void walk_list(const Params& P, const DevBuffers& B,
     const int j = (int)(x & kIdxMask);
     if (!SPH_DBG_IN(B, j, kWall ? P.woff : P.foff, kWall ? P.woff + P.nw : P.foff + P.n))
       continue;
-    if constexpr (kTab) {
+    if constexpr (kBits) {
+      const uint32_t c = x >> kIdxBits;
+      v(j, shift_f(c & 3u), shift_f((c >> 2) & 3u), shift_f(c >> 4), kWall);
+    } else if constexpr (kTab) {
       const float4 d = tab->d[x >> kIdxBits];
       v(j, d.x, d.y, d.z, kWall);
     } else {
@@ -595,9 +613,9 @@ __device__ __forceinline__ void walk_list(const Params& P, const DevBuffers& B,
 // 3^D cells: every fluid candidate (cells dz, dy, dx; ascending index), then
 // every wall candidate in the same cell order.  v(j, dx, dy, dz, wall) does
 // the test and the arithmetic; the wall argument is a constant at each call
-// site.  With kTab the list path passes the offsets as floats from `tab`
-// (the same values; direct search passes ints).
-template <int D, bool kTab = false, class V>
+// site.  With kTab the list path passes the offsets as floats from `tab`, with
+// kBits as floats from shift_f (the same values; direct search passes ints).
+template <int D, bool kTab = false, bool kBits = false, class V>
 __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffers& B, Cell ci,
                                                  int i, bool use_list, V&& v,
                                                  const ShiftTable* tab = nullptr) {
@@ -609,8 +627,8 @@ __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffe
     const int nf = (int)(c & 0xFFFFu);
     const int nt = nf + (int)(c >> 16);
     const uint32_t* __restrict__ e = B.nl + nl_slot(i, 0, P.list_cap);
-    walk_list<kTab, false>(P, B, e, 0, nf, v, tab);
-    walk_list<kTab, true>(P, B, e, nf, nt, v, tab);
+    walk_list<kTab, kBits, false>(P, B, e, 0, nf, v, tab);
+    walk_list<kTab, kBits, true>(P, B, e, nf, nt, v, tab);
     return;
   }
   const uint32_t* __restrict__ cb = B.cell_begin + P.cell_base;
@@ -1078,7 +1096,8 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
                     R::pz(pi), k.cs};
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     T ax = 0, ay = 0, az = 0;
-    visit_neighbours<D, Local<T>::kLocal>(
+    visit_neighbours<D, Local<T>::kLocal && !kShiftBitsRV<D>,
+                     Local<T>::kLocal && kShiftBitsRV<D>>(
         P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w) {
       T rx, ry, rz;
       G.rel(j, dx, dy, dz, w, rx, ry, rz);
@@ -1120,7 +1139,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_viscous(Params P, DevBuf
   DevScalars* sc = B.sc;
   if (gated && !sc->new_adv) return;
   __shared__ ShiftTable tab;
-  if constexpr (Local<T>::kLocal) fill_shift_table(tab);
+  if constexpr (Local<T>::kLocal && !kShiftBitsRV<D>) fill_shift_table(tab);
   viscous_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
                       gridDim.x * blockDim.x, &tab);
 }
@@ -1332,7 +1351,8 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     const T p_i = R::pres(pi, si), rho_i = R::rho(pi, si);
     T sum = 0;
-    visit_neighbours<D, Local<T>::kLocal>(
+    visit_neighbours<D, Local<T>::kLocal && !kShiftBitsRV<D>,
+                     Local<T>::kLocal && kShiftBitsRV<D>>(
         P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w) {
       T rx, ry, rz;
       typename R::PV pj;
@@ -1385,7 +1405,7 @@ template <int D, class T, bool kWallVel, bool kAccel = false>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) k_density_relax(Params P, DevBuffers B, KC<T> k) {
   DevScalars* sc = B.sc;
   __shared__ ShiftTable tab;
-  if constexpr (Local<T>::kLocal) fill_shift_table(tab);
+  if constexpr (Local<T>::kLocal && !kShiftBitsRV<D>) fill_shift_table(tab);
   if (blockIdx.x == 0 && threadIdx.x == 0) sc->vmax2_cur = sc->vmax2_next;
   density_relax_range<D, T, kWallVel, kAccel>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
                             gridDim.x * blockDim.x, &tab);

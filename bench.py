@@ -72,7 +72,7 @@ def source_fingerprint() -> str:
 # kernel sources it was taken on (profiles/k_pressure_dam_break_3d_643k_mixed.md);
 # a stale fingerprint reports traffic as null.
 NCU_TRAFFIC = {
-    ("pressure", "d8c3055e5991"): (283265280 + 10767872) / 643200,
+    ("pressure", "a8f1653eec8d"): (283244544 + 10778368) / 643200,
 }
 # neighbour-list bytes per list entry and launch of the stages that use the
 # lists: the loops read each entry once; the rebuild stage writes and then

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
 PIN_FILES = ["tests/test_oracle_kernel.py", "tests/test_oracle_neighbours.py",
              "tests/test_oracle_physics.py", "tests/test_oracle_variants.py",
-             "tests/test_oracle_walls.py"]
+             "tests/test_oracle_walls.py", "tests/test_oracle_sampling.py"]
 
 MUTATIONS = {
     "riemann_ustar_sign": ("*Ustar = 0.5 * (UL + UR) + (pL - pR)",
@@ -75,6 +75,15 @@ MUTATIONS = {
                        "const double coef = 0.2 * s->h * s->h;"),
     "transport_support": ("if (s->sigma[i] < 0.95 * s->sigma0) continue;",
                           "if (s->sigma[i] < 0.5 * s->sigma0) continue;"),
+    # the sampled first-step evaluations that check the full-size GPU runs
+    "sample_neighbour_not_marked": ("if (dist2(s->x[i], s->x[j]) < r2max) need[j] = 1;",
+                                    "if (dist2(s->x[i], s->x[j]) < r2max && j == i) need[j] = 1;"),
+    "sample_state_density": ("pressure_acc_of(s, slot[user_ids[q]], rho, p, a);",
+                             "pressure_acc_of(s, slot[user_ids[q]], s->rho, p, a);"),
+    "sample_density_before_clamp": ("rho[k] = density_of_sigma(s, sigma_of(s, k));",
+                                    "rho[k] = s->rho0 * sigma_of(s, k) / s->sigma0;"),
+    "sample_sigma_slot": ("for (long q = 0; q < m; ++q) sigma[q] = sigma_of(s, slot[user_ids[q]]);",
+                          "for (long q = 0; q < m; ++q) sigma[q] = sigma_of(s, user_ids[q]);"),
 }
 
 

@@ -22,6 +22,8 @@
 // with V_j = m / rho_j (walls: V_w = m / rho_w of the mirrored state).
 #pragma once
 
+#include <type_traits>
+
 #include "sph_internal.cuh"
 
 namespace sphgb {
@@ -121,6 +123,14 @@ struct KC {
   T r2max, inv_h, cW, cdW, m, c0, inv_c0, rho0, inv_c0sq, eps, two_mu, cs, half;
   T g[3];
   T riemann;  // 1: Riemann U* in the density relaxation; 0: the average of the states
+  // Relaxation loops.  With t = 1 - r / (2h) the kernel slope is
+  // W'(r) = cdW (r / h) t^3, so W'(r) e_ij = (cdW / h) t^3 r_ij needs no unit
+  // vector; the constant factors of each sum are applied once per particle.
+  T neg_inv_2h;  // -1 / (2h): t = 1 + r neg_inv_2h
+  T c0_half;     // c0 / 2
+  T kP;          // -m cdW / h: a_i = kP / rho_i sum_j 2P*_ij t^3 r_ij / rho_j
+  T kD;          // m cdW / h: drho_i = kD rho_i sum_j B_ij t^3 / rho_j
+  T kappa2;      // 2 riemann / c0
 };
 
 template <class T>
@@ -141,6 +151,12 @@ __host__ KC<T> make_kc(const Params& P) {
   k.half = (T)0.5;
   k.riemann = (P.variant & kVariantNoRiemann) ? (T)0 : (T)1;
   for (int d = 0; d < 3; ++d) k.g[d] = (T)P.g[d];
+  const double cdW_h = -5.0 * P.walpha / (P.h * P.h);
+  k.neg_inv_2h = (T)(-0.5 / P.h);
+  k.c0_half = (T)(0.5 * P.c0);
+  k.kP = (T)(-P.m * cdW_h);
+  k.kD = (T)(P.m * cdW_h);
+  k.kappa2 = (P.variant & kVariantNoRiemann) ? (T)0 : (T)(2.0 / P.c0);
   return k;
 }
 
@@ -581,6 +597,14 @@ __device__ __forceinline__ float shift_f(uint32_t c) {
 template <int D>
 constexpr bool kShiftBitsRV = D == 3;
 
+// The last argument of a visitor call says whether the candidate may be the
+// target itself: direct search meets i in its own cell, a list never holds it
+// (a compile-time constant, so the list walks carry no self test).
+using MaySelf = std::true_type;
+using NotSelf = std::false_type;
+constexpr NotSelf kNotSelf{};
+constexpr MaySelf kMaySelf{};
+
 // One run of list entries [k0, k1) of one kind; entries are prefetched two
 // ahead, so the list streams from DRAM while the previous pairs are computed.
 // The walk is unrolled by two, which lets the compiler issue the next pair's
@@ -602,13 +626,13 @@ __device__ __forceinline__ void walk_list(const Params& P, const DevBuffers& B,
       continue;
     if constexpr (kBits) {
       const uint32_t c = x >> kIdxBits;
-      v(j, shift_f(c & 3u), shift_f((c >> 2) & 3u), shift_f(c >> 4), kWall);
+      v(j, shift_f(c & 3u), shift_f((c >> 2) & 3u), shift_f(c >> 4), kWall, kNotSelf);
     } else if constexpr (kTab) {
       const float4 d = tab->d[x >> kIdxBits];
-      v(j, d.x, d.y, d.z, kWall);
+      v(j, d.x, d.y, d.z, kWall, kNotSelf);
     } else {
       const uint32_t c = x >> kIdxBits;
-      v(j, (int)(c & 3u) - 1, (int)((c >> 2) & 3u) - 1, (int)(c >> 4) - 1, kWall);
+      v(j, (int)(c & 3u) - 1, (int)((c >> 2) & 3u) - 1, (int)(c >> 4) - 1, kWall, kNotSelf);
     }
   }
 }
@@ -640,7 +664,7 @@ __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffe
     const uint32_t e = cb[c + 1];
     if (SPH_DBG_IN(B, cb[c], P.foff, P.foff + P.n + 1) &&
         SPH_DBG_IN(B, e, cb[c], P.foff + P.n + 1))
-      for (uint32_t j = cb[c]; j < e; ++j) v((int)j, dx, dy, dz, false);
+      for (uint32_t j = cb[c]; j < e; ++j) v((int)j, dx, dy, dz, false, kMaySelf);
   });
   if (P.nw > 0) {
     const uint32_t* __restrict__ wcb = B.wall_cb + P.cell_base;
@@ -648,7 +672,7 @@ __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffe
       const uint32_t we = wcb[c + 1];
       if (SPH_DBG_IN(B, wcb[c], P.woff, P.woff + P.nw + 1) &&
           SPH_DBG_IN(B, we, wcb[c], P.woff + P.nw + 1))
-        for (uint32_t w = wcb[c]; w < we; ++w) v((int)w, dx, dy, dz, true);
+        for (uint32_t w = wcb[c]; w < we; ++w) v((int)w, dx, dy, dz, true, kNotSelf);
     });
   }
 }
@@ -795,7 +819,7 @@ __device__ __forceinline__ void build_lists_range(const Params& P, const DevBuff
                     R::pz(pi), k.cs};
     ListWriter L{B.nl, P.list_cap, i, 0, 0};
     const T ri = two_h + build_budget<D, T>(pi, bud, i);
-    visit_neighbours<D>(P, B, ci, i, false, [&](int j, int dx, int dy, int dz, bool w) {
+    visit_neighbours<D>(P, B, ci, i, false, [&](int j, int dx, int dy, int dz, bool w, auto) {
       T rx, ry, rz, bj;
       if (w) {
         G.rel_wall(G.wall[j], dx, dy, dz, rx, ry, rz);
@@ -869,7 +893,7 @@ __device__ __forceinline__ void density_summation_range(const Params& P, const D
                     R::pz(pi), k.cs};
     T sig = T(0);
     bool self_done = false;
-    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
+    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w, auto) {
       if (use_list && !self_done && after_self(dx, dy, dz, w, j, i)) {
         sig += wendland(k, T(0));  // self, in its direct-search position
         self_done = true;
@@ -936,7 +960,7 @@ __device__ __forceinline__ void density_summation_fx_range(const Params& P, cons
     const FV oi = rec[i];
     dfl sig = {0.0f, 0.0f};
     bool self_done = false;
-    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w) {
+    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w, auto) {
       if (use_list && !self_done && after_self(dx, dy, dz, w, j, i)) {
         sig = df_add(sig, dfl{1.0f, 0.0f});  // self: shape(0) = 1
         self_done = true;
@@ -998,11 +1022,11 @@ __device__ __forceinline__ void transport_range(const Params& P, const DevBuffer
       PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
                       R::pz(pi), k.cs};
       visit_neighbours<D, Local<T>::kLocal>(
-          P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w) {
+          P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w, auto may_self) {
         T rx, ry, rz;
         G.rel(j, dx, dy, dz, w, rx, ry, rz);
         const T r2 = r2_of(rx, ry, rz);
-        if (!(r2 < k.r2max) || (!w && j == i)) return;
+        if (!(r2 < k.r2max) || (may_self && !w && j == i)) return;
         const T r = sqrt(r2);
         T f;
         if (w) {
@@ -1102,11 +1126,11 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
     T ax = 0, ay = 0, az = 0;
     visit_neighbours<D, Local<T>::kLocal && !kShiftBitsRV<D>,
                      Local<T>::kLocal && kShiftBitsRV<D>>(
-        P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w) {
+        P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w, auto may_self) {
       T rx, ry, rz;
       G.rel(j, dx, dy, dz, w, rx, ry, rz);
       const T r2 = r2_of(rx, ry, rz);
-      if (!(r2 < k.r2max) || (!w && j == i)) return;
+      if (!(r2 < k.r2max) || (may_self && !w && j == i)) return;
       const T r = sqrt(r2);
       if (w) {
         const T coef = wallV2 * wendland_dr(k, r) / (r + k.eps);
@@ -1233,7 +1257,7 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
     const T p_i = R::pres(pi, si), rho_i = R::rho(pi, si);
     T ax = 0, ay = 0, az = 0;
     visit_neighbours<D, Local<T>::kLocal>(
-        P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w) {
+        P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w, auto may_self) {
       T rx, ry, rz;
       typename R::PV pj;
       typename R::SV sj;
@@ -1245,37 +1269,43 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
         G.rel_rec(pj, dx, dy, dz, rx, ry, rz);
       }
       const T r2 = r2_of(rx, ry, rz);
-      if (!(r2 < k.r2max) || (!w && j == i)) return;
+      if (!(r2 < k.r2max) || (may_self && !w && j == i)) return;
       const T inv_r = inv_sqrt_t(r2);
-      const T r = r2 * inv_r;
-      const T ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
-      const T UL = -(vxi * ex + vyi * ey + vzi * ez);
-      T UR, p_j, rho_j;
+      // dvr = (v_i - v_R) . r_ij, so U_L - U_R = -dvr / r
+      T dvr, p_j, rho_j;
       if (w) {
-        // mirrored state: p_w = p_i + rho_i (x_w - x_i).(g - a_w), x_w - x_i = -r_vec
+        // mirrored state: p_w = p_i + rho_i (x_w - x_i).(g - a_w), x_w - x_i = -r_vec;
+        // v_R = 2 v_w - v_i, so v_i - v_R = 2 (v_i - v_w)
         T gdot = -(rx * k.g[0] + ry * k.g[1] + rz * k.g[2]);
         if constexpr (kAccel) gdot += wall_acc_dot<D, T>(B, j, rx, ry, rz);
         p_j = p_i + rho_i * gdot;
         rho_j = k.rho0 + p_j * k.inv_c0sq;
-        UR = -UL;
+        T d = vxi * rx + vyi * ry + vzi * rz;
         if constexpr (kWallVel)
-          if (P.variant & kVariantMovingWall) UR -= T(2) * wall_vel_dot<D, T>(B, j, ex, ey, ez);
+          if (P.variant & kVariantMovingWall) d -= wall_vel_dot<D, T>(B, j, rx, ry, rz);
+        dvr = T(2) * d;
       } else {
-        UR = -(R::vx(pj, sj) * ex + R::vy(pj, sj) * ey + R::vz(pj, sj) * ez);
+        dvr = (vxi - R::vx(pj, sj)) * rx + (vyi - R::vy(pj, sj)) * ry +
+              (vzi - R::vz(pj, sj)) * rz;
         p_j = R::pres(pj, sj);
         rho_j = R::rho(pj, sj);
       }
-      const T rbar = k.half * (rho_i + rho_j);
-      const T jump = UL - UR;
-      T beta = T(3) * (jump > T(0) ? jump : T(0)) * k.inv_c0;
-      beta = beta < T(1) ? beta : T(1);
-      const T Ps = k.half * (p_i + p_j) + k.half * beta * rbar * k.c0 * jump;
-      const T f = Ps * div_t(k.m, rho_j) * wendland_dr(k, r);
-      ax += f * ex;
-      ay += f * ey;
-      az += f * ez;
+      // [Z17] P* = (p_i + p_j)/2 + beta rbar c0 (U_L - U_R)/2 with
+      // beta = min(3 max(U_L - U_R, 0) / c0, 1) and rbar = (rho_i + rho_j)/2:
+      // for J = max(U_L - U_R, 0),  2 P* = p_i + p_j + (rho_i + rho_j) J min(3J/2, c0/2)
+      const T J0 = -dvr * inv_r;
+      const T J = J0 > T(0) ? J0 : T(0);
+      T lim = T(1.5) * J;
+      lim = lim < k.c0_half ? lim : k.c0_half;
+      const T Ps2 = (p_i + p_j) + (rho_i + rho_j) * (J * lim);
+      const T t = T(1) + (r2 * inv_r) * k.neg_inv_2h;
+      const T f = Ps2 * div_t(T(1), rho_j) * (t * t * t);
+      ax += f * rx;
+      ay += f * ry;
+      az += f * rz;
     }, tab);
-    const T s = div_t(T(-2), rho_i);
+    // -(2/rho_i) sum P* (m/rho_j) W' e_ij = (kP / rho_i) sum 2P* t^3 r_ij / rho_j
+    const T s = div_t(k.kP, rho_i);
     ax *= s;
     ay *= s;
     az *= s;
@@ -1357,7 +1387,7 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
     T sum = 0;
     visit_neighbours<D, Local<T>::kLocal && !kShiftBitsRV<D>,
                      Local<T>::kLocal && kShiftBitsRV<D>>(
-        P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w) {
+        P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w, auto may_self) {
       T rx, ry, rz;
       typename R::PV pj;
       typename R::SV sj;
@@ -1369,32 +1399,34 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
         G.rel_rec(pj, dx, dy, dz, rx, ry, rz);
       }
       const T r2 = r2_of(rx, ry, rz);
-      if (!(r2 < k.r2max) || (!w && j == i)) return;
-      const T inv_r = inv_sqrt_t(r2);
-      const T r = r2 * inv_r;
-      const T ex = rx * inv_r, ey = ry * inv_r, ez = rz * inv_r;
-      const T UL = -(vxi * ex + vyi * ey + vzi * ez);
+      if (!(r2 < k.r2max) || (may_self && !w && j == i)) return;
+      const T r = r2 * inv_sqrt_t(r2);
+      const T t = T(1) + r * k.neg_inv_2h;
+      // [Z17] U* = (U_L + U_R)/2 + riemann (p_i - p_j) / (2 rbar c0), so with
+      // W'(r) e_ij = (cdW/h) t^3 r_ij the pair term -2 rho_i V_j W' (U_L - U*)
+      // is kD rho_i t^3 B_ij / rho_j with
+      //   B_ij = (v_i - v_j).r_ij + kappa2 r (p_i - p_j) / (rho_i + rho_j);
+      // at a wall v_j is the mirrored v_R = 2 v_w - v_i, whose half-difference
+      // (v_i - v_R)/2 = v_i - v_w enters in full.
+      T Bij, rho_j;
       if (w) {
         T gdot = -(rx * k.g[0] + ry * k.g[1] + rz * k.g[2]);
         if constexpr (kAccel) gdot += wall_acc_dot<D, T>(B, j, rx, ry, rz);
         const T pw_ = p_i + rho_i * gdot;
-        const T rho_w = k.rho0 + pw_ * k.inv_c0sq;
-        const T rbar = k.half * (rho_i + rho_w);
-        // U_R = -U_L - 2 v_w.e, so (U_L + U_R)/2 = -v_w.e (0 at rest)
-        T Us = k.riemann * div_t(p_i - pw_, T(2) * rbar * k.c0);
+        rho_j = k.rho0 + pw_ * k.inv_c0sq;
+        T d = vxi * rx + vyi * ry + vzi * rz;
         if constexpr (kWallVel)
-          if (P.variant & kVariantMovingWall) Us -= wall_vel_dot<D, T>(B, j, ex, ey, ez);
-        sum += div_t(k.m, rho_w) * wendland_dr(k, r) * (UL - Us);
+          if (P.variant & kVariantMovingWall) d -= wall_vel_dot<D, T>(B, j, rx, ry, rz);
+        Bij = T(2) * d + k.kappa2 * r * div_t(p_i - pw_, rho_i + rho_j);
       } else {
-        const T UR = -(R::vx(pj, sj) * ex + R::vy(pj, sj) * ey + R::vz(pj, sj) * ez);
-        const T rho_j = R::rho(pj, sj);
-        const T rbar = k.half * (rho_i + rho_j);
-        const T Us =
-            k.half * (UL + UR) + k.riemann * div_t(p_i - R::pres(pj, sj), T(2) * rbar * k.c0);
-        sum += div_t(k.m, rho_j) * wendland_dr(k, r) * (UL - Us);
+        rho_j = R::rho(pj, sj);
+        const T dvr = (vxi - R::vx(pj, sj)) * rx + (vyi - R::vy(pj, sj)) * ry +
+                      (vzi - R::vz(pj, sj)) * rz;
+        Bij = dvr + k.kappa2 * r * div_t(p_i - R::pres(pj, sj), rho_i + rho_j);
       }
+      sum += div_t(T(1), rho_j) * (t * t * t) * Bij;
     }, tab);
-    const T dr = T(-2) * rho_i * sum;
+    const T dr = k.kD * rho_i * sum;
     S.drho[i] = dr;
     double rho = S.rho[i] + hdt * (double)dr;
     if (!(fabs(rho) <= 1e300)) bad = 1;

@@ -359,12 +359,15 @@ void sph_nsearch_destroy(sph_nsearch* ns);
  * edge cell without an error report.
  *
  * Scratch memory: a file-scope device array sized for
- * SPH_NOALLOC_MAX_PARTICLES particles (about 8.3 MB), held on every GPU that
- * loads the library until the process exits.  n above that limit fails with
+ * SPH_NOALLOC_MAX_PARTICLES particles -- 2 * 2^20 + 256 * 256 + 256 words of
+ * 4 bytes, 8 651 776 bytes (8.25 MiB) -- held on every GPU that loads the
+ * library until the process exits.  n above that limit fails with
  * SPH_E_INVALID before any work is queued.  The first call on a device looks
  * up the array's device address and sets kernel attributes for that device
  * (the device must be current); make that first call before any stream
- * capture.  No call allocates or frees memory.  All calls share the one
+ * capture.  Those per-device settings are kept for the life of the process:
+ * resetting the device (cudaDeviceReset) after the first call is not
+ * supported.  No call allocates or frees memory.  All calls share the one
  * array, which keeps the previous call's contents (what must start at zero is
  * cleared by each call), so calls whose work overlaps on the GPU -- on
  * different streams, or from different threads -- race and corrupt each

@@ -352,9 +352,8 @@ int sph_create_batch(int n_tanks, const sph_tank* tanks, int precision,
     long long ncell = 1;
     for (int a = 0; a < dim; ++a) {
       if (!(k.domain.hi[a] > k.domain.lo[a])) return SPH_E_INVALID;
-      nc[a] = (long long)std::ceil((k.domain.hi[a] - k.domain.lo[a]) / cs);
-      if (nc[a] < 1) nc[a] = 1;
-      if (nc[a] > (1ll << 30)) return SPH_E_INVALID;
+      nc[a] = grid_cells(k.domain.lo[a], k.domain.hi[a], cs);
+      if (nc[a] < 0) return SPH_E_INVALID;
       ncell *= nc[a];
       if (ncell > 0xfffffffll) return SPH_E_INVALID;
     }

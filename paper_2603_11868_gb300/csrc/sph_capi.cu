@@ -370,9 +370,8 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
   long long ncell = 1;
   for (int k = 0; k < dim; ++k) {
     if (!(domain->hi[k] > domain->lo[k])) return SPH_E_INVALID;
-    nc[k] = (long long)std::ceil((domain->hi[k] - domain->lo[k]) / cs);
-    if (nc[k] < 1) nc[k] = 1;
-    if (nc[k] > (1ll << 30)) return SPH_E_INVALID;
+    nc[k] = grid_cells(domain->lo[k], domain->hi[k], cs);
+    if (nc[k] < 0) return SPH_E_INVALID;
     ncell *= nc[k];
     if (ncell > 0xfffffffell) return SPH_E_INVALID;
   }

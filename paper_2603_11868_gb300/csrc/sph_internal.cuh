@@ -28,6 +28,20 @@
 #include <string>
 #include <vector>
 
+#include <cmath>
+
+namespace sphgb {
+// Cells along one axis of a grid of edge cs over [lo, hi): ceil((hi - lo) / cs),
+// at least 1.  The quotient is range-checked as a double before any cast:
+// -1 when it is not a finite count of at most 2^30 cells (a tiny or zero
+// edge, an infinite extent, NaN), which the callers turn into SPH_E_INVALID.
+inline long long grid_cells(double lo, double hi, double cs) {
+  const double r = std::ceil((hi - lo) / cs);
+  if (!(r <= (double)(1ll << 30))) return -1;
+  return r < 1.0 ? 1 : (long long)r;
+}
+}  // namespace sphgb
+
 namespace sphgb {
 
 constexpr int kMaxRadixBits = 11;

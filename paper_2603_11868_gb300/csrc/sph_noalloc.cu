@@ -71,9 +71,8 @@ extern "C" int sph_cell_sort_noalloc(const sph_domain* domain, double cell_size,
   int nc[3] = {1, 1, 1};
   for (int k = 0; k < dim; ++k) {
     if (!(domain->hi[k] > domain->lo[k])) return SPH_E_INVALID;
-    long long m = (long long)std::ceil((domain->hi[k] - domain->lo[k]) / cell_size);
-    if (m < 1) m = 1;
-    if (m > (1ll << 30)) return SPH_E_INVALID;
+    const long long m = grid_cells(domain->lo[k], domain->hi[k], cell_size);
+    if (m < 0) return SPH_E_INVALID;
     nc[k] = (int)m;
     ncell *= m;
     if (ncell > 0xfffffffell) return SPH_E_INVALID;

@@ -177,9 +177,17 @@ int sph_nsearch_create(const sph_domain* domain, double h, int pos_precision,
       delete s;
       return SPH_E_INVALID;
     }
-    long long m = (long long)std::ceil((domain->hi[k] - domain->lo[k]) / P.cs);
-    nc[k] = (int)(m < 1 ? 1 : m);
-    ncell *= nc[k];
+    const long long m = grid_cells(domain->lo[k], domain->hi[k], P.cs);
+    if (m < 0) {
+      delete s;
+      return SPH_E_INVALID;
+    }
+    nc[k] = (int)m;
+    ncell *= m;
+    if (ncell > 0xfffffffell) {
+      delete s;
+      return SPH_E_INVALID;
+    }
     P.lo[k] = domain->lo[k];
   }
   if (ncell > 0xfffffffell) {

@@ -119,3 +119,33 @@ def test_batches_refuse_translating_walls():
     from paper_2603_11868_gb300 import cases, sph
     with pytest.raises(ValueError):
         sph.Batch([cases.piston_channel_2d()])
+
+
+@pytest.mark.parametrize("case", ["tiny_edge", "infinite_extent", "nan_extent"])
+def test_grid_extent_checked_before_the_cast(lib, case):
+    """A cell count that is not a finite number of at most 2^30 cells per axis
+    (a tiny cell edge, an infinite or NaN extent) is refused with
+    SPH_E_INVALID by every entry point that builds a cell grid, before any
+    CUDA call: the quotient is range-checked as a double, never cast first."""
+    from paper_2603_11868_gb300 import sph
+    hi = {"tiny_edge": 1.0, "infinite_extent": float("inf"), "nan_extent": float("nan")}[case]
+    h = 1e-300 if case == "tiny_edge" else 0.013
+    dom = sph.sph_domain(3, (C.c_double * 3)(0, 0, 0), (C.c_double * 3)(hi, 1, 1))
+    mat = sph.sph_material(1.0, 10.0, 0.0, 1.0)
+    g = (C.c_double * 3)(0, 0, 0)
+    out = C.c_void_p()
+    assert lib.sph_create(C.byref(dom), 0.01, h, C.byref(mat), g, 1, None, None,
+                          C.byref(out)) == sph.SPH_E_INVALID
+    assert out.value is None
+    one = C.c_uint32()
+    assert lib.sph_cell_sort_noalloc(C.byref(dom), 2.0 * h, None, None, None, 0,
+                                     C.byref(one), C.byref(one), C.byref(one),
+                                     None) == sph.SPH_E_INVALID
+    ns = C.c_void_p()
+    assert lib.sph_nsearch_create(C.byref(dom), h, 1, None, None,
+                                  C.byref(ns)) == sph.SPH_E_INVALID
+    assert ns.value is None
+    tank = sph.sph_tank(dom, 0.01, h, mat, (C.c_double * 3)(0, 0, -1))
+    tanks = (sph.sph_tank * 1)(tank)
+    assert lib.sph_create_batch(1, tanks, 1, None, None, C.byref(out)) == sph.SPH_E_INVALID
+    assert out.value is None

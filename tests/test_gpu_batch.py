@@ -230,3 +230,61 @@ def test_kernels_per_step_and_invalid_arguments(sph):
     b.close()
     with pytest.raises(sph.SphError):
         sph.sph_create_batch([cases.batched_tank(300), cases.dam_break_3d(dp=0.05)])
+
+
+# --------------------------------------------------------------------------
+def _config4_tanks():
+    """The batched workload at its full size: 256 tanks, fluid counts
+    log-uniform in [1 000, 64 000] (seed 4), dp = 0.01, tank k seeded 100 + k."""
+    sizes = cases.batched_tank_sizes(256, seed=4)
+    return [cases.batched_tank(n, dp=0.01, seed=100 + k) for k, n in enumerate(sizes)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_size_batch_one_step_against_oracle(sph, O, precision):
+    """One step of the whole 256-tank batch; the 4 largest and the 4 smallest
+    tanks against the oracle run of that tank alone (every field within 1e-10
+    in FP64; accelerations within 1e-5 of max(|a_ref|, g) in mixed)."""
+    cs = _config4_tanks()
+    got, sc = _batch(sph, cs, precision, 1)
+    order = np.argsort([c.n for c in cs])
+    picked = list(order[:4]) + list(order[-4:])
+    assert cs[picked[0]].n < 1500 and cs[picked[-1]].n > 50000
+    worst = {}
+    for t in picked:
+        o = O.Oracle.from_case(cs[t])
+        o.step(1)
+        want = _oracle_fields(o, O)
+        if precision == "fp64":
+            for k in FIELDS:
+                assert rel(got[t][k], want[k]) <= 1e-10, (t, k, rel(got[t][k], want[k]))
+        else:
+            g = np.abs(cs[t].gravity).max()
+            for k in ("acc", "aprior"):
+                e = np.abs(got[t][k] - want[k]).max() / max(np.abs(want[k]).max(), g)
+                worst[k] = max(worst.get(k, 0.0), e)
+                assert e <= 1e-5, (t, k, e)
+        osc = o.scalars()
+        assert sc["dt_ac"][t] == osc["dt_ac"] and sc["dt_ad"][t] == osc["dt_ad"]
+    if worst:
+        print(f"\n256-tank batch, mixed, first step, 8 tanks: acc {worst['acc']:.2e}, "
+              f"aprior {worst['aprior']:.2e}")
+
+
+def test_full_size_batch_equals_one_tank_contexts(sph):
+    """20 steps of the 256-tank mixed batch against one-tank contexts of the
+    same 4 largest and 4 smallest tanks: bitwise equal (each tank on its own
+    schedule, the same kernels walking each tank's tiles)."""
+    cs = _config4_tanks()
+    got, sc = _batch(sph, cs, "mixed", 20)
+    order = np.argsort([c.n for c in cs])
+    for t in list(order[:4]) + list(order[-4:]):
+        s = sph.Solver(cs[t], precision="mixed")
+        s.set_option(sph.SPH_OPT_RECORD_DIAGNOSTICS, 1)
+        s.step(20)
+        one = s.fields(*FIELDS)
+        osc = s.scalars()
+        s.close()
+        for k in FIELDS:
+            assert np.array_equal(got[t][k], one[k]), (t, k)
+        assert sc["n_adv"][t] == osc["n_adv"] and sc["t"][t] == osc["t"]

@@ -86,3 +86,42 @@ def test_keys_on_and_next_to_cell_faces(fp32):
     # the set really straddles faces: cells on both sides of many faces
     assert len(np.unique(want["keys"])) > 100
     ns.close()
+
+
+@pytest.mark.parametrize("fp32", [True, False])
+def test_nsearch_full_size_2_24(fp32):
+    """The neighbour-search workload at its full size: 2^24 particles uniform
+    in the unit cube (seed 3), 57 neighbours within 2h on average.  Keys,
+    permutation and cell offsets bit-exact against the oracle's sort of the
+    same positions; the density pass's kernel sums on 5000 sampled particles
+    against the oracle's (1e-5 relative with float positions, 1e-12 with
+    double)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test needs a CUDA device")
+    from oracle import oracle as O
+    from paper_2603_11868_gb300 import build, sph
+    build.build()
+    case = cases.uniform_cube(n=1 << 24, seed=3, neighbours=57.0)
+    pos = case.fluid.astype(np.float32).astype(np.float64) if fp32 else case.fluid
+    dt = torch.float32 if fp32 else torch.float64
+    dev = [torch.tensor(np.ascontiguousarray(pos[:, k]), dtype=dt, device="cuda")
+           for k in range(3)]
+    ns = sph.NeighbourSearch(3, case.lo, case.hi, case.h, fp32=fp32)
+    ns.run(*dev, timed=False)
+    got = ns.results()
+    ns.close()
+    del dev
+    o = O.Oracle(3, case.lo, case.hi, case.dp, case.h, 1.0, 10.0, 0.0, 1.0, (0, 0, 0))
+    o.set_fluid(pos)
+    want = o.neighbour_state()
+    for k in ("keys", "perm", "cell_begin"):
+        assert np.array_equal(got[k], want[k]), k
+    ids = np.random.default_rng(7).choice(case.n, 5000, replace=False).astype(np.uint32)
+    slot = np.empty(case.n, np.int64)
+    slot[got["perm"]] = np.arange(case.n)
+    want_sig = o.sample_sigma(ids)
+    err = np.abs(got["sigma"][slot[ids]] - want_sig).max() / np.abs(want_sig).max()
+    print(f"\nneighbour search 2^24 ({'float' if fp32 else 'double'} positions): "
+          f"sampled sigma error {err:.2e}")
+    assert err <= (1e-5 if fp32 else 1e-12), err

@@ -49,6 +49,35 @@ def test_hydrostatic_column(sph, precision):
     assert err.max() <= 0.01 * c.rho0 * 1.0 * H, err.max() / (c.rho0 * H)
 
 
+@pytest.mark.parametrize("precision", ["mixed"])
+def test_hydrostatic_column_at_configured_h(sph, precision):
+    """The same column at the configurations' h = 1.3 dp, reported rather
+    than held to 1 %: the kernel's lattice gradient consistency there is
+    kappa = 0.974, which alone tilts the pressure slope by about 2.6 %, so the
+    column settles a few per cent off rho0 g (H - y).  The bound below only
+    guards that figure against regressions; the 1 % pin is the h = 1.5 dp
+    run above."""
+    c = cases.hydrostatic_2d(dp=0.05)
+    assert abs(c.h / c.dp - 1.3) < 1e-12
+    s = sph.Solver(c, precision=precision)
+    H, T = c.meta["H"], 20.0
+    ps, ys = [], []
+    while s.scalars()["t"] < T:
+        s.step(50)
+        if s.scalars()["t"] > 0.9 * T:
+            f = s.fields("p", "pos")
+            ps.append(f["p"])
+            ys.append(f["pos"][:, 1])
+    s.close()
+    p, y = np.mean(ps, 0), np.mean(ys, 0)
+    mask = y < H - 3 * c.dp
+    err = np.abs(p - c.rho0 * 1.0 * (H - y))[mask] / (c.rho0 * 1.0 * H)
+    bottom = np.abs(p[np.argmin(y)] / (c.rho0 * (H - y.min())) - 1.0)
+    print(f"\nhydrostatic column at h = 1.3 dp ({precision}): max |p - rho0 g (H - y)| = "
+          f"{err.max():.2%} of rho0 g H, bottom-particle pressure off by {bottom:.2%}")
+    assert err.max() <= 0.06
+
+
 def test_long_dam_break_stays_physical(sph):
     c = cases.dam_break_3d(dp=0.02, seed=3)
     s = sph.Solver(c, precision="mixed")

@@ -39,23 +39,40 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-steps/s, 5M-particle 3D dam break, FP32-mixed vs FP64 on one GB300"
 SUBSTEPS = 10
 
-# Algorithmic (compulsory) bytes per fluid particle and launch of each stage
-# in mixed precision, 3D: every per-particle array read / written once, each
-# neighbour record read once (neighbour re-reads are meant to hit L2), plus
-# the cell offsets and the static wall records.
-BYTES_PER_PARTICLE_MIXED_3D = {
-    "keys": 24 + 8,                     # read x; write key, index
-    "sort": 3 * (4 + 8 + 8),            # per pass: histogram read, scatter read + write
-    "reorder": 4 + 48 + 8 + 4 + 4 + 4 + 48 + 8 + 4 + 4 + 32,  # gather state, write state + records
-    "offsets": 4 + 2,                   # keys, offsets (about 0.5 cells per particle)
-    "density_sum": 4 + 16 + 8 + 32 + 4,  # key, own record, rho, record S r/w, offsets
-    "viscous": 4 + 32 + 12 + 4,         # key, records, a_prior, offsets
-    "half1": 24 + 24 + 8 + 4 + 4 + 24 + 8 + 32,  # x, v, rho, drho, key; x, rho, records
-    "pressure": 4 + 32 + 12 + 24 + 24 + 24 + 24 + 32 + 4,  # + records out, offsets
-    "density_relax": 4 + 32 + 8 + 4 + 8 + 4,  # key, records, rho r/w, drho, offsets
+# Algorithmic bytes per fluid particle and launch of each stage's method work
+# (mixed precision, 3D): every per-particle array of the method's state read
+# or written once (positions and density in double, velocity with its
+# compensation 24 B, pair data as one 32-byte float record per particle),
+# neighbour records read once (re-reads are meant to hit L2), about 6 B of
+# static wall records per fluid particle for each loop that reads walls, and
+# nothing for the neighbour lists, which are this design's choice rather than
+# the method's.  The first-half drift of the density stage is fused into the
+# pressure kernel, so its bytes (read x and v 36, write x 24 and the records
+# 32) move from the density relaxation to the pressure stage.
+ALG_BYTES_PER_PARTICLE_3D = {
+    "keys": 32,                 # read x 24; write key, index 8
+    "sort": 60,                 # 3 passes x (key + index read and write) + histograms
+    "reorder": 132,             # gather and write the state, write the records
+    "offsets": 6,               # sorted keys, about 0.5 cells per particle
+    "density_sum": 40,
+    "viscous": 44,
+    "half1": 112,               # read x 24, v 12, rho 8, drho 4; write x 24, rho 8, records 32
+    "pressure": 92 + 6 + 92,    # records 32, a_prior 12, v 24 r + 24 w; walls; fused drift
+    "density_relax": 52 + 6,    # records 32, drho 4, rho 8 r + 8 w; walls
     "control": 0,
 }
-WALL_RECORD_BYTES_3D = 16  # read once per neighbour loop
+# bytes per fluid particle this implementation's layout moves beyond the
+# method's (the drift check of the lists reads the rebuild offsets and the
+# budget, 16 B, wherever particles move; the key of the binned cell 4 B)
+# (the fused drift re-reads no velocity, 12 B less); half1 reads the velocity
+# state in double (12 B more)
+LAYOUT_EXTRA_BYTES = {"pressure": 4 + 16 - 12, "density_relax": 4, "half1": 12 + 4 + 16,
+                      "viscous": 4}
+WALL_RECORD_BYTES_3D = 16  # one float4 per wall particle, read once per loop
+# neighbour-list bytes per list entry and launch of the stages that use the
+# lists: the loops read each entry once; the rebuild writes and then reads
+# them once (list build + density summation)
+LIST_ENTRY_BYTES = {"pressure": 4, "density_relax": 4, "viscous": 4, "density_sum": 8}
 
 
 def source_fingerprint() -> str:
@@ -66,18 +83,17 @@ def source_fingerprint() -> str:
     return h.hexdigest()[:12]
 
 
-# dram read + write bytes of one launch of the named stage from an ncu capture,
-# per fluid particle (the capture ran a smaller case of the same geometry; its
-# traffic scales with the particle count), keyed by the fingerprint of the
-# kernel sources it was taken on (profiles/k_pressure_dam_break_3d_643k_mixed.md);
-# a stale fingerprint reports traffic as null.
-NCU_TRAFFIC = {
-    ("pressure", "a8f1653eec8d"): (283244544 + 10778368) / 643200,
+# Counters of one launch of the named stage from an ncu capture of a smaller
+# case of the same geometry and kernel (3D dam break at dp = 0.005, 643 200
+# fluid particles), keyed by the fingerprint of the kernel sources it was
+# taken on; a stale fingerprint reports them as null.  DRAM traffic is scaled
+# to the bench's launch by the fluid count (traffic per particle does not
+# depend on size at fixed h / dp), warp instructions by the list entries
+# (nearly all instructions are spent per entry).
+NCU_CAPTURES = {
+    ("pressure", "a8f1653eec8d"): {"fluid": 643200, "dram_bytes": 283244544 + 10778368,
+                                   "warp_inst": 146.6e6, "list_entries_per_particle": None},
 }
-# neighbour-list bytes per list entry and launch of the stages that use the
-# lists: the loops read each entry once; the rebuild stage writes and then
-# reads them once (list build + density summation)
-LIST_ENTRY_BYTES = {"pressure": 4, "density_relax": 4, "viscous": 4, "density_sum": 8}
 
 
 def measured_peaks() -> dict:
@@ -228,6 +244,44 @@ def cpu_oracle_sample(seconds_cap: float = 30.0) -> dict:
                       f"wall), {steps} acoustic steps incl. rebuilds, {el:.1f} s"}
 
 
+def roofline_of(stage: str, launch_s: float, n: int, nw: int, list_entries: float,
+                clocks: dict, mixed: bool) -> dict:
+    """HBM roofline of one stage's launch from its algorithmic bytes, with the
+    bytes this design adds (list entries, layout) and the ncu DRAM traffic as
+    overheads, and its issue-slot roofline: warp instructions per launch over
+    what the SMs can issue in the launch time (4 schedulers per SM, one warp
+    instruction each per cycle, at the SM clock sampled during the run)."""
+    import torch
+    peaks = measured_peaks()
+    alg = ALG_BYTES_PER_PARTICLE_3D.get(stage, 0) * n
+    list_bytes = LIST_ENTRY_BYTES.get(stage, 0) * list_entries
+    layout = LAYOUT_EXTRA_BYTES.get(stage, 0) * n
+    if stage in ("density_sum", "viscous", "pressure", "density_relax"):
+        layout += WALL_RECORD_BYTES_3D * nw - 6 * n   # the actual wall records vs the 6 B allowance
+    achieved = alg / launch_s / 1e9
+    cap = NCU_CAPTURES.get((stage, source_fingerprint())) if mixed else None
+    traffic = cap["dram_bytes"] / cap["fluid"] * n if cap else None
+    issue = None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = clocks.get("sm_mhz") if clocks else None
+    if cap and cap.get("warp_inst") and mhz:
+        e_cap = cap.get("list_entries_per_particle")
+        scale = (n * (list_entries / n) / (cap["fluid"] * e_cap)) if e_cap else n / cap["fluid"]
+        inst = cap["warp_inst"] * scale
+        slots = 4.0 * sms * mhz * 1e6 * launch_s
+        issue = {"warp_inst_per_launch": inst, "sm_count": sms, "sm_mhz": mhz,
+                 "issue_slots_per_launch": slots, "frac": inst / slots,
+                 "scaled_by": "list entries" if e_cap else "fluid particles"}
+    return {"bound": "hbm", "kernel": stage, "achieved": achieved, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "peak_source": peaks["source"], "bytes_per_launch": alg,
+            "avg_launch_ms": launch_s * 1e3,
+            "list_entries_per_particle": list_entries / n,
+            "overhead": {"list_entry_bytes": list_bytes, "layout_extra_bytes": layout,
+                         "traffic_over_algorithmic": (traffic / alg) if traffic else None},
+            "issue": issue}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -276,43 +330,53 @@ def time_steps(solver, steps, substeps, torch):
     return e0.elapsed_time(e1) / 1e3
 
 
-def run_nsearch(args):
+def measure_nsearch(steps: int, warmup: int) -> dict:
     """Neighbour-search microbenchmark: 2^24 particles uniform in the unit cube
     (seeded), h such that each particle has 57 others within 2h on average;
     cell keys + radix sort + reorder + cell offsets + one density pass, with
     float64 and float32 positions, timed per stage."""
     import torch
-    from paper_2603_11868_gb300 import build, cases, sph
+    from paper_2603_11868_gb300 import cases, sph
 
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    build.build()
-    sph.load()
     case = cases.uniform_cube(n=1 << 24, seed=3, neighbours=57.0)
-    res = {}
+    res = {"n": case.n, "h": case.h}
     for label, dt, fp32 in (("f64", torch.float64, False), ("f32", torch.float32, True)):
         dev = [torch.tensor(np.ascontiguousarray(case.fluid[:, k]), dtype=dt, device="cuda")
                for k in range(3)]
         ns = sph.NeighbourSearch(3, case.lo, case.hi, case.h, fp32=fp32)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             ns.run(*dev, timed=False)
         torch.cuda.synchronize()
         st = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(args.steps):
-            ns.run(*dev, timed=False)
-        e1.record(st)
-        e1.synchronize()
-        el = e0.elapsed_time(e1) / 1e3 / args.steps
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            e0.record(st)
+            for _ in range(steps):
+                ns.run(*dev, timed=False)
+            e1.record(st)
+            e1.synchronize()
+        el = e0.elapsed_time(e1) / 1e3 / steps
         stages = {k: 0.0 for k in ns.STAGES}
         for _ in range(3):
             for k, v in ns.run(*dev).items():
                 stages[k] += v / 3
         res[label] = {"particles_per_s": case.n / el, "ms_per_run": el * 1e3,
-                      "stage_ms": {k: round(v, 4) for k, v in stages.items()}}
+                      "stage_ms": {k: round(v, 4) for k, v in stages.items()},
+                      "clocks": clk.summary()}
         ns.close()
         del dev
+    return res
+
+
+def run_nsearch(args):
+    import torch
+    from paper_2603_11868_gb300 import build, sph
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    sph.load()
+    res = measure_nsearch(args.steps, args.warmup)
     if rank == 0:
         line = {"metric": "neighbour-search particles/s (keys + radix sort + reorder + offsets "
                           "+ density pass), 16M uniform",
@@ -321,10 +385,10 @@ def run_nsearch(args):
                 "ms_per_step": res["f32"]["ms_per_run"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 positions",
                 "data": "synthetic",
-                "config": {"workload": f"uniform cube, {case.n} particles, h={case.h:.6g}, "
+                "config": {"workload": f"uniform cube, {res['n']} particles, h={res['h']:.6g}, "
                                        f"{57} neighbours within 2h on average",
                            "l2": "inputs larger than L2 (no flush)"},
-                "f32": res["f32"], "f64": res["f64"]}
+                "f32": res["f32"], "f64": res["f64"], "clocks": res["f32"]["clocks"]}
         print(json.dumps(line), flush=True)
     return 0
 
@@ -337,9 +401,47 @@ def batched_cases(n_tanks: int = 256, dp: float = 0.01):
     return [cases.batched_tank(n, dp=dp, seed=100 + k) for k, n in enumerate(sizes)]
 
 
-def run_batched(args):
+def measure_batched(args, steps: int, warmup: int, dist=None, rank: int = 0, ws: int = 1,
+                    local: int = 0) -> dict:
     """Batched tanks: every tank advances one acoustic step (its own length)
     per graph launch; value = total fluid particles x acoustic steps / time."""
+    import torch
+    from paper_2603_11868_gb300 import sph
+
+    cs = batched_cases(args.tanks)
+    n_all = sum(c.n for c in cs)
+    if ws > 1:  # independent tanks: each rank advances its share, no collective
+        cs = [cs[t] for t in shard_tanks([c.n for c in cs], ws)[rank]]
+    b = sph.Batch(cs, precision=args.precision)
+    n, nw = b.n, b.nw
+    tuning = apply_tuning(b, args)
+    for _ in range(warmup):
+        b.step(args.substeps)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        el = time_steps(b, steps, args.substeps, torch)
+    sph.sph_batch_synchronize(b.b, 60.0)
+    value, el = replica_value(el, n * steps * args.substeps, dist, "cuda")
+    stages, rebuilds = b.profile(2 * args.substeps)
+    per_step = {k: v / (2 * args.substeps) for k, v in stages.items()}
+    kernels = sph.sph_batch_kernels_per_step(b.b)
+    sc = b.scalars()
+    b.close()
+    return {"value": value, "unit": "particle-steps/s", "ms_per_step": el / steps * 1e3,
+            "steps": steps, "warmup": warmup, "n_all": n_all, "tanks_rank0": len(cs),
+            "fluid_rank0": n, "wall_rank0": nw,
+            "acoustic_steps_per_bench_step": args.substeps,
+            "stage_ms_per_acoustic_step": {k: round(v, 4) for k, v in per_step.items()},
+            "advection_steps_begun_per_acoustic_step": rebuilds / (2 * args.substeps),
+            "gpu_launches": kernels * args.substeps * steps,
+            "kernels_per_acoustic_step": kernels,
+            "tank_time_spread": [float(np.min(sc["t"])), float(np.max(sc["t"]))],
+            "tuning": tuning, "clocks": clk.summary()}
+
+
+def run_batched(args):
     import torch
     from paper_2603_11868_gb300 import build, sph
 
@@ -351,49 +453,27 @@ def run_batched(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     sph.load()
-    cs = batched_cases(args.tanks)
-    n_all = sum(c.n for c in cs)
-    if ws > 1:  # independent tanks: each rank advances its share, no collective
-        cs = [cs[t] for t in shard_tanks([c.n for c in cs], ws)[rank]]
-    b = sph.Batch(cs, precision=args.precision)
-    n, nw = b.n, b.nw
-    tuning = apply_tuning(b, args)
-    for _ in range(args.warmup):
-        b.step(args.substeps)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    with ClockSampler(local) as clk:
-        el = time_steps(b, args.steps, args.substeps, torch)
-    sph.sph_batch_synchronize(b.b, 60.0)
-    value, el = replica_value(el, n * args.steps * args.substeps, dist, "cuda")
-    stages, rebuilds = b.profile(2 * args.substeps)
-    per_step = {k: v / (2 * args.substeps) for k, v in stages.items()}
-    kernels = sph.sph_batch_kernels_per_step(b.b)
-    sc = b.scalars()
-    b.close()
+    r = measure_batched(args, args.steps, args.warmup, dist, rank, ws, local)
     if rank == 0:
         line = {"metric": "particle-steps/s, 256 batched 2D dam-break tanks (1k-64k particles "
                           "each), FP32-mixed",
-                "value": value, "unit": "particle-steps/s", "n_gpus": ws,
+                "value": r["value"], "unit": "particle-steps/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+                "ms_per_step": r["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32 pair / f64 state" if args.precision == "mixed" else "f64",
                 "data": "synthetic",
-                "config": {"workload": f"{args.tanks} tanks, {n_all} fluid particles over {ws} rank(s) "
-                                       f"(rank 0: {len(cs)} tanks, {n} fluid + {nw} wall), "
+                "config": {"workload": f"{args.tanks} tanks, {r['n_all']} fluid particles over "
+                                       f"{ws} rank(s) (rank 0: {r['tanks_rank0']} tanks, "
+                                       f"{r['fluid_rank0']} fluid + {r['wall_rank0']} wall), "
                                        f"dp=0.01, {args.substeps} acoustic steps per bench step",
                            "parallelism": f"tanks sharded over {ws} rank(s)",
-                           "l2": "state larger than L2 (no flush)"},
-                "acoustic_steps_per_bench_step": args.substeps,
-                "stage_ms_per_acoustic_step": {k: round(v, 4) for k, v in per_step.items()},
-                "advection_steps_begun_per_acoustic_step": rebuilds / (2 * args.substeps),
-                "gpu_launches": kernels * args.substeps * args.steps,
-                "kernels_per_acoustic_step": kernels,
-                "tank_time_spread": [float(np.min(sc["t"])), float(np.max(sc["t"]))],
-                "tuning": tuning,
-                "clocks": clk.summary()}
+                           "l2": "state larger than L2 (no flush)"}}
+        line.update({k: r[k] for k in ("acoustic_steps_per_bench_step",
+                                       "stage_ms_per_acoustic_step",
+                                       "advection_steps_begun_per_acoustic_step", "gpu_launches",
+                                       "kernels_per_acoustic_step", "tank_time_spread", "tuning",
+                                       "clocks")})
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -448,17 +528,9 @@ def run_ours(args):
     rebuild_stages = ("keys", "sort", "reorder", "offsets", "density_sum", "viscous")
     launches = {k: (rebuilds if k in rebuild_stages else prof_steps) for k in ms}
     dom = max(ms, key=lambda k: ms[k])
-    peaks = measured_peaks()
-    fp = source_fingerprint()
     list_entries = float(solver.list_lengths().astype(np.float64).sum())
-    dom_bytes = BYTES_PER_PARTICLE_MIXED_3D.get(dom, 0) * n
-    if dom in ("density_sum", "viscous", "pressure", "density_relax"):
-        dom_bytes += WALL_RECORD_BYTES_3D * nw
-    dom_bytes += LIST_ENTRY_BYTES.get(dom, 0) * list_entries
-    avg_s = ms[dom] / 1e3 / max(1, launches[dom])
-    achieved = dom_bytes / avg_s / 1e9
-    per_particle = NCU_TRAFFIC.get((dom, fp))
-    traffic = per_particle * n if per_particle is not None and args.precision == "mixed" else None
+    roofline = roofline_of(dom, ms[dom] / 1e3 / max(1, launches[dom]), n, nw, list_entries,
+                           clocks, args.precision == "mixed")
 
     # FP64 path on the same workload for the speed-up (fewer steps)
     fp64 = None
@@ -510,10 +582,34 @@ def run_ours(args):
                "h2d_bytes_per_step": n * (2 * d + 1) * 8,
                "d2h_bytes_per_step": n * (2 * d + 1) * 8}
 
+    solver.close()
+    # the batched-tank and neighbour-search workloads, timed after the headline
+    # on one GPU (their own values, clocks and times; not part of `value`)
+    extras = {}
+    if ws == 1 and not args.quick and not args.no_extras:
+        torch.cuda.empty_cache()
+        b = measure_batched(args, steps=20, warmup=3, local=local)
+        extras["batched_256"] = {
+            "metric": "particle-steps/s, 256 batched 2D dam-break tanks (1k-64k particles "
+                      "each), FP32-mixed", "fluid_particles": b["n_all"],
+            **{k: b[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup",
+                                 "acoustic_steps_per_bench_step", "kernels_per_acoustic_step",
+                                 "gpu_launches", "tuning", "clocks")}}
+        torch.cuda.empty_cache()
+        ns = measure_nsearch(steps=5, warmup=3)
+        extras["nsearch_16m"] = {
+            "metric": "neighbour-search particles/s (keys + radix sort + reorder + offsets + "
+                      "density pass), 16M uniform, float positions",
+            "value": ns["f32"]["particles_per_s"], "unit": "particles/s",
+            "ms_per_step": ns["f32"]["ms_per_run"], "steps": 5, "warmup": 3,
+            "stage_ms": ns["f32"]["stage_ms"], "clocks": ns["f32"]["clocks"],
+            "f64": {"value": ns["f64"]["particles_per_s"], "ms_per_step": ns["f64"]["ms_per_run"],
+                    "stage_ms": ns["f64"]["stage_ms"]}}
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.quick and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample()
-    solver.close()
 
     if rank == 0:
         line = {
@@ -527,12 +623,7 @@ def run_ours(args):
                        "wall_particles": nw, "acoustic_steps_timed": acoustic,
                        "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{ws}"},
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved,
-                         "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                         "peak_source": peaks["source"],
-                         "bytes_per_launch": dom_bytes, "avg_launch_ms": avg_s * 1e3,
-                         "list_entries_per_particle": list_entries / n},
+            "roofline": roofline,
             "stage_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
             "rebuilds_per_step": rebuilds / prof_steps,
             "clocks": clocks,
@@ -548,8 +639,9 @@ def run_ours(args):
             "gpips": (value * mean_nb * 2 / 1e9) if mean_nb else None,
             # the same throughput counting wall particles too
             "fluid_and_wall_steps_per_s": value * (n + nw) / n,
-            "sim_time": sc["t"], "source_fingerprint": fp, "tuning": tuning,
+            "sim_time": sc["t"], "source_fingerprint": source_fingerprint(), "tuning": tuning,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -572,6 +664,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="main number only")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched-tank and neighbour-search lines nested in the default line")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch configuration")
     ap.add_argument("--tanks", type=int, default=256,

@@ -125,7 +125,7 @@ template <int D, class T>
 __global__ void __launch_bounds__(256, kMinBlocks<T>) kb_viscous(BatchArgs A, DevBuffers B,
                                                                  const WorkList* wl) {
   __shared__ ShiftTable tab;
-  if constexpr (Local<T>::kLocal && !kShiftBitsRV<D>) fill_shift_table(tab);
+  if constexpr (Local<T>::kLocal && !kShiftBits<D>) fill_shift_table(tab);
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
     viscous_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x, &tab);
   });
@@ -142,7 +142,7 @@ template <int D, class T, bool kWallVel>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) kb_pressure(BatchArgs A, DevBuffers B,
                                                                   const WorkList* wl) {
   __shared__ ShiftTable tab;
-  if constexpr (Local<T>::kLocal) fill_shift_table(tab);
+  if constexpr (Local<T>::kLocal && !kShiftBits<D>) fill_shift_table(tab);
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
     pressure_range<D, T, kWallVel>(P, tank_buffers(A, B, t), tank_kc<T>(A, t), A.tsc + t, i, end,
                          blockDim.x, &tab);
@@ -153,7 +153,7 @@ template <int D, class T, bool kWallVel>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) kb_density_relax(BatchArgs A, DevBuffers B,
                                                                        const WorkList* wl) {
   __shared__ ShiftTable tab;
-  if constexpr (Local<T>::kLocal && !kShiftBitsRV<D>) fill_shift_table(tab);
+  if constexpr (Local<T>::kLocal && !kShiftBits<D>) fill_shift_table(tab);
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
     density_relax_range<D, T, kWallVel>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x,
                                        &tab);

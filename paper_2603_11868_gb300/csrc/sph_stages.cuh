@@ -591,11 +591,11 @@ __device__ __forceinline__ float shift_f(uint32_t c) {
 
 // Which float loops take the shifts from the entry bits (shift_f) rather than
 // the shared-memory table: measured per loop on the 5.1 M 3D dam break and the
-// 256 2D tanks (same values either way), the 3D density relaxation and viscous
-// loops ran faster without the table's shared-memory reads, the pressure loop
-// and every 2D loop slower.
+// 256 2D tanks (same values either way), every 3D loop ran faster without the
+// table's shared-memory reads (pressure 1.62 -> 1.44 ms per launch), every 2D
+// loop slower.
 template <int D>
-constexpr bool kShiftBitsRV = D == 3;
+constexpr bool kShiftBits = D == 3;
 
 // The last argument of a visitor call says whether the candidate may be the
 // target itself: direct search meets i in its own cell, a list never holds it
@@ -1124,8 +1124,8 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
                     R::pz(pi), k.cs};
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     T ax = 0, ay = 0, az = 0;
-    visit_neighbours<D, Local<T>::kLocal && !kShiftBitsRV<D>,
-                     Local<T>::kLocal && kShiftBitsRV<D>>(
+    visit_neighbours<D, Local<T>::kLocal && !kShiftBits<D>,
+                     Local<T>::kLocal && kShiftBits<D>>(
         P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w, auto may_self) {
       T rx, ry, rz;
       G.rel(j, dx, dy, dz, w, rx, ry, rz);
@@ -1167,7 +1167,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) k_viscous(Params P, DevBuf
   DevScalars* sc = B.sc;
   if (gated && !sc->new_adv) return;
   __shared__ ShiftTable tab;
-  if constexpr (Local<T>::kLocal && !kShiftBitsRV<D>) fill_shift_table(tab);
+  if constexpr (Local<T>::kLocal && !kShiftBits<D>) fill_shift_table(tab);
   viscous_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
                       gridDim.x * blockDim.x, &tab);
 }
@@ -1256,7 +1256,7 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     const T p_i = R::pres(pi, si), rho_i = R::rho(pi, si);
     T ax = 0, ay = 0, az = 0;
-    visit_neighbours<D, Local<T>::kLocal>(
+    visit_neighbours<D, Local<T>::kLocal && !kShiftBits<D>, Local<T>::kLocal && kShiftBits<D>>(
         P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w, auto may_self) {
       T rx, ry, rz;
       typename R::PV pj;
@@ -1354,7 +1354,7 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
 template <int D, class T, bool kWallVel, bool kAccel = false>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) k_pressure(Params P, DevBuffers B, KC<T> k) {
   __shared__ ShiftTable tab;
-  if constexpr (Local<T>::kLocal) fill_shift_table(tab);
+  if constexpr (Local<T>::kLocal && !kShiftBits<D>) fill_shift_table(tab);
   pressure_range<D, T, kWallVel, kAccel>(P, B, k, B.sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
                        gridDim.x * blockDim.x, &tab);
 }
@@ -1385,8 +1385,8 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     const T p_i = R::pres(pi, si), rho_i = R::rho(pi, si);
     T sum = 0;
-    visit_neighbours<D, Local<T>::kLocal && !kShiftBitsRV<D>,
-                     Local<T>::kLocal && kShiftBitsRV<D>>(
+    visit_neighbours<D, Local<T>::kLocal && !kShiftBits<D>,
+                     Local<T>::kLocal && kShiftBits<D>>(
         P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w, auto may_self) {
       T rx, ry, rz;
       typename R::PV pj;
@@ -1441,7 +1441,7 @@ template <int D, class T, bool kWallVel, bool kAccel = false>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) k_density_relax(Params P, DevBuffers B, KC<T> k) {
   DevScalars* sc = B.sc;
   __shared__ ShiftTable tab;
-  if constexpr (Local<T>::kLocal && !kShiftBitsRV<D>) fill_shift_table(tab);
+  if constexpr (Local<T>::kLocal && !kShiftBits<D>) fill_shift_table(tab);
   if (blockIdx.x == 0 && threadIdx.x == 0) sc->vmax2_cur = sc->vmax2_next;
   density_relax_range<D, T, kWallVel, kAccel>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
                             gridDim.x * blockDim.x, &tab);

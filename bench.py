@@ -91,8 +91,8 @@ def source_fingerprint() -> str:
 # depend on size at fixed h / dp), warp instructions by the list entries
 # (nearly all instructions are spent per entry).
 NCU_CAPTURES = {
-    ("pressure", "a8f1653eec8d"): {"fluid": 643200, "dram_bytes": 283244544 + 10778368,
-                                   "warp_inst": 146.6e6, "list_entries_per_particle": None},
+    ("pressure", "feecbce91878"): {"fluid": 643200, "dram_bytes": 283206656 + 10978560,
+                                   "warp_inst": 135902559, "list_entries_per_particle": None},
 }
 
 

@@ -17,8 +17,11 @@ steps / device time, summed over ranks.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Inputs stay resident in HBM (about 1.5 GB of state, far above the 129 MB L2,
-so no L2 flush is needed between steps).  Under torchrun each rank runs its
-own replica (weak scaling, no collective on the data path).
+so no L2 flush is needed between steps).  Under torchrun (N > 1) the tank is
+split into slabs along x over the ranks (strong scaling; the ranks exchange
+ghost particles and reduce the velocity maximum every acoustic step, see
+paper_2603_11868_gb300/slab.py); --replicas runs N independent replicas
+instead (weak scaling, no collective on the data path).
 """
 from __future__ import annotations
 
@@ -481,6 +484,94 @@ def run_batched(args):
     return 0
 
 
+def run_slab(args):
+    """The headline workload as one tank split into slabs along x over the N
+    ranks (paper_2603_11868_gb300/slab.py): each rank advances its own
+    particles and ghost copies of its neighbours'; after every acoustic step
+    the ranks all-reduce the velocity maximum and refresh the ghosts, and at
+    every advection-step boundary they hand over the particles that changed
+    slab.  value = the tank's fluid particles x acoustic steps / the slowest
+    rank's time: strong scaling (the total work is fixed)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2603_11868_gb300 import build, slab, sph
+
+    ws, rank, local = dist_env()
+    ndev = torch.cuda.device_count()
+    torch.cuda.set_device(local % ndev)
+    backend = args.slab_backend
+    if backend == "nccl":
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local % ndev))
+        device = f"cuda:{local % ndev}"
+    else:
+        dist.init_process_group("gloo")
+        device = "cpu"
+    build.build()
+    sph.load()
+    case, wname = make_workload(args.workload, args.dp)
+    n, nw = case.n, case.nw
+    t_e0 = time.perf_counter()
+    eng = slab.LibraryEngine(case, args.precision, device_rows=backend == "nccl")
+    r = slab.SlabRank(case, rank, ws, eng)
+    setup_s = time.perf_counter() - t_e0
+    slab.run_distributed(r, args.warmup * args.substeps, dist, device)
+    torch.cuda.synchronize()
+    dist.barrier()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local % ndev) as clk:
+        e0.record(st)
+        slab.run_distributed(r, args.steps * args.substeps, dist, device)
+        e1.record(st)
+        e1.synchronize()
+    el = e0.elapsed_time(e1) / 1e3
+    t = torch.tensor([el], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    el = float(t.item())
+    acoustic = args.steps * args.substeps
+    value = n * acoustic / el
+    # end to end: the set-up that uploads this rank's particles, the steps, and
+    # the owned state read back to the host
+    t_b = time.perf_counter()
+    slab.run_distributed(r, args.substeps, dist, device)
+    gid, own = r.owned_state()
+    torch.cuda.synchronize()
+    e2e_s = setup_s + (time.perf_counter() - t_b) * args.steps
+    t = torch.tensor([e2e_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_s = float(t.item())
+    counts = torch.tensor([r.n_own, r.n_gl + r.n_gr], dtype=torch.float64, device=device)
+    tot = counts.clone()
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    kps = sph.sph_kernels_per_step(eng.ctx)
+    eng.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": f"{wname}: {n} fluid + {nw} wall particles, "
+                                   f"{args.substeps} acoustic steps per bench step",
+                       "precision": args.precision, "fluid_particles": n,
+                       "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"slabs along x over {ws} ranks, halo "
+                                      f"{slab.HALO_CELLS} cells, {backend}"},
+            "slabs": {"cuts": [float(c) for c in r.cuts[1:-1]],
+                      "ghosts_over_owned": float(tot[1].item() / tot[0].item())},
+            "e2e": {"value": n * acoustic / e2e_s, "unit": "particle-steps/s",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                    "note": "set-up upload and final owned-state read, amortised over the "
+                            "timed steps"},
+            "gpu_launches": int(kps * acoustic) if kps > 0 else None,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    dist.barrier()
+    dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_2603_11868_gb300 import build, sph
@@ -664,6 +755,12 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="main number only")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with N > 1 ranks, N independent replicas instead of one tank split "
+                         "into slabs")
+    ap.add_argument("--slab-backend", choices=["nccl", "gloo"], default="nccl",
+                    help="transport of the slab split: nccl (device rows) or gloo (host "
+                         "arrays; ranks may share a GPU)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched-tank and neighbour-search lines nested in the default line")
     ap.add_argument("--no-autotune", action="store_true",
@@ -684,6 +781,8 @@ def main():
         return run_nsearch(args)
     if args.workload == "batched_256":
         return run_batched(args)
+    if dist_env()[0] > 1 and not args.replicas:
+        return run_slab(args)
     return run_ours(args)
 
 

@@ -336,6 +336,65 @@ size_t sph_nsearch_cell_count(const sph_nsearch* ns);
 /* Frees everything (waits first). */
 void sph_nsearch_destroy(sph_nsearch* ns);
 
+/* ---- Decomposition of one tank into slabs: state by id range, schedule ----
+ * A tank split into slabs along x (paper_2603_11868_gb300/slab.py) runs one
+ * context per rank holding its own particles and ghost copies of its
+ * neighbours' within a halo; after every acoustic step the ranks agree on the
+ * velocity maximum and refresh the ghosts, and at every advection-step
+ * boundary they hand over the particles that changed slab.  These calls move
+ * that state; the paper has no counterpart (its runs are single-device).
+ *
+ * User ids are the indices of the last sph_set_particles(SPH_FLUID) call.
+ * The state of user ids [id0, id0 + m) -- position and velocity (m x dim),
+ * density, density rate (m), prior acceleration (m x dim), each a host array
+ * in id order or NULL to skip it -- is copied out of the context / into it.
+ * The density rate and the prior acceleration are held in the pair type
+ * (float in mixed precision: values put are rounded to it).  Both calls
+ * wait for the context's queued work.  SPH_E_INVALID when id0 + m > n,
+ * SPH_E_STATE before fluid particles are set. */
+int sph_get_state_range(sph_ctx* ctx, uint32_t id0, size_t m, double* pos, double* vel,
+                        double* rho, double* drho, double* aprior);
+int sph_put_state_range(sph_ctx* ctx, uint32_t id0, size_t m, const double* pos,
+                        const double* vel, const double* rho, const double* drho,
+                        const double* aprior);
+
+/* Schedule scalars as eight doubles: t, tau (time since the advection step
+ * began), dt_ad, dt_ac, acoustic steps, advection steps, started (0/1), and
+ * the squared velocity maximum the next step's time steps come from.  get
+ * reads them (waits); set writes them, and only where the next step begins
+ * an advection step (tau >= dt_ad, or started = 0): SPH_E_INVALID otherwise
+ * or for a negative or non-finite value.  set does not touch the particles. */
+int sph_get_schedule(sph_ctx* ctx, double sched[8]);
+int sph_set_schedule(sph_ctx* ctx, const double sched[8]);
+
+/* max |v|^2 over the fluid particles whose user id is below n_own (a rank's
+ * own particles, its ghosts excluded), into *vmax2.  Waits. */
+int sph_owned_vmax2(sph_ctx* ctx, uint32_t n_own, double* vmax2);
+
+/* Sets the squared velocity maximum the next step's time steps come from
+ * (the ranks' common value, in place of the context's own).  Waits.
+ * SPH_E_INVALID for a negative or non-finite value. */
+int sph_set_vmax2(sph_ctx* ctx, double vmax2);
+
+/* Device-memory forms of the per-step exchange, queued on the context's
+ * stream in order with sph_step and returning without waiting (errors of the
+ * queued work surface at the next waiting call), so that ghost refreshes and
+ * the velocity maximum travel device to device (e.g. by NCCL on the same
+ * stream):
+ *   rows: m x (3 dim + 2) doubles per particle of user ids [id0, id0 + m):
+ *         position, velocity, density, density rate, prior acceleration,
+ *         caller-owned device memory (get writes them, put reads them);
+ *   sph_owned_vmax2_device writes max |v|^2 of user ids below n_own as one
+ *         double at device address vmax2 (non-negative doubles order like
+ *         their 64-bit patterns, so an integer max-reduction of the bits
+ *         combines ranks exactly);
+ *   sph_set_vmax2_device reads the common value from device address vmax2.
+ * SPH_E_INVALID for a bad range or NULL, SPH_E_STATE before fluid is set. */
+int sph_get_state_rows_device(sph_ctx* ctx, uint32_t id0, size_t m, double* rows);
+int sph_put_state_rows_device(sph_ctx* ctx, uint32_t id0, size_t m, const double* rows);
+int sph_owned_vmax2_device(sph_ctx* ctx, uint32_t n_own, double* vmax2);
+int sph_set_vmax2_device(sph_ctx* ctx, const double* vmax2);
+
 /* Largest n accepted by sph_cell_sort_noalloc. */
 #define SPH_NOALLOC_MAX_PARTICLES (1u << 20)
 

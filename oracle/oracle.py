@@ -99,6 +99,10 @@ def lib():
             L.osph_sample_sigma.argtypes = [vp, l, vp, vp]
             L.osph_sample_first_step_acc.restype = None
             L.osph_sample_first_step_acc.argtypes = [vp, l, vp, vp]
+            L.osph_state_range.restype = i
+            L.osph_state_range.argtypes = [vp, l, l, vp, vp, vp, vp, vp, i]
+            L.osph_set_schedule.restype = None
+            L.osph_set_schedule.argtypes = [vp, d, d, d, d, l, l, i]
             _lib = L
     return _lib
 
@@ -308,6 +312,35 @@ class Oracle:
         out = np.zeros((len(ids), self.dim), np.float64)
         lib().osph_sample_first_step_acc(self._s, len(ids), _ptr(ids), _ptr(out))
         return out
+
+    def state_range(self, id0, m):
+        """State of user ids [id0, id0 + m): pos, vel, aprior (m, dim), rho, drho (m)."""
+        out = {k: np.zeros((m, 3)) for k in ("pos", "vel", "aprior")}
+        out.update(rho=np.zeros(m), drho=np.zeros(m))
+        if lib().osph_state_range(self._s, id0, m, _ptr(out["pos"]), _ptr(out["vel"]),
+                                  _ptr(out["rho"]), _ptr(out["drho"]), _ptr(out["aprior"]), 0):
+            raise ValueError("oracle: id range beyond n")
+        for k in ("pos", "vel", "aprior"):
+            out[k] = np.ascontiguousarray(out[k][:, :self.dim])
+        return out
+
+    def put_state_range(self, id0, state):
+        """Write the state of user ids [id0, id0 + m) (keys as state_range)."""
+        m = len(state["rho"])
+        full = {}
+        for k in ("pos", "vel", "aprior"):
+            a = np.zeros((m, 3))
+            a[:, :self.dim] = state[k]
+            full[k] = a
+        rho = np.ascontiguousarray(state["rho"], dtype=np.float64)
+        drho = np.ascontiguousarray(state["drho"], dtype=np.float64)
+        if lib().osph_state_range(self._s, id0, m, _ptr(full["pos"]), _ptr(full["vel"]),
+                                  _ptr(rho), _ptr(drho), _ptr(full["aprior"]), 1):
+            raise ValueError("oracle: id range beyond n")
+
+    def set_schedule(self, t, tau, dt_ad, dt_ac, n_ac, n_adv, started):
+        lib().osph_set_schedule(self._s, t, tau, dt_ad, dt_ac, int(n_ac), int(n_adv),
+                                int(started))
 
     def sample_sigma(self, user_ids):
         ids = np.ascontiguousarray(user_ids, dtype=np.uint32)

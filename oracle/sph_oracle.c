@@ -437,6 +437,44 @@ int osph_set_drho(osim* s, const double* drho) {
   return 0;
 }
 
+/* State of the fluid particles with user ids [id0, id0 + m), arrays in id
+ * order (position, velocity and prior acceleration m x 3 with the unused
+ * components 0; NULL skips a field): copied in (put) or out.  Test
+ * infrastructure for running the oracle as the ranks of a slab
+ * decomposition; no arithmetic of the method. */
+int osph_state_range(osim* s, long id0, long m, double* pos, double* vel, double* rho,
+                     double* drho, double* aprior, int put) {
+  if (id0 < 0 || m < 0 || id0 + m > s->n) return 1;
+  for (long k = 0; k < s->n; ++k) {
+    long u = (long)s->id[k] - id0;
+    if (u < 0 || u >= m) continue;
+    for (int c = 0; c < 3; ++c) {
+      if (pos) { if (put) s->x[k][c] = pos[u * 3 + c]; else pos[u * 3 + c] = s->x[k][c]; }
+      if (vel) { if (put) s->v[k][c] = vel[u * 3 + c]; else vel[u * 3 + c] = s->v[k][c]; }
+      if (aprior) {
+        if (put) s->aprior[k][c] = aprior[u * 3 + c];
+        else aprior[u * 3 + c] = s->aprior[k][c];
+      }
+    }
+    if (rho) { if (put) s->rho[k] = rho[u]; else rho[u] = s->rho[k]; }
+    if (drho) { if (put) s->drho[k] = drho[u]; else drho[u] = s->drho[k]; }
+  }
+  return 0;
+}
+
+/* The schedule scalars t, tau, dt_ad, dt_ac, acoustic and advection step
+ * counts and the started flag (test infrastructure, as above). */
+void osph_set_schedule(osim* s, double t, double tau, double dt_ad, double dt_ac, long n_ac,
+                       long n_adv, int started) {
+  s->t = t;
+  s->tau = tau;
+  s->dt_ad = dt_ad;
+  s->dt_ac = dt_ac;
+  s->n_ac = n_ac;
+  s->n_adv = n_adv;
+  s->started = started;
+}
+
 /* The 3^d cells around a binned cell, in the order dz, dy, dx = -1..1,
  * skipping cells outside the grid. */
 static int neighbour_cells(const osim* s, uint32_t key, long* out) {

@@ -88,6 +88,12 @@ void osph_transport_correction(osim* s);
 
 /* set the carried density rate (user order, n values); default 0 */
 int osph_set_drho(osim* s, const double* drho);
+/* test infrastructure for slab-decomposed oracle runs: state of user ids
+ * [id0, id0 + m) in / out (vectors m x 3), and the schedule scalars */
+int osph_state_range(osim* s, long id0, long m, double* pos, double* vel, double* rho,
+                     double* drho, double* aprior, int put);
+void osph_set_schedule(osim* s, double t, double tau, double dt_ad, double dt_ac, long n_ac,
+                       long n_adv, int started);
 
 /* the full schedule: n acoustic steps */
 int osph_step(osim* s, long n);

@@ -48,6 +48,17 @@ struct sph_ctx {
 
 namespace {
 
+double __longlong_as_double_host(long long v) {
+  double d;
+  memcpy(&d, &v, sizeof d);
+  return d;
+}
+long long __double_as_longlong_host(double d) {
+  long long v;
+  memcpy(&v, &d, sizeof v);
+  return v;
+}
+
 int set_err(sph_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
@@ -433,11 +444,12 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
   c->B.cell_begin = (uint32_t*)dev_alloc(c, ((size_t)P.ncell + 1) * 4, c->fixed_blocks);
   c->B.wall_cb = (uint32_t*)dev_alloc(c, ((size_t)P.ncell + 1) * 4, c->fixed_blocks);
   c->B.digit_total = (uint32_t*)dev_alloc(c, ((size_t)1 << kMaxRadixBits) * 4, c->fixed_blocks);
+  c->B.u64_io = (unsigned long long*)dev_alloc(c, 8, c->fixed_blocks);
   double* ctab = nullptr;
   if (precision == SPH_MIXED)
     ctab = (double*)dev_alloc(c, (size_t)(P.nx + P.ny + P.nz) * 8, c->fixed_blocks);
   c->B.ctab = ctab;
-  if (!c->B.sc || !c->B.cell_begin || !c->B.wall_cb || !c->B.digit_total ||
+  if (!c->B.sc || !c->B.cell_begin || !c->B.wall_cb || !c->B.digit_total || !c->B.u64_io ||
       (precision == SPH_MIXED && !ctab)) {
     sph_destroy(c);
     return SPH_E_OOM;
@@ -1085,6 +1097,175 @@ int sph_debug_neighbour_stats(sph_ctx* c, uint32_t* cnt_fluid, uint32_t* cnt_wal
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   dev_free_list(c, tmp);
   if (e != cudaSuccess) return cuda_err(c, e, "sph_debug_neighbour_stats");
+  rc = leave(c);
+  if (rc) return rc;
+  return sync_status(c);
+}
+
+// ---------------------------------------------------------------------------
+// State by user-id range and the schedule scalars: what a decomposition of one
+// tank into slabs exchanges between the contexts of its ranks.
+namespace {
+int state_range(sph_ctx* c, uint32_t id0, size_t m, double* const host[5], int put) {
+  if (!c) return SPH_E_INVALID;
+  if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
+  if ((size_t)id0 + m > (size_t)c->P.n) return set_err(c, SPH_E_INVALID, "id range beyond n");
+  if (m == 0) return SPH_OK;
+  int rc = enter(c);
+  if (rc) return rc;
+  const int d = c->P.dim;
+  const int is_float = c->precision == SPH_MIXED ? 1 : 0;
+  for (int f = 0; f < 5; ++f) {
+    if (!host[f]) continue;
+    const size_t bytes = m * (size_t)(f == 0 || f == 1 || f == 4 ? d : 1) * 8;
+    if (put) {
+      CK(cudaMemcpyAsync(c->B.io, host[f], bytes, cudaMemcpyHostToDevice, c->stream));
+      launch_state_range(c->P, c->L, c->B, id0, (uint32_t)m, c->B.io, f, 1, is_float, c->stream);
+    } else {
+      launch_state_range(c->P, c->L, c->B, id0, (uint32_t)m, c->B.io, f, 0, is_float, c->stream);
+      CK(cudaMemcpyAsync(host[f], c->B.io, bytes, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaGetLastError());
+    // the staging buffer is reused by the next field
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  rc = leave(c);
+  if (rc) return rc;
+  return sync_status(c);
+}
+}  // namespace
+
+int sph_get_state_range(sph_ctx* c, uint32_t id0, size_t m, double* pos, double* vel,
+                        double* rho, double* drho, double* aprior) {
+  TraceRange tr("sph_get_state_range");
+  double* const h[5] = {pos, vel, rho, drho, aprior};
+  return state_range(c, id0, m, h, 0);
+}
+
+int sph_put_state_range(sph_ctx* c, uint32_t id0, size_t m, const double* pos, const double* vel,
+                        const double* rho, const double* drho, const double* aprior) {
+  TraceRange tr("sph_put_state_range");
+  double* const h[5] = {(double*)pos, (double*)vel, (double*)rho, (double*)drho,
+                        (double*)aprior};
+  return state_range(c, id0, m, h, 1);
+}
+
+namespace {
+int state_rows_device(sph_ctx* c, uint32_t id0, size_t m, double* rows, int put) {
+  if (!c || (m > 0 && !rows)) return SPH_E_INVALID;
+  if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
+  if ((size_t)id0 + m > (size_t)c->P.n) return set_err(c, SPH_E_INVALID, "id range beyond n");
+  if (m == 0) return SPH_OK;
+  int rc = enter(c);
+  if (rc) return rc;
+  launch_state_rows(c->P, c->L, c->B, id0, (uint32_t)m, rows, put,
+                    c->precision == SPH_MIXED ? 1 : 0, c->stream);
+  CK(cudaGetLastError());
+  return leave(c);
+}
+}  // namespace
+
+int sph_get_state_rows_device(sph_ctx* c, uint32_t id0, size_t m, double* rows) {
+  return state_rows_device(c, id0, m, rows, 0);
+}
+
+int sph_put_state_rows_device(sph_ctx* c, uint32_t id0, size_t m, const double* rows) {
+  return state_rows_device(c, id0, m, (double*)rows, 1);
+}
+
+int sph_owned_vmax2_device(sph_ctx* c, uint32_t n_own, double* vmax2) {
+  if (!c || !vmax2) return SPH_E_INVALID;
+  if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
+  int rc = enter(c);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(vmax2, 0, sizeof(double), c->stream));
+  launch_vmax_owned(c->P, c->L, c->B, n_own, (unsigned long long*)vmax2, c->stream);
+  CK(cudaGetLastError());
+  return leave(c);
+}
+
+int sph_set_vmax2_device(sph_ctx* c, const double* vmax2) {
+  if (!c || !vmax2) return SPH_E_INVALID;
+  int rc = enter(c);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync((char*)c->B.sc + offsetof(DevScalars, vmax2_cur), vmax2, sizeof(double),
+                     cudaMemcpyDeviceToDevice, c->stream));
+  return leave(c);
+}
+
+int sph_get_schedule(sph_ctx* c, double sched[8]) {
+  if (!c || !sched) return SPH_E_INVALID;
+  int rc = enter(c);
+  if (rc) return rc;
+  DevScalars hs;
+  rc = read_scalars(c, &hs);
+  if (rc) return rc;
+  sched[0] = hs.t;
+  sched[1] = hs.tau;
+  sched[2] = hs.dt_ad;
+  sched[3] = hs.dt_ac;
+  sched[4] = (double)hs.n_ac;
+  sched[5] = (double)hs.n_adv;
+  sched[6] = (double)hs.started;
+  sched[7] = __longlong_as_double_host((long long)hs.vmax2_cur);
+  return flags_status(c, hs);
+}
+
+int sph_set_schedule(sph_ctx* c, const double sched[8]) {
+  if (!c || !sched) return SPH_E_INVALID;
+  if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
+  for (int k = 0; k < 8; ++k)
+    if (!std::isfinite(sched[k])) return set_err(c, SPH_E_INVALID, "schedule value not finite");
+  if (!(sched[7] >= 0) || !(sched[1] >= 0) || !(sched[2] >= 0) || !(sched[3] >= 0))
+    return set_err(c, SPH_E_INVALID, "negative schedule value");
+  // only where the next step begins an advection step (its rebuild sets the
+  // neighbour structure, lists and budgets anew)
+  if (sched[6] != 0.0 && !(sched[1] >= sched[2]))
+    return set_err(c, SPH_E_INVALID, "schedule must be at an advection-step boundary (tau >= dt_ad)");
+  int rc = enter(c);
+  if (rc) return rc;
+  DevScalars hs;
+  rc = read_scalars(c, &hs);
+  if (rc) return rc;
+  hs.t = sched[0];
+  hs.tau = sched[1];
+  hs.dt_ad = sched[2];
+  hs.dt_ac = sched[3];
+  hs.n_ac = (long long)sched[4];
+  hs.n_adv = (long long)sched[5];
+  hs.started = sched[6] != 0.0 ? 1 : 0;
+  hs.vmax2_cur = (unsigned long long)__double_as_longlong_host(sched[7]);
+  CK(cudaMemcpyAsync(c->B.sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return leave(c);
+}
+
+int sph_set_vmax2(sph_ctx* c, double vmax2) {
+  if (!c) return SPH_E_INVALID;
+  if (!(vmax2 >= 0) || !std::isfinite(vmax2))
+    return set_err(c, SPH_E_INVALID, "vmax2 must be finite and non-negative");
+  int rc = enter(c);
+  if (rc) return rc;
+  const unsigned long long bits = (unsigned long long)__double_as_longlong_host(vmax2);
+  CK(cudaMemcpyAsync((char*)c->B.sc + offsetof(DevScalars, vmax2_cur), &bits, sizeof(bits),
+                     cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return leave(c);
+}
+
+int sph_owned_vmax2(sph_ctx* c, uint32_t n_own, double* vmax2) {
+  if (!c || !vmax2) return SPH_E_INVALID;
+  if (!c->fluid_set) return set_err(c, SPH_E_STATE, "no fluid particles set");
+  int rc = enter(c);
+  if (rc) return rc;
+  unsigned long long* out = c->B.u64_io;
+  CK(cudaMemsetAsync(out, 0, sizeof(*out), c->stream));
+  launch_vmax_owned(c->P, c->L, c->B, n_own, out, c->stream);
+  CK(cudaGetLastError());
+  unsigned long long bits = 0;
+  CK(cudaMemcpyAsync(&bits, out, sizeof(bits), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *vmax2 = __longlong_as_double_host((long long)bits);
   rc = leave(c);
   if (rc) return rc;
   return sync_status(c);

@@ -407,6 +407,19 @@ void launch_control_cond(const Params& P, DevScalars* sc, cudaGraphConditionalHa
 void launch_vmax_reset(const Params& P, const LaunchCfg& L, const DevBuffers& B,
                        cudaStream_t s);
 // debug neighbour statistics (double positions of the live copy)
+// State of the particles with user ids [id0, id0 + m) gathered into (put = 0)
+// or scattered from (put = 1) the device array buf in user-id order; field 0
+// position, 1 velocity, 2 density, 3 density rate, 4 prior acceleration.
+void launch_state_range(const Params& P, const LaunchCfg& L, const DevBuffers& B, uint32_t id0,
+                        uint32_t m, double* buf, int field, int put, int pair_is_float,
+                        cudaStream_t s);
+// the same as packed rows (3 dim + 2 doubles per particle: position,
+// velocity, density, density rate, prior acceleration), device memory
+void launch_state_rows(const Params& P, const LaunchCfg& L, const DevBuffers& B, uint32_t id0,
+                       uint32_t m, double* rows, int put, int pair_is_float, cudaStream_t s);
+// max |v|^2 of the particles with user ids below n_own, atomically maxed into *out
+void launch_vmax_owned(const Params& P, const LaunchCfg& L, const DevBuffers& B, uint32_t n_own,
+                       unsigned long long* out, cudaStream_t s);
 void launch_neighbour_stats(const Params& P, const LaunchCfg& L, const DevBuffers& B,
                             const double* wall_xyz, uint32_t* cnt_f, uint32_t* cnt_w,
                             unsigned long long* hash, cudaStream_t s);

@@ -505,6 +505,109 @@ __global__ void k_vmax(Params P, DevBuffers B, int n) {
   }
 }
 
+// Per-particle state of the particles with user ids [id0, id0 + m) (the
+// live copy): gather into / scatter from arrays in user-id order, `comps`
+// values per particle (field: 0 position, 1 velocity, 2 density, 3 density
+// rate, 4 prior acceleration; the last two in the pair type).
+__global__ void k_state_range(Params P, DevBuffers B, uint32_t id0, uint32_t m, double* buf,
+                              int field, int put, int pair_is_float) {
+  DevScalars* sc = B.sc;
+  const int par = sc->par;
+  const uint32_t* id = B.id[par];
+  const int d = P.dim;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.n; s += gridDim.x * blockDim.x) {
+    const uint32_t u = id[s] - id0;
+    if (u >= m) continue;
+    switch (field) {
+      case 0:
+      case 1:
+        for (int k = 0; k < d; ++k) {
+          double* a = field == 0 ? B.x[par][k] : B.v[par][k];
+          if (put) a[s] = buf[(size_t)u * d + k]; else buf[(size_t)u * d + k] = a[s];
+        }
+        break;
+      case 2:
+        if (put) B.rho[par][s] = buf[u]; else buf[u] = B.rho[par][s];
+        break;
+      case 3:
+        if (pair_is_float) {
+          float* a = (float*)B.drho[par];
+          if (put) a[s] = (float)buf[u]; else buf[u] = a[s];
+        } else {
+          double* a = (double*)B.drho[par];
+          if (put) a[s] = buf[u]; else buf[u] = a[s];
+        }
+        break;
+      default:
+        for (int k = 0; k < d; ++k) {
+          if (pair_is_float) {
+            float* a = (float*)B.aprior[k];
+            if (put) a[s] = (float)buf[(size_t)u * d + k]; else buf[(size_t)u * d + k] = a[s];
+          } else {
+            double* a = (double*)B.aprior[k];
+            if (put) a[s] = buf[(size_t)u * d + k]; else buf[(size_t)u * d + k] = a[s];
+          }
+        }
+    }
+  }
+}
+
+// The state of user ids [id0, id0 + m) as packed rows in user-id order,
+// 3 dim + 2 doubles each: position, velocity, density, density rate, prior
+// acceleration; gathered into (put = 0) or scattered from (put = 1) rows.
+__global__ void k_state_rows(Params P, DevBuffers B, uint32_t id0, uint32_t m, double* rows,
+                             int put, int pair_is_float) {
+  DevScalars* sc = B.sc;
+  const int par = sc->par;
+  const uint32_t* id = B.id[par];
+  const int d = P.dim, w = 3 * d + 2;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < P.n; s += gridDim.x * blockDim.x) {
+    const uint32_t u = id[s] - id0;
+    if (u >= m) continue;
+    double* r = rows + (size_t)u * w;
+    for (int k = 0; k < d; ++k) {
+      if (put) {
+        B.x[par][k][s] = r[k];
+        B.v[par][k][s] = r[d + k];
+      } else {
+        r[k] = B.x[par][k][s];
+        r[d + k] = B.v[par][k][s];
+      }
+    }
+    if (put) B.rho[par][s] = r[2 * d]; else r[2 * d] = B.rho[par][s];
+    if (pair_is_float) {
+      float* dr = (float*)B.drho[par];
+      if (put) dr[s] = (float)r[2 * d + 1]; else r[2 * d + 1] = dr[s];
+      for (int k = 0; k < d; ++k) {
+        float* a = (float*)B.aprior[k];
+        if (put) a[s] = (float)r[2 * d + 2 + k]; else r[2 * d + 2 + k] = a[s];
+      }
+    } else {
+      double* dr = (double*)B.drho[par];
+      if (put) dr[s] = r[2 * d + 1]; else r[2 * d + 1] = dr[s];
+      for (int k = 0; k < d; ++k) {
+        double* a = (double*)B.aprior[k];
+        if (put) a[s] = r[2 * d + 2 + k]; else r[2 * d + 2 + k] = a[s];
+      }
+    }
+  }
+}
+
+// max |v|^2 over the particles with user ids below n_own (the live copy)
+__global__ void k_vmax_owned(Params P, DevBuffers B, uint32_t n_own, unsigned long long* out) {
+  DevScalars* sc = B.sc;
+  const int par = sc->par;
+  const uint32_t* id = B.id[par];
+  double m = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    if (id[i] >= n_own) continue;
+    const double s = speed2(B.v[par][0][i], B.v[par][1][i], P.dim == 3 ? B.v[par][2][i] : 0.0);
+    m = s > m ? s : m;
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
 __global__ void kb_vmax(BatchArgs A, DevBuffers B) {
   __shared__ double wm[32];
   const WorkList* wl = A.wl_all;
@@ -761,6 +864,31 @@ void launch_vmax_reset(const Params& P, const LaunchCfg& L, const DevBuffers& B,
   if (blocks > L.blocks_stream) blocks = L.blocks_stream;
   if (blocks < 1) blocks = 1;
   k_vmax<<<blocks, L.block_stream, 0, s>>>(P, B, P.n);
+}
+
+void launch_state_range(const Params& P, const LaunchCfg& L, const DevBuffers& B, uint32_t id0,
+                        uint32_t m, double* buf, int field, int put, int pair_is_float,
+                        cudaStream_t s) {
+  int blocks = (P.n + L.block_stream - 1) / L.block_stream;
+  if (blocks > L.blocks_stream) blocks = L.blocks_stream;
+  if (blocks < 1) blocks = 1;
+  k_state_range<<<blocks, L.block_stream, 0, s>>>(P, B, id0, m, buf, field, put, pair_is_float);
+}
+
+void launch_state_rows(const Params& P, const LaunchCfg& L, const DevBuffers& B, uint32_t id0,
+                       uint32_t m, double* rows, int put, int pair_is_float, cudaStream_t s) {
+  int blocks = (P.n + L.block_stream - 1) / L.block_stream;
+  if (blocks > L.blocks_stream) blocks = L.blocks_stream;
+  if (blocks < 1) blocks = 1;
+  k_state_rows<<<blocks, L.block_stream, 0, s>>>(P, B, id0, m, rows, put, pair_is_float);
+}
+
+void launch_vmax_owned(const Params& P, const LaunchCfg& L, const DevBuffers& B, uint32_t n_own,
+                       unsigned long long* out, cudaStream_t s) {
+  int blocks = (P.n + L.block_stream - 1) / L.block_stream;
+  if (blocks > L.blocks_stream) blocks = L.blocks_stream;
+  if (blocks < 1) blocks = 1;
+  k_vmax_owned<<<blocks, L.block_stream, 0, s>>>(P, B, n_own, out);
 }
 
 void launch_neighbour_stats(const Params& P, const LaunchCfg& L, const DevBuffers& B,

@@ -53,7 +53,10 @@ EXPORTS = ("sph_create", "sph_set_particles", "sph_step", "sph_get_fields", "sph
            "sph_autotune", "sph_batch_autotune", "sph_debug_list_lengths",
            "sph_set_wall_translation", "sph_set_wall_motion", "sph_checkpoint_bytes",
            "sph_checkpoint_save",
-           "sph_checkpoint_load")
+           "sph_checkpoint_load", "sph_get_state_range", "sph_put_state_range",
+           "sph_get_schedule", "sph_set_schedule", "sph_owned_vmax2", "sph_set_vmax2",
+           "sph_get_state_rows_device", "sph_put_state_rows_device", "sph_owned_vmax2_device",
+           "sph_set_vmax2_device")
 SPH_MAX_TANKS = 1024
 SPH_NOALLOC_MAX_PARTICLES = 1 << 20
 STAGE_NAMES = ("control", "keys", "sort", "reorder", "offsets", "density_sum", "viscous",
@@ -204,6 +207,25 @@ def load(path: str | None = None):
         L.sph_cell_sort_noalloc.restype = i
         L.sph_cell_sort_noalloc.argtypes = [C.POINTER(sph_domain), d, vp, vp, vp, sz, vp, vp, vp,
                                             vp]
+        u32 = C.c_uint32
+        for name in ("sph_get_state_range", "sph_put_state_range"):
+            getattr(L, name).restype = i
+            getattr(L, name).argtypes = [vp, u32, sz, vp, vp, vp, vp, vp]
+        L.sph_get_schedule.restype = i
+        L.sph_get_schedule.argtypes = [vp, vp]
+        L.sph_set_schedule.restype = i
+        L.sph_set_schedule.argtypes = [vp, vp]
+        L.sph_owned_vmax2.restype = i
+        L.sph_owned_vmax2.argtypes = [vp, u32, C.POINTER(C.c_double)]
+        L.sph_set_vmax2.restype = i
+        L.sph_set_vmax2.argtypes = [vp, d]
+        for name in ("sph_get_state_rows_device", "sph_put_state_rows_device"):
+            getattr(L, name).restype = i
+            getattr(L, name).argtypes = [vp, u32, sz, vp]
+        L.sph_owned_vmax2_device.restype = i
+        L.sph_owned_vmax2_device.argtypes = [vp, u32, vp]
+        L.sph_set_vmax2_device.restype = i
+        L.sph_set_vmax2_device.argtypes = [vp, vp]
         _lib = L
         return L
 
@@ -320,6 +342,52 @@ def sph_debug_neighbour_stats(ctx, n):
     cf = np.empty(n, np.uint32); cw = np.empty(n, np.uint32); hs = np.empty(n, np.uint64)
     _check(ctx, load().sph_debug_neighbour_stats(ctx, _ptr(cf), _ptr(cw), _ptr(hs)))
     return cf, cw, hs
+
+
+STATE_FIELDS = ("pos", "vel", "rho", "drho", "aprior")
+
+
+def sph_get_state_range(ctx, id0, m, dim):
+    """State of user ids [id0, id0 + m): dict of pos, vel (m, dim), rho, drho (m),
+    aprior (m, dim), float64."""
+    out = {"pos": np.empty((m, dim)), "vel": np.empty((m, dim)), "rho": np.empty(m),
+           "drho": np.empty(m), "aprior": np.empty((m, dim))}
+    _check(ctx, load().sph_get_state_range(ctx, id0, m, *(_ptr(out[k]) for k in STATE_FIELDS)))
+    return out
+
+
+def sph_put_state_range(ctx, id0, state):
+    """Write the state of user ids [id0, id0 + m) (dict as sph_get_state_range
+    returns; missing keys are left as they are)."""
+    arr = {k: (np.ascontiguousarray(state[k], dtype=np.float64) if state.get(k) is not None
+               else None) for k in STATE_FIELDS}
+    m = len(next(a for a in arr.values() if a is not None)) if any(
+        a is not None for a in arr.values()) else 0
+    _check(ctx, load().sph_put_state_range(ctx, id0, m, *(_ptr(arr[k]) for k in STATE_FIELDS)))
+
+
+SCHEDULE_KEYS = ("t", "tau", "dt_ad", "dt_ac", "n_ac", "n_adv", "started", "vmax2")
+
+
+def sph_get_schedule(ctx):
+    out = np.zeros(8)
+    _check(ctx, load().sph_get_schedule(ctx, _ptr(out)))
+    return dict(zip(SCHEDULE_KEYS, out.tolist()))
+
+
+def sph_set_schedule(ctx, sched):
+    arr = np.array([float(sched[k]) for k in SCHEDULE_KEYS])
+    _check(ctx, load().sph_set_schedule(ctx, _ptr(arr)))
+
+
+def sph_owned_vmax2(ctx, n_own):
+    v = C.c_double()
+    _check(ctx, load().sph_owned_vmax2(ctx, int(n_own), C.byref(v)))
+    return v.value
+
+
+def sph_set_vmax2(ctx, vmax2):
+    _check(ctx, load().sph_set_vmax2(ctx, float(vmax2)))
 
 
 def sph_debug_list_lengths(ctx, n):

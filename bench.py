@@ -94,7 +94,7 @@ def source_fingerprint() -> str:
 # depend on size at fixed h / dp), warp instructions by the list entries
 # (nearly all instructions are spent per entry).
 NCU_CAPTURES = {
-    ("pressure", "feecbce91878"): {"fluid": 643200, "dram_bytes": 283206656 + 10978560,
+    ("pressure", "26068f2cade4"): {"fluid": 643200, "dram_bytes": 283195392 + 11122688,
                                    "warp_inst": 135902559, "list_entries_per_particle": None},
 }
 

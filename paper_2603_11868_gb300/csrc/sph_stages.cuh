@@ -1131,9 +1131,12 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
       G.rel(j, dx, dy, dz, w, rx, ry, rz);
       const T r2 = r2_of(rx, ry, rz);
       if (!(r2 < k.r2max) || (may_self && !w && j == i)) return;
-      const T r = sqrt(r2);
+      const T r = r2 * inv_sqrt_t(r2);
+      const T t = T(1) + r * k.neg_inv_2h;
+      // W'(r) / (r + eps) = (cdW/h) t^3 r / (r + eps); cdW/h applied per particle
+      const T g = (t * t * t) * div_t(r, r + k.eps);
       if (w) {
-        const T coef = wallV2 * wendland_dr(k, r) / (r + k.eps);
+        const T coef = wallV2 * g;
         T ux = vxi, uy = vyi, uz = vzi;
         if (moving) {
           using WR = WallRec<D, T>;
@@ -1148,13 +1151,13 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
       } else {
         const typename R::PV pj = recP[j];
         const typename R::SV sj = recS[j];
-        const T coef = div_t(k.m, R::rho(pj, sj)) * wendland_dr(k, r) / (r + k.eps);
+        const T coef = div_t(k.m, R::rho(pj, sj)) * g;
         ax += coef * (vxi - R::vx(pj, sj));
         ay += coef * (vyi - R::vy(pj, sj));
         az += coef * (vzi - R::vz(pj, sj));
       }
     }, tab);
-    const T f = div_t(k.two_mu, R::rho(pi, si));
+    const T f = div_t(k.two_mu * (k.cdW * k.inv_h), R::rho(pi, si));
     ap0[i] = k.g[0] + f * ax;
     ap1[i] = k.g[1] + f * ay;
     if (D == 3) ap2[i] = k.g[2] + f * az;

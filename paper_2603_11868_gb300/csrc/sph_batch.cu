@@ -237,15 +237,14 @@ int alloc_fluid(sph_batch* b, size_t n) {
     ok &= k >= d || B.xreb[k];
   }
   B.bud = (float*)Al(nn * 4);
-  ok &= B.sigma64 != nullptr && B.bud != nullptr;
-  const size_t pbytes = 4 * ts;
-  const size_t sbytes = (d == 3 ? 4 : 2) * ts;
+  B.brec = Al(nn * 4 * ts);
+  ok &= B.sigma64 != nullptr && B.bud != nullptr && B.brec != nullptr;
   for (int p = 0; p < 2; ++p) {
-    B.recP[p] = Al(nn * pbytes);
-    B.recS[p] = Al(nn * sbytes);
+    B.rec[p] = Al(nn * (d == 3 ? 8 : 4) * ts);
+    B.rec_s[p] = d == 3 ? nullptr : Al(nn * 2 * ts);
     B.keys[p] = (uint32_t*)Al(nn * 4);
     B.vals[p] = (uint32_t*)Al(nn * 4);
-    ok &= B.recP[p] && B.recS[p] && B.keys[p] && B.vals[p];
+    ok &= B.rec[p] && (d == 3 || B.rec_s[p]) && B.keys[p] && B.vals[p];
   }
   B.recI = b->precision == SPH_MIXED ? Al(nn * (d == 3 ? 16 : 8)) : nullptr;
   ok &= b->precision != SPH_MIXED || B.recI;
@@ -740,9 +739,9 @@ int sph_batch_get_fields(sph_batch* b, unsigned mask, double* out) {
       case SPH_F_P:
         // pressure of the last first half-step, kept in the records of buffer 0
         if (d == 3)
-          f = field_src(B.recP[0], 0, 0, B.recP[0], 0, 0, B, isf, 4, 3, 1);
+          f = field_src(B.rec[0], 0, 0, B.rec[0], 0, 0, B, isf, 8, 3, 1);
         else
-          f = field_src(B.recS[0], 0, 0, B.recS[0], 0, 0, B, isf, 2, 0, 1);
+          f = field_src(B.rec_s[0], 0, 0, B.rec_s[0], 0, 0, B, isf, 2, 0, 1);
         break;
       case SPH_F_DRHO:
         f = field_src(B.drho[0], 0, 0, B.drho[1], 0, 0, B, isf, 1, 0, 1);

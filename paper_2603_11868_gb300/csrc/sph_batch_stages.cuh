@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256, kMinBlocks<T>) kb_build_lists(BatchArgs A
                                                                      const WorkList* wl) {
   for_each_tank_tile(A, wl, [&](int t, const Params& P, int i, int end) {
     if (P.use_list)
-      build_lists_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x, B.bud);
+      build_lists_range<D, T>(P, B, tank_kc<T>(A, t), A.tsc + t, i, end, blockDim.x);
   });
 }
 

@@ -326,16 +326,15 @@ int alloc_fluid(sph_ctx* c, size_t n) {
     ok &= k >= d || B.xreb[k];
   }
   B.bud = (float*)A(nn * 4);
-  ok &= B.bud != nullptr;
+  B.brec = A(nn * 4 * ts);
+  ok &= B.bud != nullptr && B.brec != nullptr;
   ok &= B.sigma64 != nullptr;
-  const size_t pbytes = 4 * ts;
-  const size_t sbytes = (d == 3 ? 4 : 2) * ts;
   for (int p = 0; p < 2; ++p) {
-    B.recP[p] = A(nn * pbytes);
-    B.recS[p] = A(nn * sbytes);
+    B.rec[p] = A(nn * (d == 3 ? 8 : 4) * ts);
+    B.rec_s[p] = d == 3 ? nullptr : A(nn * 2 * ts);
     B.keys[p] = (uint32_t*)A(nn * 4);
     B.vals[p] = (uint32_t*)A(nn * 4);
-    ok &= B.recP[p] && B.recS[p] && B.keys[p] && B.vals[p];
+    ok &= B.rec[p] && (d == 3 || B.rec_s[p]) && B.keys[p] && B.vals[p];
   }
   B.recI = c->precision == SPH_MIXED ? A(nn * (d == 3 ? 16 : 8)) : nullptr;
   ok &= c->precision != SPH_MIXED || B.recI;
@@ -1001,9 +1000,9 @@ int sph_get_fields(sph_ctx* c, unsigned mask, double* out) {
       case SPH_F_P:
         // pressure of the last first half-step, kept in the records of buffer 0
         if (d == 3)
-          rc = scatter_out(c, B.recP[0], nullptr, nullptr, isf, 4, 3, 1, par, o);
+          rc = scatter_out(c, B.rec[0], nullptr, nullptr, isf, 8, 3, 1, par, o);
         else
-          rc = scatter_out(c, B.recS[0], nullptr, nullptr, isf, 2, 0, 1, par, o);
+          rc = scatter_out(c, B.rec_s[0], nullptr, nullptr, isf, 2, 0, 1, par, o);
         break;
       case SPH_F_DRHO:
         rc = scatter_out(c, B.drho[par], nullptr, nullptr, isf, 1, 0, 1, par, o);

@@ -173,13 +173,19 @@ struct DevBuffers {
   void* acc[3];     // T, diagnostics
   void* sigma;      // T, diagnostics
   double* sigma64;  // kernel sum of the last summation (transport correction's support test)
-  void* recP[2];    // T4
-  void* recS[2];    // T4 (3D) or T2 (2D)
+  // loop records.  3D: 8 T per slot, the position record (T 0-3) and the
+  // state record (T 4-7) side by side; rec_s unused.  2D: the position
+  // records (4 T per slot) in rec, the state records (2 T) in rec_s.
+  void* rec[2];
+  void* rec_s[2];
   void* recI;       // mixed mode: int4 (3D) / int2 (2D) fixed-point offsets at the rebuild
   uint32_t* nl;     // neighbour lists: entry k of particle i at ((i/32) cap + k) 32 + i%32
   uint32_t* nl_cnt; // list length per particle
   void* xreb[3];  // position of every slot at the last rebuild, record frame (T)
   float* bud;     // drift budget of every slot since the last rebuild
+  // what the list build reads of every slot: Vec4<T> (x, y, z, b), its
+  // record-frame position (2D: z = 0) and drift budget
+  void* brec;
   uint32_t* keys[2];  // sort ping-pong; keys[sorted_buf] holds the sorted keys
   uint32_t* vals[2];
   int sorted_buf;

@@ -37,9 +37,7 @@ struct Rec;
 
 template <class T>
 struct Rec<3, T> {
-  // (x, y, z, p); in buffer 0 from the reorder to the next first half-step
-  // the w slot holds the drift budget instead, which the list build reads
-  using PV = typename Vec4<T>::type;
+  using PV = typename Vec4<T>::type;  // (x, y, z, p)
   using SV = typename Vec4<T>::type;  // (vx, vy, vz, rho)
   __device__ static PV makeP(T x, T y, T z, T vx, T vy, T vz, T p) {
     PV r;
@@ -59,7 +57,6 @@ struct Rec<3, T> {
   __device__ static T vz(const PV&, const SV& b) { return b.z; }
   __device__ static T pres(const PV& a, const SV&) { return a.w; }
   __device__ static T rho(const PV&, const SV& b) { return b.w; }
-  __device__ static void set_rho(SV& b, T r) { b.w = r; }
   __device__ static void set_pos(PV& a, T x, T y, T z) {
     a.x = x; a.y = y; a.z = z;
   }
@@ -87,9 +84,62 @@ struct Rec<2, T> {
   __device__ static T vz(const PV&, const SV&) { return T(0); }
   __device__ static T pres(const PV&, const SV& b) { return b.x; }
   __device__ static T rho(const PV&, const SV& b) { return b.y; }
-  __device__ static void set_rho(SV& b, T r) { b.y = r; }
   __device__ static void set_pos(PV& a, T x, T y, T) {
     a.x = x; a.y = y;
+  }
+};
+
+// Loop records of buffer b.  3D: 8 T per slot, the position record PV in
+// T 0-3 and the state record SV in T 4-7, so a neighbour's two records share
+// one 32-byte sector in the mixed path and the loops that only read a buffer
+// fetch both with one 256-bit gather.  2D: PV (4 T) and SV (2 T) in two
+// arrays; a 2D slot padded to 8 T ran 3% slower on batches of small tanks.
+template <int D, class T>
+struct RecArr {
+  using R = Rec<D, T>;
+  using PV = typename R::PV;
+  using SV = typename R::SV;
+  static constexpr int kStride = D == 3 ? 8 : 4;  // T per slot in rec
+  T* base;
+  SV* sbase;
+  __device__ RecArr(const DevBuffers& B, int b)
+      : base((T*)B.rec[b]), sbase(D == 3 ? nullptr : (SV*)B.rec_s[b]) {}
+  __device__ PV& P(int i) const { return *(PV*)(base + kStride * (size_t)i); }
+  __device__ SV& S(int i) const {
+    if constexpr (D == 3) return *(SV*)(base + 8 * (size_t)i + 4);
+    else return sbase[i];
+  }
+  // the density slot of S (3D: w, 2D: y)
+  __device__ T& rho(int i) const {
+    if constexpr (D == 3) return base[8 * (size_t)i + 7];
+    else return sbase[i].y;
+  }
+  // both records of slot j, from a buffer that no thread of the kernel writes
+  __device__ void gather(int j, PV& p, SV& s) const {
+    if constexpr (D == 3 && std::is_same<T, float>::value) {
+      float a[8];
+      asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+          : "=f"(a[0]), "=f"(a[1]), "=f"(a[2]), "=f"(a[3]), "=f"(a[4]), "=f"(a[5]),
+            "=f"(a[6]), "=f"(a[7])
+          : "l"(base + 8 * (size_t)j));
+      p = make_float4(a[0], a[1], a[2], a[3]);
+      s = make_float4(a[4], a[5], a[6], a[7]);
+    } else {
+      p = P(j);
+      s = S(j);
+    }
+  }
+  // both records of slot i (3D mixed path: one 256-bit store)
+  __device__ void store(int i, const PV& p, const SV& s) const {
+    if constexpr (D == 3 && std::is_same<T, float>::value) {
+      asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                   :: "l"(base + 8 * (size_t)i), "f"(p.x), "f"(p.y), "f"(p.z), "f"(p.w),
+                      "f"(s.x), "f"(s.y), "f"(s.z), "f"(s.w)
+                   : "memory");
+    } else {
+      P(i) = p;
+      S(i) = s;
+    }
   }
 };
 
@@ -436,13 +486,20 @@ __device__ __forceinline__ BudgetArgs budget_args(const Params& P, const DevScal
   return BudgetArgs{(float)span, (float)(g * span), (float)(0.01 * P.h), (float)(0.5 * sc.skin)};
 }
 
+// Build record of a slot: record-frame position and drift budget.
+template <int D, class T>
+__device__ __forceinline__ typename Vec4<T>::type build_rec(T ox, T oy, T oz, T b) {
+  typename Vec4<T>::type r;
+  r.x = ox; r.y = oy; r.z = D == 3 ? oz : T(0); r.w = b;
+  return r;
+}
+
 template <int D, class T>
 __device__ __forceinline__ void reorder_slot(const Params& P, const DevBuffers& B,
                                              const Live<T>& S, const Live<T>& Dd, int k,
                                              uint32_t j, uint32_t key, const BudgetArgs& ba) {
   using R = Rec<D, T>;
-  typename R::PV* recP = (typename R::PV*)B.recP[0];
-  typename R::SV* recS = (typename R::SV*)B.recS[0];
+  const RecArr<D, T> rec(B, 0);
   if (!SPH_DBG_IN(B, j, P.foff, P.foff + P.n)) return;
   {
     double x = S.x0[j], y = S.x1[j], z = D == 3 ? S.x2[j] : 0.0;
@@ -469,9 +526,10 @@ __device__ __forceinline__ void reorder_slot(const Params& P, const DevBuffers& 
     ((T*)B.xreb[0])[k] = ox;
     ((T*)B.xreb[1])[k] = oy;
     if (D == 3) ((T*)B.xreb[2])[k] = oz;
+    ((typename Vec4<T>::type*)B.brec)[k] = build_rec<D, T>(ox, oy, oz, (T)bk);
     T p = (T)(P.c0sq * (rho - P.rho0));
-    recP[k] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, D == 3 ? (T)bk : p);
-    recS[k] = R::makeS((T)vx, (T)vy, (T)vz, (T)rho, p);
+    rec.store(k, R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p),
+              R::makeS((T)vx, (T)vy, (T)vz, (T)rho, p));
     if constexpr (Local<T>::kLocal)
       ((typename FxRec<D>::V*)B.recI)[k] = fx_encode<D>(P, ck, x, y, z);
   }
@@ -483,8 +541,7 @@ template <int D, class T>
 __global__ void k_encode_records(Params P, DevBuffers B) {
   using R = Rec<D, T>;
   const Live<T> S = live<T>(B, B.sc->par);
-  typename R::PV* recP = (typename R::PV*)B.recP[0];
-  typename R::SV* recS = (typename R::SV*)B.recS[0];
+  const RecArr<D, T> rec(B, 0);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
     const double x = S.x0[i], y = S.x1[i], z = D == 3 ? S.x2[i] : 0.0;
     const double vx = S.v0[i], vy = S.v1[i], vz = D == 3 ? S.v2[i] : 0.0;
@@ -492,8 +549,8 @@ __global__ void k_encode_records(Params P, DevBuffers B) {
     T ox, oy, oz;
     Local<T>::enc(P, B.ctab, decode(B.binned[i], P), x, y, z, ox, oy, oz);
     const T p = (T)(P.c0sq * (rho - P.rho0));
-    recP[i] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p);
-    recS[i] = R::makeS((T)vx, (T)vy, (T)vz, (T)rho, p);
+    rec.store(i, R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p),
+              R::makeS((T)vx, (T)vy, (T)vz, (T)rho, p));
   }
 }
 
@@ -723,7 +780,7 @@ template <int D, class T>
 struct PairGeo {
   using R = Rec<D, T>;
   using WR = WallRec<D, T>;
-  const typename R::PV* __restrict__ recP;
+  RecArr<D, T> rec;
   const typename WR::WV* __restrict__ wall;
   T xi, yi, zi;
   T cs;
@@ -751,7 +808,7 @@ struct PairGeo {
       const typename WR::WV pw = wall[j];
       rx = dsub(bx, pw.x); ry = dsub(by, pw.y); rz = dsub(bz, WR::z(pw));
     } else {
-      const typename R::PV pj = recP[j];
+      const typename R::PV pj = rec.P(j);
       rx = dsub(bx, R::px(pj)); ry = dsub(by, R::py(pj)); rz = dsub(bz, R::pz(pj));
     }
   }
@@ -776,21 +833,9 @@ __device__ __forceinline__ T wall_acc_dot(const DevBuffers& B, int j, T rx, T ry
   return aw.x * rx + aw.y * ry + WR::z(aw) * rz;
 }
 
-// Drift budget of fluid slot j for the list build.  In 3D it is the w slot of
-// j's buffer-0 position record (written there by the reorder, or by the list
-// restore with its grown budgets, in place of the pressure that the next
-// first half-step writes), so a candidate costs one gather; 2D position
-// records have no free slot and read the budget array.
-template <int D, class T>
-__device__ __forceinline__ T build_budget(const typename Rec<D, T>::PV& pj,
-                                          const float* __restrict__ bud, int j) {
-  if constexpr (D == 3) return pj.w;
-  else return (T)bud[j];
-}
-
 // List build (right after the rebuild, positions = binned positions): one
 // direct search per particle that records the candidates closer than
-// 2h + skin.  The membership test runs in the pair type on the loop records;
+// 2h + skin.  The membership test runs in the pair type on the build records;
 // its rounding is far below the skin, so the list is a superset of every
 // pair the later loops accept.
 //
@@ -798,15 +843,17 @@ __device__ __forceinline__ T build_budget(const typename Rec<D, T>::PV& pj,
 // tank (the whole fluid for one tank; one tile of a batch), ending with the
 // block-wide reductions; k_* are the one-tank kernels around them.
 // A candidate j enters i's list when closer than 2h + b_i + b_j (b the drift
-// budgets of the rebuild, or larger ones when lists are restored: 3D reads
-// them from the position records, 2D from bud): while no particle leaves its
-// budget, a pair left out stays farther than 2h.
+// budgets of the rebuild, or larger ones when lists are restored): while no
+// particle leaves its budget, a pair left out stays farther than 2h.  Each
+// candidate is one 16-byte gather of its build record (position, budget).
 template <int D, class T>
 __device__ __forceinline__ void build_lists_range(const Params& P, const DevBuffers& B,
                                                   const KC<T>& k, DevScalars* sc, int i, int end,
-                                                  int stride, const float* __restrict__ bud) {
+                                                  int stride) {
   using R = Rec<D, T>;
-  const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
+  using BV = typename Vec4<T>::type;
+  const BV* __restrict__ brec = (const BV*)B.brec;
+  const RecArr<D, T> rec(B, 0);
   const uint32_t* __restrict__ keys = B.binned;
   const T two_h = (T)(2.0 * P.h);
   const T bw = (T)sc->wall_budget;
@@ -814,20 +861,21 @@ __device__ __forceinline__ void build_lists_range(const Params& P, const DevBuff
   int overflow = 0;
   for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
-    const typename R::PV pi = recP[i];
-    PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
-                    R::pz(pi), k.cs};
+    const BV pi = brec[i];
+    PairGeo<D, T> G{rec, (const typename WallRec<D, T>::WV*)B.wallP, pi.x, pi.y, pi.z, k.cs};
     ListWriter L{B.nl, P.list_cap, i, 0, 0};
-    const T ri = two_h + build_budget<D, T>(pi, bud, i);
+    const T ri = two_h + pi.w;
     visit_neighbours<D>(P, B, ci, i, false, [&](int j, int dx, int dy, int dz, bool w, auto) {
       T rx, ry, rz, bj;
       if (w) {
         G.rel_wall(G.wall[j], dx, dy, dz, rx, ry, rz);
         bj = bw;
       } else {
-        const typename R::PV pj = recP[j];
-        G.rel_rec(pj, dx, dy, dz, rx, ry, rz);
-        bj = build_budget<D, T>(pj, bud, j);
+        const BV pj = brec[j];
+        rx = dsub(shifted<T>(G.xi, dx, G.cs), pj.x);
+        ry = dsub(shifted<T>(G.yi, dy, G.cs), pj.y);
+        rz = dsub(shifted<T>(G.zi, dz, G.cs), pj.z);
+        bj = pj.w;
       }
       const T rl = (ri + bj) * grow;
       if (r2_of(rx, ry, rz) < rl * rl && (w || j != i))
@@ -841,12 +889,11 @@ __device__ __forceinline__ void build_lists_range(const Params& P, const DevBuff
 
 template <int D, class T>
 __global__ void __launch_bounds__(256, kMinBlocks<T>) k_build_lists(Params P, DevBuffers B, KC<T> k,
-                                                                    int gated,
-                                                                    const float* bud = nullptr) {
+                                                                    int gated) {
   DevScalars* sc = B.sc;
   if (!P.use_list || (gated && !sc->new_adv)) return;
   build_lists_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
-                          gridDim.x * blockDim.x, bud ? bud : B.bud);
+                          gridDim.x * blockDim.x);
 }
 
 // Density from the kernel sum: the free-surface clamp rho0 max(sigma/sigma0, 1),
@@ -883,13 +930,12 @@ __device__ __forceinline__ void density_summation_range(const Params& P, const D
   using R = Rec<D, T>;
   const bool use_list = list_ok(P, sc, sc->drift_bad_p, sc->t_reb);
   double* rho_live = sc->par ? B.rho[1] : B.rho[0];
-  const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
-  typename R::SV* recS = (typename R::SV*)B.recS[0];
+  const RecArr<D, T> rec(B, 0);
   const uint32_t* __restrict__ keys = B.binned;
   for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
-    const typename R::PV pi = recP[i];
-    PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
+    const typename R::PV pi = rec.P(i);
+    PairGeo<D, T> G{rec, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
                     R::pz(pi), k.cs};
     T sig = T(0);
     bool self_done = false;
@@ -908,9 +954,7 @@ __device__ __forceinline__ void density_summation_range(const Params& P, const D
     const double rho = reinit_density(P, (double)sig, rho_live[i]);
     if (P.variant & kVariantTransport) B.sigma64[i] = (double)sig;
     rho_live[i] = rho;
-    typename R::SV s = recS[i];
-    R::set_rho(s, (T)rho);
-    recS[i] = s;
+    rec.rho(i) = (T)rho;
     if (P.diag) ((T*)B.sigma)[i] = sig;
   }
 }
@@ -952,7 +996,7 @@ __device__ __forceinline__ void density_summation_fx_range(const Params& P, cons
   double* rho_live = sc->par ? B.rho[1] : B.rho[0];
   const FV* __restrict__ rec = (const FV*)B.recI;
   const FV* __restrict__ wrec = (const FV*)B.wallI;
-  typename R::SV* recS = (typename R::SV*)B.recS[0];
+  const RecArr<D, float> lrec(B, 0);
   const uint32_t* __restrict__ keys = B.binned;
   const unsigned long long cut2 = 1ull << (2 * kFxShift);
   for (; i < end; i += stride) {
@@ -974,9 +1018,7 @@ __device__ __forceinline__ void density_summation_fx_range(const Params& P, cons
     const double rho = reinit_density(P, sigma, rho_live[i]);
     if (P.variant & kVariantTransport) B.sigma64[i] = sigma;
     rho_live[i] = rho;
-    typename R::SV s = recS[i];
-    R::set_rho(s, (float)rho);
-    recS[i] = s;
+    lrec.rho(i) = (float)rho;
     if (P.diag) ((float*)B.sigma)[i] = (float)sigma;
   }
 }
@@ -1006,8 +1048,7 @@ __device__ __forceinline__ void transport_range(const Params& P, const DevBuffer
                                      const ShiftTable* tab) {
   using R = Rec<D, T>;
   const bool use_list = list_ok(P, sc, sc->drift_bad_p, sc->t_reb);
-  const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
-  const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
+  const RecArr<D, T> rec(B, 0);
   const uint32_t* __restrict__ keys = B.binned;
   T* d0 = (T*)B.aprior[0];
   T* d1 = (T*)B.aprior[1];
@@ -1018,13 +1059,20 @@ __device__ __forceinline__ void transport_range(const Params& P, const DevBuffer
     T gx = 0, gy = 0, gz = 0;
     if (B.sigma64[i] >= 0.95 * P.sigma0) {
       const Cell ci = decode(keys[i], P);
-      const typename R::PV pi = recP[i];
-      PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
+      const typename R::PV pi = rec.P(i);
+      PairGeo<D, T> G{rec, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
                       R::pz(pi), k.cs};
       visit_neighbours<D, Local<T>::kLocal>(
           P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w, auto may_self) {
         T rx, ry, rz;
-        G.rel(j, dx, dy, dz, w, rx, ry, rz);
+        typename R::PV pj;
+        typename R::SV sj;
+        if (w) {
+          G.rel_wall(G.wall[j], dx, dy, dz, rx, ry, rz);
+        } else {
+          rec.gather(j, pj, sj);
+          G.rel_rec(pj, dx, dy, dz, rx, ry, rz);
+        }
         const T r2 = r2_of(rx, ry, rz);
         if (!(r2 < k.r2max) || (may_self && !w && j == i)) return;
         const T r = sqrt(r2);
@@ -1032,8 +1080,7 @@ __device__ __forceinline__ void transport_range(const Params& P, const DevBuffer
         if (w) {
           f = wallV * wendland_dr(k, r) / r;
         } else {
-          const typename R::PV pj = recP[j];
-          f = div_t(k.m, R::rho(pj, recS[j])) * wendland_dr(k, r) / r;
+          f = div_t(k.m, R::rho(pj, sj)) * wendland_dr(k, r) / r;
         }
         gx += f * rx;
         gy += f * ry;
@@ -1066,7 +1113,7 @@ __device__ __forceinline__ void transport_apply_range(const Params& P, const Dev
                                                       int stride) {
   using R = Rec<D, T>;
   const Live<T> S = live<T>(B, sc->par);
-  typename R::PV* recP = (typename R::PV*)B.recP[0];
+  const RecArr<D, T> rec(B, 0);
   const uint32_t* __restrict__ keys = B.binned;
   const T* d0 = (const T*)B.aprior[0];
   const T* d1 = (const T*)B.aprior[1];
@@ -1081,9 +1128,9 @@ __device__ __forceinline__ void transport_apply_range(const Params& P, const Dev
     T ox, oy, oz;
     Local<T>::enc(P, B.ctab, decode(keys[i], P), x, y, z, ox, oy, oz);
     drift |= drifted<D, T>(B, i, ox, oy, oz);
-    typename R::PV p = recP[i];
+    typename R::PV p = rec.P(i);
     R::set_pos(p, ox, oy, oz);
-    recP[i] = p;
+    rec.P(i) = p;
   }
   // shifted positions, read by the viscous loop: outside a budget -> no lists
   flag_drift(&sc->drift_bad_p, drift);
@@ -1108,8 +1155,7 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
                                      const ShiftTable* tab) {
   using R = Rec<D, T>;
   const bool use_list = list_ok(P, sc, sc->drift_bad_p, sc->t_reb);
-  const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
-  const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
+  const RecArr<D, T> rec(B, 0);
   const uint32_t* __restrict__ keys = B.binned;
   T* ap0 = (T*)B.aprior[0];
   T* ap1 = (T*)B.aprior[1];
@@ -1118,9 +1164,10 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
   const bool moving = (P.variant & kVariantMovingWall) != 0;
   for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
-    const typename R::PV pi = recP[i];
-    const typename R::SV si = recS[i];
-    PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
+    typename R::PV pi;
+    typename R::SV si;
+    rec.gather(i, pi, si);
+    PairGeo<D, T> G{rec, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
                     R::pz(pi), k.cs};
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     T ax = 0, ay = 0, az = 0;
@@ -1128,7 +1175,14 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
                      Local<T>::kLocal && kShiftBits<D>>(
         P, B, ci, i, use_list, [&](int j, auto dx, auto dy, auto dz, bool w, auto may_self) {
       T rx, ry, rz;
-      G.rel(j, dx, dy, dz, w, rx, ry, rz);
+      typename R::PV pj;
+      typename R::SV sj;
+      if (w) {
+        G.rel_wall(G.wall[j], dx, dy, dz, rx, ry, rz);
+      } else {
+        rec.gather(j, pj, sj);
+        G.rel_rec(pj, dx, dy, dz, rx, ry, rz);
+      }
       const T r2 = r2_of(rx, ry, rz);
       if (!(r2 < k.r2max) || (may_self && !w && j == i)) return;
       const T r = r2 * inv_sqrt_t(r2);
@@ -1149,8 +1203,6 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
         ay += coef * uy;
         az += coef * uz;
       } else {
-        const typename R::PV pj = recP[j];
-        const typename R::SV sj = recS[j];
         const T coef = div_t(k.m, R::rho(pj, sj)) * g;
         ax += coef * (vxi - R::vx(pj, sj));
         ay += coef * (vyi - R::vy(pj, sj));
@@ -1184,8 +1236,7 @@ __device__ __forceinline__ void half1_range(const Params& P, const DevBuffers& B
   const double dt = sc->dt_ac;
   const double hdt = 0.5 * dt;
   const uint32_t* __restrict__ keys = B.binned;
-  typename R::PV* recP = (typename R::PV*)B.recP[0];
-  typename R::SV* recS = (typename R::SV*)B.recS[0];
+  const RecArr<D, T> rec(B, 0);
   const Live<T> S = live<T>(B, par);
   int drift = 0;
   for (; i < end; i += stride) {
@@ -1201,8 +1252,8 @@ __device__ __forceinline__ void half1_range(const Params& P, const DevBuffers& B
     if (D == 3) S.x2[i] = z;
     T ox, oy, oz;
     Local<T>::enc(P, B.ctab, decode(keys[i], P), x, y, z, ox, oy, oz);
-    recP[i] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, (T)p);
-    recS[i] = R::makeS((T)vx, (T)vy, (T)vz, (T)rho, (T)p);
+    rec.store(i, R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, (T)p),
+              R::makeS((T)vx, (T)vy, (T)vz, (T)rho, (T)p));
     drift |= drifted<D, T>(B, i, ox, oy, oz);
   }
   // positions the pressure loop reads: outside a budget -> no lists for it
@@ -1239,10 +1290,7 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
   const double hdt = 0.5 * dt;
   const bool use_list =
       list_ok(P, sc, sc->drift_bad_p, sc->t0 + hdt);
-  const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[0];
-  const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[0];
-  typename R::PV* outP = (typename R::PV*)B.recP[1];
-  typename R::SV* outS = (typename R::SV*)B.recS[1];
+  const RecArr<D, T> rec(B, 0), out(B, 1);
   const uint32_t* __restrict__ keys = B.binned;
   const T* ap0 = (const T*)B.aprior[0];
   const T* ap1 = (const T*)B.aprior[1];
@@ -1252,9 +1300,10 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
   int bad = 0, drift = 0;
   for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
-    const typename R::PV pi = recP[i];
-    const typename R::SV si = recS[i];
-    PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
+    typename R::PV pi;
+    typename R::SV si;
+    rec.gather(i, pi, si);
+    PairGeo<D, T> G{rec, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
                     R::pz(pi), k.cs};
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     const T p_i = R::pres(pi, si), rho_i = R::rho(pi, si);
@@ -1267,8 +1316,7 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
       if (w) {
         G.rel_wall(G.wall[j], dx, dy, dz, rx, ry, rz);
       } else {
-        pj = recP[j];
-        sj = recS[j];  // issued together with pj: both are needed once accepted
+        rec.gather(j, pj, sj);
         G.rel_rec(pj, dx, dy, dz, rx, ry, rz);
       }
       const T r2 = r2_of(rx, ry, rz);
@@ -1336,8 +1384,8 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
     vmax2 = s2 > vmax2 ? s2 : vmax2;
     T ox, oy, oz;
     Local<T>::enc(P, B.ctab, ci, x, y, z, ox, oy, oz);
-    outP[i] = R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p_i);
-    outS[i] = R::makeS((T)vx, (T)vy, (T)vz, rho_i, p_i);
+    out.store(i, R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p_i),
+              R::makeS((T)vx, (T)vy, (T)vz, rho_i, p_i));
     drift |= drifted<D, T>(B, i, ox, oy, oz);
   }
   vmax2 = warp_max(vmax2);
@@ -1374,16 +1422,16 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
   const double hdt = 0.5 * sc->dt_ac;
   const bool use_list =
       list_ok(P, sc, sc->drift_bad_r, sc->t0 + 2.0 * hdt);
-  const typename R::PV* __restrict__ recP = (const typename R::PV*)B.recP[1];
-  const typename R::SV* __restrict__ recS = (const typename R::SV*)B.recS[1];
+  const RecArr<D, T> rec(B, 1);
   const uint32_t* __restrict__ keys = B.binned;
   const Live<T> S = live<T>(B, par);
   int bad = 0;
   for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
-    const typename R::PV pi = recP[i];
-    const typename R::SV si = recS[i];
-    PairGeo<D, T> G{recP, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
+    typename R::PV pi;
+    typename R::SV si;
+    rec.gather(i, pi, si);
+    PairGeo<D, T> G{rec, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
                     R::pz(pi), k.cs};
     const T vxi = R::vx(pi, si), vyi = R::vy(pi, si), vzi = R::vz(pi, si);
     const T p_i = R::pres(pi, si), rho_i = R::rho(pi, si);
@@ -1397,8 +1445,7 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
       if (w) {
         G.rel_wall(G.wall[j], dx, dy, dz, rx, ry, rz);
       } else {
-        pj = recP[j];
-        sj = recS[j];
+        rec.gather(j, pj, sj);
         G.rel_rec(pj, dx, dy, dz, rx, ry, rz);
       }
       const T r2 = r2_of(rx, ry, rz);
@@ -1749,7 +1796,7 @@ void enqueue_advection_t(const StageArgs& a, cudaStream_t s) {
 // A list's sums depend only on the pairs within 2h, visited in candidate
 // order: the same sums as the lists of the rebuild.
 template <int D, class T>
-__global__ void k_restore_budgets(Params P, DevBuffers B, float* grown) {
+__global__ void k_restore_budgets(Params P, DevBuffers B) {
   const Live<T> S = live<T>(B, B.sc->par);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
     T ox, oy, oz;
@@ -1759,8 +1806,9 @@ __global__ void k_restore_budgets(Params P, DevBuffers B, float* grown) {
     const double dy = (double)oy - (double)((const T*)B.xreb[1])[i];
     const double dz = D == 3 ? (double)oz - (double)((const T*)B.xreb[2])[i] : 0.0;
     // b + d with a margin for the record frame's rounding, rounded up
-    grown[i] = __double2float_ru(1.001 * ((double)B.bud[i] + sqrt(dx * dx + dy * dy + dz * dz)));
-    if constexpr (D == 3) ((typename Rec<D, T>::PV*)B.recP[0])[i].w = (T)grown[i];
+    const float grown =
+        __double2float_ru(1.001 * ((double)B.bud[i] + sqrt(dx * dx + dy * dy + dz * dz)));
+    ((typename Vec4<T>::type*)B.brec)[i] = build_rec<D, T>(ox, oy, oz, (T)grown);
   }
 }
 
@@ -1771,11 +1819,10 @@ void enqueue_restore_lists_t(const StageArgs& a, cudaStream_t s) {
   if (!P.use_list || P.n <= 0) return;
   const int gs = grid_for(P.n, L.block_stream, L.blocks_stream);
   k_encode_records<D, T><<<gs, L.block_stream, 0, s>>>(P, a.B);
-  // budgets b + (drift so far) in the summation scratch
-  float* grown = (float*)a.B.sigma;
-  k_restore_budgets<D, T><<<gs, L.block_stream, 0, s>>>(P, a.B, grown);
+  // build records: current positions, budgets b + (drift so far)
+  k_restore_budgets<D, T><<<gs, L.block_stream, 0, s>>>(P, a.B);
   k_build_lists<D, T><<<grid_for(P.n, L.block_loop, L.blocks_loop), L.block_loop, 0, s>>>(
-      P, a.B, make_kc<T>(P), 0, grown);
+      P, a.B, make_kc<T>(P), 0);
 }
 
 template <int D, class T>

@@ -694,6 +694,19 @@ __device__ __forceinline__ void walk_list(const Params& P, const DevBuffers& B,
   }
 }
 
+// Rows 0 .. n-1 of the list block of a group of 32 slots (128 bytes a row,
+// group base `g`), n the longest list of the warp's active lanes, fetched into
+// L2 with one bulk prefetch issued by the lowest active lane before the walk:
+// the walk's row loads then wait for L2 rather than DRAM.  A hint only (no
+// completion to wait for); the rows lie inside the group's list_cap rows.
+__device__ __forceinline__ void prefetch_list_rows(const uint32_t* g, int n) {
+  const unsigned am = __activemask();
+  const int mx = __reduce_max_sync(am, n);
+  if ((int)(threadIdx.x & 31) == __ffs(am) - 1 && mx > 0)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g), "r"(mx * 128)
+                 : "memory");
+}
+
 // Visit the candidates of target i either through its list or through the
 // 3^D cells: every fluid candidate (cells dz, dy, dx; ascending index), then
 // every wall candidate in the same cell order.  v(j, dx, dy, dz, wall) does
@@ -712,6 +725,7 @@ __device__ __forceinline__ void visit_neighbours(const Params& P, const DevBuffe
     const int nf = (int)(c & 0xFFFFu);
     const int nt = nf + (int)(c >> 16);
     const uint32_t* __restrict__ e = B.nl + nl_slot(i, 0, P.list_cap);
+    prefetch_list_rows(e - (i & 31), nt);
     walk_list<kTab, kBits, false>(P, B, e, 0, nf, v, tab);
     walk_list<kTab, kBits, true>(P, B, e, nf, nt, v, tab);
     return;

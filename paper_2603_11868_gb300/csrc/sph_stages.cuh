@@ -377,27 +377,25 @@ __device__ __forceinline__ typename FxRec<D>::V fx_encode(const Params& P, Cell 
 }
 
 // Double-float arithmetic on FP32 (value = hi + lo), built from the error-free
-// transformations TwoSum (Knuth) and TwoProduct with a fused multiply-add
-// (Dekker / Ogita-Rump-Oishi); additions carry no multiplications, so no
-// contraction can change them.
+// transformations FastTwoSum (Dekker) and TwoProduct with a fused
+// multiply-add (Dekker / Ogita-Rump-Oishi); additions carry no multiplications
+// other than by powers of two, so no contraction can change them.
 struct dfl {
   float hi, lo;
 };
-__device__ __forceinline__ dfl two_sum(float a, float b) {
-  float s = a + b;
-  float bb = s - a;
-  float e = (a - (s - bb)) + (b - bb);
-  return {s, e};
-}
 __device__ __forceinline__ dfl fast_two_sum(float a, float b) {  // |a| >= |b|
   float s = a + b;
   float e = b - (s - a);
   return {s, e};
 }
-__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
-  dfl s = two_sum(a.hi, b.hi);
-  s.lo += a.lo + b.lo;
-  return fast_two_sum(s.hi, s.lo);
+// a + b for a running sum a with |a.hi| >= |b.hi| (a sum of non-negative
+// terms that starts at the largest one): the rounding error of the high
+// parts is exact (fast two-sum) and joins the low part, which is
+// renormalised once at the end (fast_two_sum(a.hi, a.lo)).
+__device__ __forceinline__ dfl df_acc(dfl a, dfl b) {
+  const float s = a.hi + b.hi;
+  const float e = b.hi - (s - a.hi);
+  return {s, a.lo + (e + b.lo)};
 }
 __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
   float p = a.hi * b.hi;
@@ -412,23 +410,29 @@ __device__ __forceinline__ dfl df_sqr(dfl a) {
   return fast_two_sum(p, e);
 }
 
-// Wendland C2 shape (1 - q/2)^4 (2q + 1) in double-float from the exact
-// integer r^2 in fixed-point units (R2 = r^2 2^56 / cell^2; the cell edge is
-// 2h, so q = 2 sqrt(R2) 2^-28 = sqrt(R2) 2^-27).
+// Wendland C2 shape (1 - q/2)^4 (2q + 1) = u^4 (5 - 4u), u = 1 - q/2, in
+// double-float from the exact integer r^2 in fixed-point units (R2 = r^2 2^56
+// / cell^2; the cell edge is 2h, so q = 2 sqrt(R2) 2^-28 = sqrt(R2) 2^-27),
+// for R2 < 2^56.  R2 = hi + lo exactly; s = hi y with y the approximate
+// reciprocal square root (relative error about 2^-22), and one Newton step
+// s + (R2 - s^2) y / 2 leaves a relative error near 2^-43 in the root (R2 = 0,
+// coincident particles: y = 1, s = 0, q = 0).  With 0 <= q <= 2 both 1 - q/2
+// and 5 - 4u are exact fast two-sums.
 __device__ __forceinline__ dfl wendland_shape_fx(unsigned long long R2) {
   const float hi = __ull2float_rn(R2);
   const long long rem = (long long)(R2 - (unsigned long long)hi);
   const float lo = (float)rem;
-  const float s = sqrtf(hi);
-  const float e = fmaf(s, s, -hi);  // exact residual of the rounded root
-  const float s_lo = s > 0.0f ? __fdividef(lo - e, 2.0f * s) : 0.0f;
+  const float y = inv_sqrt_t(fmaxf(hi, 1.0f));
+  const float s = hi * y;
+  const float e = fmaf(s, s, -hi);  // s^2 - hi
+  const float s_lo = (lo - e) * (0.5f * y);
   const float qh = s * 0x1p-27f, ql = s_lo * 0x1p-27f;
-  dfl u = two_sum(1.0f, -0.5f * qh);
+  dfl u = fast_two_sum(1.0f, -0.5f * qh);
   u.lo -= 0.5f * ql;
   u = fast_two_sum(u.hi, u.lo);
   const dfl u4 = df_sqr(df_sqr(u));
-  dfl v = two_sum(1.0f, 2.0f * qh);
-  v.lo += 2.0f * ql;
+  dfl v = fast_two_sum(5.0f, -4.0f * u.hi);
+  v.lo -= 4.0f * u.lo;
   v = fast_two_sum(v.hi, v.lo);
   return df_mul(u4, v);
 }
@@ -922,21 +926,10 @@ __device__ __forceinline__ double reinit_density(const Params& P, double sigma, 
   return rho_sum + (excess > 0.0 ? excess : 0.0) * P.rho0 / rho_prev;
 }
 
-// Whether candidate (dx, dy, dz, wall, j) comes after particle i itself in the
-// candidate order of direct search (every fluid candidate by cells dz, dy, dx
-// and ascending index, then every wall candidate).
-__device__ __forceinline__ bool after_self(int dx, int dy, int dz, bool w, int j, int i) {
-  if (w) return true;
-  if (dz != 0) return dz > 0;
-  if (dy != 0) return dy > 0;
-  if (dx != 0) return dx > 0;
-  return j > i;
-}
-
 // Density summation (FP64 path): reads records P of buffer 0; writes rho
 // (state) and the rho slot of records S of buffer 0.  Self is part of the
-// sum (W(0)); the list holds the other particles in candidate order, so the
-// self term is added where direct search meets it.
+// sum (W(0)) and comes first; direct search skips i where it meets it (a list
+// never holds it), so both visit the other particles in the same order.
 template <int D, class T>
 __device__ __forceinline__ void density_summation_range(const Params& P, const DevBuffers& B,
                                                         const KC<T>& k, DevScalars* sc, int i,
@@ -951,20 +944,15 @@ __device__ __forceinline__ void density_summation_range(const Params& P, const D
     const typename R::PV pi = rec.P(i);
     PairGeo<D, T> G{rec, (const typename WallRec<D, T>::WV*)B.wallP, R::px(pi), R::py(pi),
                     R::pz(pi), k.cs};
-    T sig = T(0);
-    bool self_done = false;
-    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w, auto) {
-      if (use_list && !self_done && after_self(dx, dy, dz, w, j, i)) {
-        sig += wendland(k, T(0));  // self, in its direct-search position
-        self_done = true;
-      }
+    T sig = wendland(k, T(0));
+    visit_neighbours<D>(P, B, ci, i, use_list,
+                        [&](int j, int dx, int dy, int dz, bool w, auto may_self) {
+      if (may_self && !w && j == i) return;
       T rx, ry, rz;
       G.rel(j, dx, dy, dz, w, rx, ry, rz);
       const T r2 = r2_of(rx, ry, rz);
       if (r2 < k.r2max) sig += wendland(k, sqrt(r2));
-      if (!w && j == i) self_done = true;
     });
-    if (!self_done) sig += wendland(k, T(0));
     const double rho = reinit_density(P, (double)sig, rho_live[i]);
     if (P.variant & kVariantTransport) B.sigma64[i] = (double)sig;
     rho_live[i] = rho;
@@ -1016,18 +1004,14 @@ __device__ __forceinline__ void density_summation_fx_range(const Params& P, cons
   for (; i < end; i += stride) {
     const Cell ci = decode(keys[i], P);
     const FV oi = rec[i];
-    dfl sig = {0.0f, 0.0f};
-    bool self_done = false;
-    visit_neighbours<D>(P, B, ci, i, use_list, [&](int j, int dx, int dy, int dz, bool w, auto) {
-      if (use_list && !self_done && after_self(dx, dy, dz, w, j, i)) {
-        sig = df_add(sig, dfl{1.0f, 0.0f});  // self: shape(0) = 1
-        self_done = true;
-      }
+    dfl sig = {1.0f, 0.0f};  // self first: shape(0) = 1, no term is larger
+    visit_neighbours<D>(P, B, ci, i, use_list,
+                        [&](int j, int dx, int dy, int dz, bool w, auto may_self) {
+      if (may_self && !w && j == i) return;
       const unsigned long long R2 = fx_r2<D>(oi, w ? wrec[j] : rec[j], dx, dy, dz);
-      if (R2 < cut2) sig = df_add(sig, wendland_shape_fx(R2));
-      if (!w && j == i) self_done = true;
+      if (R2 < cut2) sig = df_acc(sig, wendland_shape_fx(R2));
     });
-    if (!self_done) sig = df_add(sig, dfl{1.0f, 0.0f});
+    sig = fast_two_sum(sig.hi, sig.lo);
     const double sigma = P.walpha * ((double)sig.hi + (double)sig.lo);
     const double rho = reinit_density(P, sigma, rho_live[i]);
     if (P.variant & kVariantTransport) B.sigma64[i] = sigma;

@@ -421,15 +421,28 @@ __device__ __forceinline__ dfl df_sqr(dfl a) {
 // Wendland C2 shape (1 - q/2)^4 (2q + 1) = u^4 (5 - 4u), u = 1 - q/2, in
 // double-float from the exact integer r^2 in fixed-point units (R2 = r^2 2^56
 // / cell^2; the cell edge is 2h, so q = 2 sqrt(R2) 2^-28 = sqrt(R2) 2^-27),
-// for R2 < 2^56.  R2 = hi + lo exactly; s = hi y with y the approximate
-// reciprocal square root (relative error about 2^-22), and one Newton step
-// s + (R2 - s^2) y / 2 leaves a relative error near 2^-43 in the root (R2 = 0,
-// coincident particles: y = 1, s = 0, q = 0).  With 0 <= q <= 2 both 1 - q/2
-// and 5 - 4u are exact fast two-sums.
+// for R2 < 2^56.  R2 splits into 23-bit limbs l0 + l1 2^23 + l2 2^46, each
+// turned into an exact float by placing it in the mantissa of a power of two
+// (2^23, 2^46, 2^69) and subtracting that power (no integer-to-float
+// conversion: the 64-bit ones measured slow enough to bound the kernel); two
+// fast two-sums give hi + lo = R2 to about 2^-48.  s = hi y with y the
+// approximate reciprocal square root (relative error about 2^-22), and one
+// Newton step s + (R2 - s^2) y / 2 leaves a relative error near 2^-43 in the
+// root (R2 = 0, coincident particles: y = 1, s = 0, q = 0).  With 0 <= q <= 2
+// both 1 - q/2 and 5 - 4u are exact fast two-sums.
 __device__ __forceinline__ dfl wendland_shape_fx(unsigned long long R2) {
-  const float hi = __ull2float_rn(R2);
-  const long long rem = (long long)(R2 - (unsigned long long)hi);
-  const float lo = (float)rem;
+  const uint32_t w0 = (uint32_t)R2, w1 = (uint32_t)(R2 >> 32);
+  const uint32_t l0 = w0 & 0x7FFFFFu;
+  const uint32_t l1 = __funnelshift_r(w0, w1, 23) & 0x7FFFFFu;
+  const uint32_t l2 = w1 >> 14;
+  const float f0 = __uint_as_float(0x4B000000u | l0) - 0x1p23f;  // l0
+  const float f1 = __uint_as_float(0x56800000u | l1) - 0x1p46f;  // l1 2^23
+  const float f2 = __uint_as_float(0x62000000u | l2) - 0x1p69f;  // l2 2^46
+  // exact: f2 is 0 or >= 2^46 > f1, and the partial sum 0 or >= 2^23 > f0
+  const dfl a = fast_two_sum(f2, f1);
+  const dfl b = fast_two_sum(a.hi, f0);
+  const float hi = b.hi;
+  const float lo = b.lo + a.lo;
   const float y = inv_sqrt_t(fmaxf(hi, 1.0f));
   const float s = hi * y;
   const float e = fmaf(s, s, -hi);  // s^2 - hi

@@ -264,6 +264,11 @@ int sync_status(sph_ctx* c, DevScalars* out = nullptr) {
 }
 
 // user-order scatter of one field: out[id[k] * comps + q] = src_q[k * stride + off]
+__global__ void k_iota(uint32_t* a, uint32_t n) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = i;
+}
+
 __global__ void k_scatter_field(const void* s0, const void* s1, const void* s2, int is_float,
                                 int stride, int off, int comps, const uint32_t* __restrict__ id,
                                 int n, double* __restrict__ out) {
@@ -343,6 +348,16 @@ int alloc_fluid(sph_ctx* c, size_t n) {
   // two extra rows of 32 entries: the list walk reads up to two entries past
   // a particle's last one (prefetch), which stays inside the allocation
   B.nl = (uint32_t*)A((warps * (size_t)c->P.list_cap + 2) * 32 * 4);
+  if (B.parts) {
+    B.units = (uint32_t*)A(warps * 4);
+    B.unit_brick = (uint32_t*)A(warps * 4);
+    ok &= B.units && B.unit_brick;
+    // a valid order (identity) until the first rebuild makes the brick order
+    if (B.units) {
+      k_iota<<<(int)((warps + 255) / 256), 256, 0, c->stream>>>(B.units, (uint32_t)warps);
+      CK(cudaGetLastError());
+    }
+  }
   B.nl_cnt = (uint32_t*)A(nn * 4);
   ok &= B.nl && B.nl_cnt;
   const size_t tiles = (nn + kSortTile - 1) / kSortTile;
@@ -444,12 +459,20 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
   c->B.wall_cb = (uint32_t*)dev_alloc(c, ((size_t)P.ncell + 1) * 4, c->fixed_blocks);
   c->B.digit_total = (uint32_t*)dev_alloc(c, ((size_t)1 << kMaxRadixBits) * 4, c->fixed_blocks);
   c->B.u64_io = (unsigned long long*)dev_alloc(c, 8, c->fixed_blocks);
+  if (P.dim == 3 && precision == SPH_MIXED) {
+    const size_t nb = (size_t)brick_count(P);
+    c->B.brick_start = (uint32_t*)dev_alloc(c, (nb + 1) * 4, c->fixed_blocks);
+    c->B.brick_fill = (uint32_t*)dev_alloc(c, nb * 4, c->fixed_blocks);
+    c->B.unit_ctr = (uint32_t*)dev_alloc(c, 2 * (size_t)c->L.sms * 4, c->fixed_blocks);
+    c->B.parts = c->L.sms;
+  }
   double* ctab = nullptr;
   if (precision == SPH_MIXED)
     ctab = (double*)dev_alloc(c, (size_t)(P.nx + P.ny + P.nz) * 8, c->fixed_blocks);
   c->B.ctab = ctab;
   if (!c->B.sc || !c->B.cell_begin || !c->B.wall_cb || !c->B.digit_total || !c->B.u64_io ||
-      (precision == SPH_MIXED && !ctab)) {
+      (precision == SPH_MIXED && !ctab) ||
+      (c->B.parts && (!c->B.brick_start || !c->B.brick_fill || !c->B.unit_ctr))) {
     sph_destroy(c);
     return SPH_E_OOM;
   }
@@ -800,6 +823,7 @@ int sph_checkpoint_load(sph_ctx* c, const void* buf, size_t bytes) {
   CK(cudaMemcpyAsync(B.sc, &hs, sizeof(hs), cudaMemcpyHostToDevice, c->stream));
   launch_cell_offsets(B.keys[B.sorted_buf], (int)n, c->P.ncell, B.cell_begin, B.sc, 0, 0,
                       c->stream);
+  if (c->precision == SPH_MIXED) enqueue_units_mixed(args(c), c->stream);
   // translating walls: binned at the saved rebuild time, moved to the saved time
   if ((c->P.variant & kVariantTranslatingWall) && c->P.nw > 0) {
     if (c->precision == SPH_FP64)

@@ -162,6 +162,12 @@ struct Vec2<double> {
   using type = double2;
 };
 
+// Bricks of 4 x 4 x 4 cells over a one-tank grid (the processing order of
+// the 3D mixed relaxation loops).
+inline __host__ __device__ uint32_t brick_count(const Params& P) {
+  return (uint32_t)(((P.nx + 3) / 4) * ((P.ny + 3) / 4) * ((P.nz + 3) / 4));
+}
+
 // Raw device pointers of one context (all owned by the context).
 struct DevBuffers {
   double* x[2][3];
@@ -186,6 +192,16 @@ struct DevBuffers {
   // what the list build reads of every slot: Vec4<T> (x, y, z, b), its
   // record-frame position (2D: z = 0) and drift budget
   void* brec;
+  // processing order of the one-tank 3D mixed relaxation loops: the 32-slot
+  // groups sorted by brick of 4 x 4 x 4 cells and split into `parts` equal
+  // runs, each taken group by group by the warps of one multiprocessor (a
+  // warp that finds its run done takes groups from the others)
+  uint32_t* units;        // ceil(n / 32) group indices, brick order
+  uint32_t* unit_brick;   // brick of every group at the last rebuild
+  uint32_t* brick_start;  // nbrick + 1: counts, then starts
+  uint32_t* brick_fill;   // nbrick
+  uint32_t* unit_ctr;     // 2 x parts claim counters (pressure, relaxation)
+  int parts;
   uint32_t* keys[2];  // sort ping-pong; keys[sorted_buf] holds the sorted keys
   uint32_t* vals[2];
   int sorted_buf;
@@ -379,6 +395,9 @@ void enqueue_wall_rebin_mixed(const StageArgs& a, cudaStream_t s, int at_rebuild
 // its stored skin (the loops then give the sums of the uninterrupted run).
 void enqueue_restore_lists_fp64(const StageArgs& a, cudaStream_t s);
 void enqueue_restore_lists_mixed(const StageArgs& a, cudaStream_t s);
+// Brick processing order of the 3D mixed loops from the binned keys as they
+// stand (a restored state; the rebuild makes it otherwise).
+void enqueue_units_mixed(const StageArgs& a, cudaStream_t s);
 
 // --- neighbour search (sph_nsearch.cu), precision independent
 // keys from positions x[par] (or an explicit coordinate set), vals = iota

@@ -63,6 +63,10 @@ void enqueue_wall_rebin_mixed(const StageArgs& a, cudaStream_t s, int at_rebuild
     stages::enqueue_wall_rebin_t<3, float>(a, s, 0, when);
 }
 
+void enqueue_units_mixed(const StageArgs& a, cudaStream_t s) {
+  if (a.P.dim == 3) stages::enqueue_units<3, float>(a, s, 0);
+}
+
 void enqueue_restore_lists_mixed(const StageArgs& a, cudaStream_t s) {
   if (a.P.dim == 2)
     stages::enqueue_restore_lists_t<2, float>(a, s);

@@ -593,6 +593,89 @@ __global__ void k_reorder(Params P, DevBuffers B, int gated) {
 }
 
 // ---------------------------------------------------------------------------
+// Processing order of the one-tank 3D mixed relaxation loops, made at every
+// rebuild: the 32-slot groups (a warp's slots and list block) sorted by the
+// brick of 4 x 4 x 4 cells that holds each group's first slot.  The warps of
+// one multiprocessor then walk neighbouring bricks together, so the records
+// they gather stay in its L1 longer than along the cell rows of the storage
+// order.  The order of the groups within a brick is left to the atomics: the
+// loops give the same results in any order.
+__device__ __forceinline__ uint32_t brick_of(const Cell& c, const Params& P) {
+  const int nbx = (P.nx + 3) >> 2, nby = (P.ny + 3) >> 2;
+  return (uint32_t)((c.x >> 2) + nbx * ((c.y >> 2) + nby * (c.z >> 2)));
+}
+
+template <int D>
+__global__ void k_units_clear(Params P, DevBuffers B, int gated) {
+  if (gated && !B.sc->new_adv) return;
+  const uint32_t nb = brick_count(P);
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= nb; b += gridDim.x * blockDim.x) {
+    B.brick_start[b] = 0;
+    if (b < nb) B.brick_fill[b] = 0;
+  }
+}
+
+template <int D>
+__global__ void k_units_count(Params P, DevBuffers B, int gated) {
+  if (gated && !B.sc->new_adv) return;
+  const int ng = (P.n + 31) >> 5;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+    const uint32_t b = brick_of(decode(B.binned[g * 32], P), P);
+    B.unit_brick[g] = b;
+    atomicAdd(&B.brick_start[b], 1u);
+  }
+}
+
+// exclusive scan of the brick counts in place (one block of kUnitScanThreads)
+constexpr int kUnitScanThreads = 1024;
+template <int D>
+__global__ void __launch_bounds__(kUnitScanThreads) k_units_scan(Params P, DevBuffers B, int gated) {
+  if (gated && !B.sc->new_adv) return;
+  __shared__ uint32_t part[kUnitScanThreads / 32];
+  const uint32_t nb = brick_count(P);
+  const uint32_t chunk = (nb + kUnitScanThreads - 1) / kUnitScanThreads;
+  const uint32_t b0 = threadIdx.x * chunk;
+  const uint32_t b1 = min(b0 + chunk, nb);
+  uint32_t local = 0;
+  for (uint32_t b = b0; b < b1; ++b) local += B.brick_start[b];
+  // block-wide exclusive scan of the per-thread sums
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(kFullMask, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) part[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = part[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(kFullMask, w, o);
+      if (lane >= o) w += v;
+    }
+    part[lane] = w;
+  }
+  __syncthreads();
+  uint32_t run = incl - local + (warp > 0 ? part[warp - 1] : 0u);
+  for (uint32_t b = b0; b < b1; ++b) {
+    const uint32_t c = B.brick_start[b];
+    B.brick_start[b] = run;
+    run += c;
+  }
+  if (threadIdx.x == kUnitScanThreads - 1) B.brick_start[nb] = run;
+}
+
+template <int D>
+__global__ void k_units_scatter(Params P, DevBuffers B, int gated) {
+  if (gated && !B.sc->new_adv) return;
+  const int ng = (P.n + 31) >> 5;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+    const uint32_t b = B.unit_brick[g];
+    B.units[B.brick_start[b] + atomicAdd(&B.brick_fill[b], 1u)] = (uint32_t)g;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Neighbour lists.  Direct search tests every particle of the 3^D cells
 // (about 475 in 3D) for about 81 accepted neighbours, and the pair arithmetic
 // then runs with few lanes of a warp active.  Right after each rebuild every
@@ -1281,6 +1364,9 @@ __device__ __forceinline__ void half1_range(const Params& P, const DevBuffers& B
 
 template <int D, class T>
 __global__ void k_half1(Params P, DevBuffers B) {
+  // claim counters of this step's relaxation loops (brick order)
+  if (B.units && blockIdx.x == 0)
+    for (int t = threadIdx.x; t < 2 * B.parts; t += blockDim.x) B.unit_ctr[t] = 0;
   half1_range<D, T>(P, B, B.sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
                     gridDim.x * blockDim.x);
 }
@@ -1295,14 +1381,73 @@ inline bool wall_vel_code(int variant) {
   return (variant & kVariantMovingWall) != 0 || D == 3;
 }
 
+// Slots one thread of a loop body visits: i, i + stride, ... < end.
+struct StrideSlots {
+  int i, end, stride;
+  template <class F>
+  __device__ __forceinline__ void each(F&& f) const {
+    for (int k = i; k < end; k += stride) f(k);
+  }
+};
+
+__device__ __forceinline__ int sm_id() {
+  int r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+
+// Slots of the groups in brick order (DevBuffers::units): the order is cut
+// into `parts` runs of near-equal length; a warp claims one group at a time
+// (lane 0, one atomic) from the run of its multiprocessor, and when that is
+// done looks for any run with groups left (its lanes test 32 runs per load),
+// so every group is processed once whatever the multiprocessor numbering.
+// ctr holds the runs' claim counters (zeroed before the launch).
+struct UnitSlots {
+  const uint32_t* units;
+  uint32_t* ctr;
+  int parts, ngroups, end;
+  template <class F>
+  __device__ __forceinline__ void each(F&& f) const {
+    const int lane = threadIdx.x & 31;
+    const int base = ngroups / parts, rem = ngroups - base * parts;
+    int p = sm_id() % parts;
+    for (;;) {
+      const int u0 = p * base + min(p, rem);
+      const int size = base + (p < rem ? 1 : 0);
+      for (;;) {
+        int u = size;
+        if (lane == 0 && *(volatile uint32_t*)(ctr + p) < (uint32_t)size)
+          u = (int)atomicAdd(ctr + p, 1u);
+        u = __shfl_sync(kFullMask, u, 0);
+        if (u >= size) break;
+        const uint32_t g = units[u0 + u];
+        const int i = (int)(g * 32u) + lane;
+        if (g < (uint32_t)ngroups && i < end) f(i);
+      }
+      // another run with unclaimed groups, if any
+      int next = -1;
+      for (int r = 0; r < parts - 1 && next < 0; r += 32) {
+        int q = p + 1 + r + lane;
+        if (q >= parts) q -= parts;
+        const bool open = r + lane < parts - 1 &&
+                          *(volatile uint32_t*)(ctr + q) < (uint32_t)(base + (q < rem ? 1 : 0));
+        const unsigned m = __ballot_sync(kFullMask, open);
+        if (m) next = __shfl_sync(kFullMask, q, __ffs(m) - 1);
+      }
+      if (next < 0) return;
+      p = next;
+    }
+  }
+};
+
 // Riemann pressure relaxation + kick + the drift that opens the density stage.
 // Reads records of buffer 0, writes records of buffer 1.  kWallVel compiles
 // in the (run-time checked) wall-velocity term of sliding walls
 // (kVariantMovingWall); see wall_vel_code() for when it is left out.
-template <int D, class T, bool kWallVel = true, bool kAccel = false>
-__device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers& B, const KC<T>& k,
-                                               DevScalars* sc, int i, int end, int stride,
-                                     const ShiftTable* tab) {
+template <int D, class T, bool kWallVel = true, bool kAccel = false, class Slots>
+__device__ __forceinline__ void pressure_slots(const Params& P, const DevBuffers& B, const KC<T>& k,
+                                               DevScalars* sc, const Slots& slots,
+                                               const ShiftTable* tab) {
   using R = Rec<D, T>;
   const int par = sc->par;
   const double dt = sc->dt_ac;
@@ -1317,7 +1462,7 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
   const Live<T> S = live<T>(B, par);
   double vmax2 = 0.0;
   int bad = 0, drift = 0;
-  for (; i < end; i += stride) {
+  slots.each([&](const int i) {
     const Cell ci = decode(keys[i], P);
     typename R::PV pi;
     typename R::SV si;
@@ -1406,7 +1551,7 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
     out.store(i, R::makeP(ox, oy, oz, (T)vx, (T)vy, (T)vz, p_i),
               R::makeS((T)vx, (T)vy, (T)vz, rho_i, p_i));
     drift |= drifted<D, T>(B, i, ox, oy, oz);
-  }
+  });
   vmax2 = warp_max(vmax2);
   __shared__ double wm[32];
   __syncthreads();  // the previous body call of this block has read wm
@@ -1421,21 +1566,32 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
   }
 }
 
-template <int D, class T, bool kWallVel, bool kAccel = false>
-__global__ void __launch_bounds__(256, kMinBlocksPres<D, T>) k_pressure(Params P, DevBuffers B, KC<T> k) {
+template <int D, class T, bool kWallVel = true, bool kAccel = false>
+__device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers& B, const KC<T>& k,
+                                               DevScalars* sc, int i, int end, int stride,
+                                               const ShiftTable* tab) {
+  pressure_slots<D, T, kWallVel, kAccel>(P, B, k, sc, StrideSlots{i, end, stride}, tab);
+}
+
+// kUnits: the slots in brick order (one tank, 3D mixed), else strided.
+template <int D, class T, bool kWallVel, bool kAccel = false, bool kUnits = false>
+__global__ void __launch_bounds__(256, kUnits ? 4 : kMinBlocksPres<D, T>) k_pressure(Params P, DevBuffers B, KC<T> k) {
   __shared__ ShiftTable tab;
   if constexpr (Local<T>::kLocal && !kShiftBits<D>) fill_shift_table(tab);
-  pressure_range<D, T, kWallVel, kAccel>(P, B, k, B.sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
-                       gridDim.x * blockDim.x, &tab);
+  if constexpr (kUnits)
+    pressure_slots<D, T, kWallVel, kAccel>(
+        P, B, k, B.sc, UnitSlots{B.units, B.unit_ctr, B.parts, (P.n + 31) >> 5, P.n}, &tab);
+  else
+    pressure_range<D, T, kWallVel, kAccel>(P, B, k, B.sc, blockIdx.x * blockDim.x + threadIdx.x,
+                                           P.n, gridDim.x * blockDim.x, &tab);
 }
 
 // Riemann density relaxation: reads records of buffer 1; drho and rho (state).
 // kWallVel as for the pressure relaxation.
-template <int D, class T, bool kWallVel = true, bool kAccel = false>
-__device__ __forceinline__ void density_relax_range(const Params& P, const DevBuffers& B,
-                                                    const KC<T>& k, DevScalars* sc, int i,
-                                                    int end, int stride,
-                                     const ShiftTable* tab) {
+template <int D, class T, bool kWallVel = true, bool kAccel = false, class Slots>
+__device__ __forceinline__ void density_relax_slots(const Params& P, const DevBuffers& B,
+                                                    const KC<T>& k, DevScalars* sc,
+                                                    const Slots& slots, const ShiftTable* tab) {
   using R = Rec<D, T>;
   const int par = sc->par;
   const double hdt = 0.5 * sc->dt_ac;
@@ -1445,7 +1601,7 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
   const uint32_t* __restrict__ keys = B.binned;
   const Live<T> S = live<T>(B, par);
   int bad = 0;
-  for (; i < end; i += stride) {
+  slots.each([&](const int i) {
     const Cell ci = decode(keys[i], P);
     typename R::PV pi;
     typename R::SV si;
@@ -1503,20 +1659,33 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
     double rho = S.rho[i] + hdt * (double)dr;
     if (!(fabs(rho) <= 1e300)) bad = 1;
     S.rho[i] = rho;
-  }
+  });
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&sc->flags, kFlagNonFinite);
+}
+
+template <int D, class T, bool kWallVel = true, bool kAccel = false>
+__device__ __forceinline__ void density_relax_range(const Params& P, const DevBuffers& B,
+                                                    const KC<T>& k, DevScalars* sc, int i,
+                                                    int end, int stride,
+                                                    const ShiftTable* tab) {
+  density_relax_slots<D, T, kWallVel, kAccel>(P, B, k, sc, StrideSlots{i, end, stride}, tab);
 }
 
 // One tank: block 0 also publishes this step's velocity maximum for the next
 // step's schedule (a batch does that in its schedule kernel).
-template <int D, class T, bool kWallVel, bool kAccel = false>
+template <int D, class T, bool kWallVel, bool kAccel = false, bool kUnits = false>
 __global__ void __launch_bounds__(256, kMinBlocksP<D, T>) k_density_relax(Params P, DevBuffers B, KC<T> k) {
   DevScalars* sc = B.sc;
   __shared__ ShiftTable tab;
   if constexpr (Local<T>::kLocal && !kShiftBits<D>) fill_shift_table(tab);
   if (blockIdx.x == 0 && threadIdx.x == 0) sc->vmax2_cur = sc->vmax2_next;
-  density_relax_range<D, T, kWallVel, kAccel>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
-                            gridDim.x * blockDim.x, &tab);
+  if constexpr (kUnits)
+    density_relax_slots<D, T, kWallVel, kAccel>(
+        P, B, k, sc,
+        UnitSlots{B.units, B.unit_ctr + B.parts, B.parts, (P.n + 31) >> 5, P.n}, &tab);
+  else
+    density_relax_range<D, T, kWallVel, kAccel>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x,
+                                                P.n, gridDim.x * blockDim.x, &tab);
 }
 
 // Wall setup: gather sorted wall positions (double SoA for the parity kernel,
@@ -1717,6 +1886,32 @@ void enqueue_wall_rebin_t(const StageArgs& a, cudaStream_t s, int gated, int whe
   }
 }
 
+// Grid of one resident wave of a loop kernel that takes its work from
+// UnitSlots (blocks of L.block_loop threads on every multiprocessor).
+template <class K>
+int one_wave(K kernel, const LaunchCfg& L) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, L.block_loop, 0) != cudaSuccess ||
+      nb < 1) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  return nb * L.sms;
+}
+
+template <int D, class T>
+void enqueue_units(const StageArgs& a, cudaStream_t s, int gated) {
+  const Params& P = a.P;
+  if (D != 3 || !Local<T>::kLocal || !a.B.units || P.n <= 0) return;
+  const int ng = (P.n + 31) >> 5;
+  const int gs = grid_for(ng, 256, a.L.blocks_stream);
+  k_units_clear<D><<<grid_for((int)brick_count(P) + 1, 256, a.L.blocks_stream), 256, 0, s>>>(P, a.B,
+                                                                                          gated);
+  k_units_count<D><<<gs, 256, 0, s>>>(P, a.B, gated);
+  k_units_scan<D><<<1, kUnitScanThreads, 0, s>>>(P, a.B, gated);
+  k_units_scatter<D><<<gs, 256, 0, s>>>(P, a.B, gated);
+}
+
 template <int D, class T>
 void enqueue_rebuild(const StageArgs& a, cudaStream_t s, int gated, cudaEvent_t* ev) {
   const Params& P = a.P;
@@ -1733,6 +1928,7 @@ void enqueue_rebuild(const StageArgs& a, cudaStream_t s, int gated, cudaEvent_t*
       P, B, gated);
   mark(ev, kStageOffsets, s);
   launch_cell_offsets(B.keys[B.sorted_buf], P.n, P.ncell, B.cell_begin, B.sc, gated, 1, s);
+  enqueue_units<D, T>(a, s, gated);
   if (P.variant & kVariantTranslatingWall) enqueue_wall_rebin_t<D, T>(a, s, gated, kBinAtStepStart);
 }
 
@@ -1776,18 +1972,32 @@ void enqueue_acoustic_t(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev = nu
   mark(ev, kStagePressure, s);
   const bool wall_vel = wall_vel_code<D>(P.variant);
   const bool accel = (P.variant & kVariantAccelWall) != 0;
+  constexpr bool kU = D == 3 && Local<T>::kLocal;  // brick order when B.units is set
+  const bool units = kU && B.units;
   if (accel)
     k_pressure<D, T, true, true><<<gl, L.block_loop, 0, s>>>(P, B, k);
+  else if (wall_vel && units)
+    k_pressure<D, T, true, false, kU><<<one_wave(k_pressure<D, T, true, false, kU>, L), L.block_loop,
+                                        0, s>>>(P, B, k);
   else if (wall_vel)
     k_pressure<D, T, true><<<gl, L.block_loop, 0, s>>>(P, B, k);
+  else if (units)
+    k_pressure<D, T, false, false, kU><<<one_wave(k_pressure<D, T, false, false, kU>, L),
+                                         L.block_loop, 0, s>>>(P, B, k);
   else
     k_pressure<D, T, false><<<gl, L.block_loop, 0, s>>>(P, B, k);
   if (translating) k_wall_move<D, T><<<gw, 256, 0, s>>>(P, B, kMoveFull);
   mark(ev, kStageDensityRelax, s);
   if (accel)
     k_density_relax<D, T, true, true><<<gl, L.block_loop, 0, s>>>(P, B, k);
+  else if (wall_vel && units)
+    k_density_relax<D, T, true, false, kU><<<one_wave(k_density_relax<D, T, true, false, kU>, L),
+                                             L.block_loop, 0, s>>>(P, B, k);
   else if (wall_vel)
     k_density_relax<D, T, true><<<gl, L.block_loop, 0, s>>>(P, B, k);
+  else if (units)
+    k_density_relax<D, T, false, false, kU><<<one_wave(k_density_relax<D, T, false, false, kU>, L),
+                                              L.block_loop, 0, s>>>(P, B, k);
   else
     k_density_relax<D, T, false><<<gl, L.block_loop, 0, s>>>(P, B, k);
   mark(ev, kStages, s);

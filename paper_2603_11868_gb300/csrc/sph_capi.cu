@@ -463,7 +463,7 @@ int sph_create(const sph_domain* domain, double dp, double h, const sph_material
     const size_t nb = (size_t)brick_count(P);
     c->B.brick_start = (uint32_t*)dev_alloc(c, (nb + 1) * 4, c->fixed_blocks);
     c->B.brick_fill = (uint32_t*)dev_alloc(c, nb * 4, c->fixed_blocks);
-    c->B.unit_ctr = (uint32_t*)dev_alloc(c, 2 * (size_t)c->L.sms * 4, c->fixed_blocks);
+    c->B.unit_ctr = (uint32_t*)dev_alloc(c, 5 * (size_t)c->L.sms * 4, c->fixed_blocks);
     c->B.parts = c->L.sms;
   }
   double* ctab = nullptr;

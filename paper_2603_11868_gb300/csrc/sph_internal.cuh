@@ -162,10 +162,14 @@ struct Vec2<double> {
   using type = double2;
 };
 
-// Bricks of 4 x 4 x 4 cells over a one-tank grid (the processing order of
-// the 3D mixed relaxation loops).
+// Bricks of 2^kBrickLog2 cells along each axis over a one-tank grid (the
+// processing order of the 3D mixed neighbour loops).
+constexpr int kBrickLog2X = 2, kBrickLog2Y = 2, kBrickLog2Z = 2;
 inline __host__ __device__ uint32_t brick_count(const Params& P) {
-  return (uint32_t)(((P.nx + 3) / 4) * ((P.ny + 3) / 4) * ((P.nz + 3) / 4));
+  const int bx = (P.nx + (1 << kBrickLog2X) - 1) >> kBrickLog2X;
+  const int by = (P.ny + (1 << kBrickLog2Y) - 1) >> kBrickLog2Y;
+  const int bz = (P.nz + (1 << kBrickLog2Z) - 1) >> kBrickLog2Z;
+  return (uint32_t)(bx * by * bz);
 }
 
 // Raw device pointers of one context (all owned by the context).
@@ -200,7 +204,9 @@ struct DevBuffers {
   uint32_t* unit_brick;   // brick of every group at the last rebuild
   uint32_t* brick_start;  // nbrick + 1: counts, then starts
   uint32_t* brick_fill;   // nbrick
-  uint32_t* unit_ctr;     // 2 x parts claim counters (pressure, relaxation)
+  uint32_t* unit_ctr;     // 5 x parts claim counters: pressure, relaxation (zeroed by
+                          // the first half-step), list build, density summation,
+                          // viscous force (zeroed with the brick order)
   int parts;
   uint32_t* keys[2];  // sort ping-pong; keys[sorted_buf] holds the sorted keys
   uint32_t* vals[2];

@@ -601,17 +601,24 @@ __global__ void k_reorder(Params P, DevBuffers B, int gated) {
 // order.  The order of the groups within a brick is left to the atomics: the
 // loops give the same results in any order.
 __device__ __forceinline__ uint32_t brick_of(const Cell& c, const Params& P) {
-  const int nbx = (P.nx + 3) >> 2, nby = (P.ny + 3) >> 2;
-  return (uint32_t)((c.x >> 2) + nbx * ((c.y >> 2) + nby * (c.z >> 2)));
+  const int nbx = (P.nx + (1 << kBrickLog2X) - 1) >> kBrickLog2X;
+  const int nby = (P.ny + (1 << kBrickLog2Y) - 1) >> kBrickLog2Y;
+  return (uint32_t)((c.x >> kBrickLog2X) +
+                    nbx * ((c.y >> kBrickLog2Y) + nby * (c.z >> kBrickLog2Z)));
 }
 
+// (also zeroes the claim counters of the rebuild's loops: list build,
+// density summation, viscous force)
 template <int D>
 __global__ void k_units_clear(Params P, DevBuffers B, int gated) {
   if (gated && !B.sc->new_adv) return;
   const uint32_t nb = brick_count(P);
-  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= nb; b += gridDim.x * blockDim.x) {
-    B.brick_start[b] = 0;
+  const uint32_t nc = 3u * (uint32_t)B.parts;
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= nb || b < nc;
+       b += gridDim.x * blockDim.x) {
+    if (b <= nb) B.brick_start[b] = 0;
     if (b < nb) B.brick_fill[b] = 0;
+    if (b < nc) B.unit_ctr[2 * B.parts + b] = 0;
   }
 }
 
@@ -674,6 +681,66 @@ __global__ void k_units_scatter(Params P, DevBuffers B, int gated) {
     B.units[B.brick_start[b] + atomicAdd(&B.brick_fill[b], 1u)] = (uint32_t)g;
   }
 }
+
+// ---------------------------------------------------------------------------
+// Slots one thread of a loop body visits: i, i + stride, ... < end.
+struct StrideSlots {
+  int i, end, stride;
+  template <class F>
+  __device__ __forceinline__ void each(F&& f) const {
+    for (int k = i; k < end; k += stride) f(k);
+  }
+};
+
+__device__ __forceinline__ int sm_id() {
+  int r;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+  return r;
+}
+
+// Slots of the groups in brick order (DevBuffers::units): the order is cut
+// into `parts` runs of near-equal length; a warp claims one group at a time
+// (lane 0, one atomic) from the run of its multiprocessor, and when that is
+// done looks for any run with groups left (its lanes test 32 runs per load),
+// so every group is processed once whatever the multiprocessor numbering.
+// ctr holds the runs' claim counters (zeroed before the launch).
+struct UnitSlots {
+  const uint32_t* units;
+  uint32_t* ctr;
+  int parts, ngroups, end;
+  template <class F>
+  __device__ __forceinline__ void each(F&& f) const {
+    const int lane = threadIdx.x & 31;
+    const int base = ngroups / parts, rem = ngroups - base * parts;
+    int p = sm_id() % parts;
+    for (;;) {
+      const int u0 = p * base + min(p, rem);
+      const int size = base + (p < rem ? 1 : 0);
+      for (;;) {
+        int u = size;
+        if (lane == 0 && *(volatile uint32_t*)(ctr + p) < (uint32_t)size)
+          u = (int)atomicAdd(ctr + p, 1u);
+        u = __shfl_sync(kFullMask, u, 0);
+        if (u >= size) break;
+        const uint32_t g = units[u0 + u];
+        const int i = (int)(g * 32u) + lane;
+        if (g < (uint32_t)ngroups && i < end) f(i);
+      }
+      // another run with unclaimed groups, if any
+      int next = -1;
+      for (int r = 0; r < parts - 1 && next < 0; r += 32) {
+        int q = p + 1 + r + lane;
+        if (q >= parts) q -= parts;
+        const bool open = r + lane < parts - 1 &&
+                          *(volatile uint32_t*)(ctr + q) < (uint32_t)(base + (q < rem ? 1 : 0));
+        const unsigned m = __ballot_sync(kFullMask, open);
+        if (m) next = __shfl_sync(kFullMask, q, __ffs(m) - 1);
+      }
+      if (next < 0) return;
+      p = next;
+    }
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Neighbour lists.  Direct search tests every particle of the 3^D cells
@@ -968,10 +1035,8 @@ __device__ __forceinline__ T wall_acc_dot(const DevBuffers& B, int j, T rx, T ry
 // budgets of the rebuild, or larger ones when lists are restored): while no
 // particle leaves its budget, a pair left out stays farther than 2h.  Each
 // candidate is one 16-byte gather of its build record (position, budget).
-template <int D, class T>
-__device__ __forceinline__ void build_lists_range(const Params& P, const DevBuffers& B,
-                                                  const KC<T>& k, DevScalars* sc, int i, int end,
-                                                  int stride) {
+template <int D, class T, class Slots>
+__device__ __forceinline__ void build_lists_slots(const Params& P, const DevBuffers& B, const KC<T>& k, DevScalars* sc, const Slots& slots) {
   using R = Rec<D, T>;
   using BV = typename Vec4<T>::type;
   const BV* __restrict__ brec = (const BV*)B.brec;
@@ -981,7 +1046,7 @@ __device__ __forceinline__ void build_lists_range(const Params& P, const DevBuff
   const T bw = (T)sc->wall_budget;
   const T grow = (T)(1.0 + 1e-6);
   int overflow = 0;
-  for (; i < end; i += stride) {
+  slots.each([&](const int i) {
     const Cell ci = decode(keys[i], P);
     const BV pi = brec[i];
     PairGeo<D, T> G{rec, (const typename WallRec<D, T>::WV*)B.wallP, pi.x, pi.y, pi.z, k.cs};
@@ -1005,17 +1070,27 @@ __device__ __forceinline__ void build_lists_range(const Params& P, const DevBuff
     });
     B.nl_cnt[i] = L.packed();
     if (L.overflowed()) overflow = 1;
-  }
+  });
   if (__syncthreads_or(overflow) && threadIdx.x == 0) atomicOr(&sc->list_bad, 1);
 }
 
 template <int D, class T>
+__device__ __forceinline__ void build_lists_range(const Params& P, const DevBuffers& B, const KC<T>& k, DevScalars* sc, int i, int end, int stride) {
+  build_lists_slots<D, T>(P, B, k, sc, StrideSlots{i, end, stride});
+}
+
+// kUnits: the slots in brick order (one tank, 3D mixed), else strided.
+template <int D, class T, bool kUnits = false>
 __global__ void __launch_bounds__(256, kMinBlocks<T>) k_build_lists(Params P, DevBuffers B, KC<T> k,
                                                                     int gated) {
   DevScalars* sc = B.sc;
   if (!P.use_list || (gated && !sc->new_adv)) return;
-  build_lists_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
-                          gridDim.x * blockDim.x);
+  if constexpr (kUnits)
+    build_lists_slots<D, T>(
+        P, B, k, sc, UnitSlots{B.units, B.unit_ctr + 2 * B.parts, B.parts, (P.n + 31) >> 5, P.n});
+  else
+    build_lists_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+                            gridDim.x * blockDim.x);
 }
 
 // Density from the kernel sum: the free-surface clamp rho0 max(sigma/sigma0, 1),
@@ -1092,10 +1167,8 @@ __device__ __forceinline__ unsigned long long fx_r2(const typename FxRec<D>::V& 
   return R2;
 }
 
-template <int D>
-__device__ __forceinline__ void density_summation_fx_range(const Params& P, const DevBuffers& B,
-                                                           DevScalars* sc, int i, int end,
-                                                           int stride) {
+template <int D, class Slots>
+__device__ __forceinline__ void density_summation_fx_slots(const Params& P, const DevBuffers& B, DevScalars* sc, const Slots& slots) {
   using R = Rec<D, float>;
   using FV = typename FxRec<D>::V;
   const bool use_list = list_ok(P, sc, sc->drift_bad_p, sc->t_reb);
@@ -1105,7 +1178,7 @@ __device__ __forceinline__ void density_summation_fx_range(const Params& P, cons
   const RecArr<D, float> lrec(B, 0);
   const uint32_t* __restrict__ keys = B.binned;
   const unsigned long long cut2 = 1ull << (2 * kFxShift);
-  for (; i < end; i += stride) {
+  slots.each([&](const int i) {
     const Cell ci = decode(keys[i], P);
     const FV oi = rec[i];
     dfl sig = {1.0f, 0.0f};  // self first: shape(0) = 1, no term is larger
@@ -1122,16 +1195,25 @@ __device__ __forceinline__ void density_summation_fx_range(const Params& P, cons
     rho_live[i] = rho;
     lrec.rho(i) = (float)rho;
     if (P.diag) ((float*)B.sigma)[i] = (float)sigma;
-  }
+  });
 }
 
 template <int D>
+__device__ __forceinline__ void density_summation_fx_range(const Params& P, const DevBuffers& B, DevScalars* sc, int i, int end, int stride) {
+  density_summation_fx_slots<D>(P, B, sc, StrideSlots{i, end, stride});
+}
+
+template <int D, bool kUnits = false>
 __global__ void __launch_bounds__(256, 4) k_density_summation_fx(Params P, DevBuffers B,
                                                                  int gated) {
   DevScalars* sc = B.sc;
   if (gated && !sc->new_adv) return;
-  density_summation_fx_range<D>(P, B, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
-                                gridDim.x * blockDim.x);
+  if constexpr (kUnits)
+    density_summation_fx_slots<D>(
+        P, B, sc, UnitSlots{B.units, B.unit_ctr + 3 * B.parts, B.parts, (P.n + 31) >> 5, P.n});
+  else
+    density_summation_fx_range<D>(P, B, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+                                  gridDim.x * blockDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1251,10 +1333,8 @@ __global__ void k_transport_apply(Params P, DevBuffers B, int gated) {
 // mirrored velocity 2 v_w - v_i, so its pair term carries 2 (v_i - v_w) (the
 // factor folded into its volume).  Positions are those of the rebuild, so the
 // lists are always usable here (unless one overflowed).
-template <int D, class T>
-__device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers& B, const KC<T>& k,
-                                              DevScalars* sc, int i, int end, int stride,
-                                     const ShiftTable* tab) {
+template <int D, class T, class Slots>
+__device__ __forceinline__ void viscous_slots(const Params& P, const DevBuffers& B, const KC<T>& k, DevScalars* sc, const Slots& slots, const ShiftTable* tab) {
   using R = Rec<D, T>;
   const bool use_list = list_ok(P, sc, sc->drift_bad_p, sc->t_reb);
   const RecArr<D, T> rec(B, 0);
@@ -1264,7 +1344,7 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
   T* ap2 = (T*)B.aprior[2];
   const T wallV2 = (T)(2.0 * P.V);
   const bool moving = (P.variant & kVariantMovingWall) != 0;
-  for (; i < end; i += stride) {
+  slots.each([&](const int i) {
     const Cell ci = decode(keys[i], P);
     typename R::PV pi;
     typename R::SV si;
@@ -1315,18 +1395,28 @@ __device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers&
     ap0[i] = k.g[0] + f * ax;
     ap1[i] = k.g[1] + f * ay;
     if (D == 3) ap2[i] = k.g[2] + f * az;
-  }
+  });
 }
 
 template <int D, class T>
+__device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers& B, const KC<T>& k, DevScalars* sc, int i, int end, int stride, const ShiftTable* tab) {
+  viscous_slots<D, T>(P, B, k, sc, StrideSlots{i, end, stride}, tab);
+}
+
+template <int D, class T, bool kUnits = false>
 __global__ void __launch_bounds__(256, kMinBlocks<T>) k_viscous(Params P, DevBuffers B, KC<T> k,
                                                                 int gated) {
   DevScalars* sc = B.sc;
   if (gated && !sc->new_adv) return;
   __shared__ ShiftTable tab;
   if constexpr (Local<T>::kLocal && !kShiftBits<D>) fill_shift_table(tab);
-  viscous_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
-                      gridDim.x * blockDim.x, &tab);
+  if constexpr (kUnits)
+    viscous_slots<D, T>(
+        P, B, k, sc, UnitSlots{B.units, B.unit_ctr + 4 * B.parts, B.parts, (P.n + 31) >> 5, P.n},
+        &tab);
+  else
+    viscous_range<D, T>(P, B, k, sc, blockIdx.x * blockDim.x + threadIdx.x, P.n,
+                        gridDim.x * blockDim.x, &tab);
 }
 
 // First half of the acoustic step; writes records of buffer 0.
@@ -1380,65 +1470,6 @@ template <int D>
 inline bool wall_vel_code(int variant) {
   return (variant & kVariantMovingWall) != 0 || D == 3;
 }
-
-// Slots one thread of a loop body visits: i, i + stride, ... < end.
-struct StrideSlots {
-  int i, end, stride;
-  template <class F>
-  __device__ __forceinline__ void each(F&& f) const {
-    for (int k = i; k < end; k += stride) f(k);
-  }
-};
-
-__device__ __forceinline__ int sm_id() {
-  int r;
-  asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
-  return r;
-}
-
-// Slots of the groups in brick order (DevBuffers::units): the order is cut
-// into `parts` runs of near-equal length; a warp claims one group at a time
-// (lane 0, one atomic) from the run of its multiprocessor, and when that is
-// done looks for any run with groups left (its lanes test 32 runs per load),
-// so every group is processed once whatever the multiprocessor numbering.
-// ctr holds the runs' claim counters (zeroed before the launch).
-struct UnitSlots {
-  const uint32_t* units;
-  uint32_t* ctr;
-  int parts, ngroups, end;
-  template <class F>
-  __device__ __forceinline__ void each(F&& f) const {
-    const int lane = threadIdx.x & 31;
-    const int base = ngroups / parts, rem = ngroups - base * parts;
-    int p = sm_id() % parts;
-    for (;;) {
-      const int u0 = p * base + min(p, rem);
-      const int size = base + (p < rem ? 1 : 0);
-      for (;;) {
-        int u = size;
-        if (lane == 0 && *(volatile uint32_t*)(ctr + p) < (uint32_t)size)
-          u = (int)atomicAdd(ctr + p, 1u);
-        u = __shfl_sync(kFullMask, u, 0);
-        if (u >= size) break;
-        const uint32_t g = units[u0 + u];
-        const int i = (int)(g * 32u) + lane;
-        if (g < (uint32_t)ngroups && i < end) f(i);
-      }
-      // another run with unclaimed groups, if any
-      int next = -1;
-      for (int r = 0; r < parts - 1 && next < 0; r += 32) {
-        int q = p + 1 + r + lane;
-        if (q >= parts) q -= parts;
-        const bool open = r + lane < parts - 1 &&
-                          *(volatile uint32_t*)(ctr + q) < (uint32_t)(base + (q < rem ? 1 : 0));
-        const unsigned m = __ballot_sync(kFullMask, open);
-        if (m) next = __shfl_sync(kFullMask, q, __ffs(m) - 1);
-      }
-      if (next < 0) return;
-      p = next;
-    }
-  }
-};
 
 // Riemann pressure relaxation + kick + the drift that opens the density stage.
 // Reads records of buffer 0, writes records of buffer 1.  kWallVel compiles
@@ -1905,8 +1936,8 @@ void enqueue_units(const StageArgs& a, cudaStream_t s, int gated) {
   if (D != 3 || !Local<T>::kLocal || !a.B.units || P.n <= 0) return;
   const int ng = (P.n + 31) >> 5;
   const int gs = grid_for(ng, 256, a.L.blocks_stream);
-  k_units_clear<D><<<grid_for((int)brick_count(P) + 1, 256, a.L.blocks_stream), 256, 0, s>>>(P, a.B,
-                                                                                          gated);
+  const int nclear = max((int)brick_count(P) + 1, 3 * a.B.parts);
+  k_units_clear<D><<<grid_for(nclear, 256, a.L.blocks_stream), 256, 0, s>>>(P, a.B, gated);
   k_units_count<D><<<gs, 256, 0, s>>>(P, a.B, gated);
   k_units_scan<D><<<1, kUnitScanThreads, 0, s>>>(P, a.B, gated);
   k_units_scatter<D><<<gs, 256, 0, s>>>(P, a.B, gated);
@@ -1941,19 +1972,33 @@ void enqueue_advection_loops(const StageArgs& a, cudaStream_t s, int gated, cuda
   const DevBuffers& B = a.B;
   const KC<T> k = make_kc<T>(P);
   const int gl = grid_for(P.n, L.block_loop, L.blocks_loop);
+  constexpr bool kU = D == 3 && Local<T>::kLocal;  // brick order when B.units is set
+  const bool units = kU && B.units;
   mark(ev, kStageDensitySum, s);
-  k_build_lists<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, gated);
-  if constexpr (Local<T>::kLocal)
-    k_density_summation_fx<D><<<gl, L.block_loop, 0, s>>>(P, B, gated);
+  if (units)
+    k_build_lists<D, T, kU><<<one_wave(k_build_lists<D, T, kU>, L), L.block_loop, 0, s>>>(P, B, k,
+                                                                                       gated);
   else
+    k_build_lists<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, gated);
+  if constexpr (Local<T>::kLocal) {
+    if (units)
+      k_density_summation_fx<D, kU><<<one_wave(k_density_summation_fx<D, kU>, L), L.block_loop, 0,
+                                      s>>>(P, B, gated);
+    else
+      k_density_summation_fx<D><<<gl, L.block_loop, 0, s>>>(P, B, gated);
+  } else {
     k_density_summation<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, gated);
+  }
   if (P.variant & kVariantTransport) {
     k_transport<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, gated);
     k_transport_apply<D, T><<<grid_for(P.n, L.block_stream, L.blocks_stream), L.block_stream, 0,
                               s>>>(P, B, gated);
   }
   mark(ev, kStageViscous, s);
-  k_viscous<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, gated);
+  if (units)
+    k_viscous<D, T, kU><<<one_wave(k_viscous<D, T, kU>, L), L.block_loop, 0, s>>>(P, B, k, gated);
+  else
+    k_viscous<D, T><<<gl, L.block_loop, 0, s>>>(P, B, k, gated);
 }
 
 template <int D, class T>

@@ -260,9 +260,10 @@ __device__ __forceinline__ T wendland_dr(const KC<T>& k, T r) {
 // Register budget of the neighbour-loop kernels (blocks of up to 256 threads):
 // 5 resident blocks -> at most 48 registers in float, 2 -> 128 in double.  The
 // 3D density-relaxation loop keeps 4 blocks (64 registers); the one-tank 3D
-// pressure loop (k_pressure) fits 48 without spills and measured faster at 5
-// (1.38 -> 1.33 ms per launch on the 5.1 M dam break), the relaxation loop
-// slower (1.12 -> 1.20 ms).
+// pressure loop (k_pressure) measured faster at 5 (1.38 -> 1.33 ms per launch
+// on the 5.1 M dam break in storage order, 1.155 -> 1.08 ms in brick order,
+// where it spills 16 bytes), the relaxation loop slower (1.12 -> 1.20 ms;
+// 0.950 -> 0.977 ms in brick order).
 template <class T>
 constexpr int kMinBlocks = sizeof(T) == 8 ? 2 : 5;
 template <int D, class T>
@@ -1606,7 +1607,7 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
 
 // kUnits: the slots in brick order (one tank, 3D mixed), else strided.
 template <int D, class T, bool kWallVel, bool kAccel = false, bool kUnits = false>
-__global__ void __launch_bounds__(256, kUnits ? 4 : kMinBlocksPres<D, T>) k_pressure(Params P, DevBuffers B, KC<T> k) {
+__global__ void __launch_bounds__(256, kMinBlocksPres<D, T>) k_pressure(Params P, DevBuffers B, KC<T> k) {
   __shared__ ShiftTable tab;
   if constexpr (Local<T>::kLocal && !kShiftBits<D>) fill_shift_table(tab);
   if constexpr (kUnits)

@@ -94,8 +94,8 @@ def source_fingerprint() -> str:
 # depend on size at fixed h / dp), warp instructions by the list entries
 # (nearly all instructions are spent per entry).
 NCU_CAPTURES = {
-    ("pressure", "26068f2cade4"): {"fluid": 643200, "dram_bytes": 283195392 + 11122688,
-                                   "warp_inst": 135902559, "list_entries_per_particle": None},
+    ("pressure", "1e8047bd5d9d"): {"fluid": 643200, "dram_bytes": 294704896 + 22504704,
+                                   "warp_inst": 134504296, "list_entries_per_particle": None},
 }
 
 

@@ -497,17 +497,28 @@ int bits_for(uint32_t ncell);
 // < 2e-7 relative), the double quotient has the same floor and the division
 // is skipped.  Only coordinates within that distance of a cell face take the
 // double division, so the result always equals the plain double formula.
+// On that path fq is an integer below 2^20 (a larger quotient has no
+// fractional bits in float and takes the double path), so the clamp and the
+// conversion run in float and int, off the FP64 pipe.
 __device__ __forceinline__ int cell_coord_fast(double x, double lo, double cs, float inv_cs,
                                                int nc, int& oob) {
   const double d = __dsub_rn(x, lo);
   const float qf = __fmul_rn((float)d, inv_cs);
   const float fq = floorf(qf);
   const float dist = fminf(qf - fq, fq + 1.0f - qf);
-  double f;
-  if (dist > 1e-6f * fabsf(qf) + 4e-6f)
-    f = (double)fq;
-  else
-    f = floor(__ddiv_rn(d, cs));
+  if (dist > 1e-6f * fabsf(qf) + 4e-6f) {
+    if (!(fq >= 0.0f)) {
+      oob = 1;
+      return 0;
+    }
+    const int c = (int)fq;
+    if (c >= nc) {
+      oob = 1;
+      return nc - 1;
+    }
+    return c;
+  }
+  const double f = floor(__ddiv_rn(d, cs));
   if (!(f >= 0.0)) {
     oob = 1;
     return 0;

@@ -72,9 +72,48 @@ void ns_free(sph_nsearch* s, std::vector<sph_nsearch::Blk>& list) {
   list.clear();
 }
 
-// Cell key from float or double coordinates: the coordinate is widened to
-// double (exact) and binned with the same formula as the simulation path
-// (clamped; this entry point reports no out-of-domain flag).
+// Cell index of a float coordinate: the same value as cell_coord_fast on the
+// widened coordinate (the plain double formula), with no double arithmetic
+// off the faces.  x - lo is formed in float against lo split into
+// lo_hi + lo_lo (floats, |lo - lo_hi - lo_lo| <= 2^-48 |lo|); with the product
+// by the float 1 / cs that is four float roundings (< 2.4e-7 relative), inside
+// the distance the test below asks of the quotient from the nearest integer.
+// Nearer a face the double subtraction and division decide.
+__device__ __forceinline__ int cell_coord_f32(float x, double lo, float lo_hi, float lo_lo,
+                                              double cs, float inv_cs, int nc, int& oob) {
+  const float qf = __fmul_rn(__fsub_rn(__fsub_rn(x, lo_hi), lo_lo), inv_cs);
+  const float fq = floorf(qf);
+  const float dist = fminf(qf - fq, fq + 1.0f - qf);
+  if (dist > 1e-6f * fabsf(qf) + 4e-6f) {
+    if (!(fq >= 0.0f)) {
+      oob = 1;
+      return 0;
+    }
+    const int c = (int)fq;
+    if (c >= nc) {
+      oob = 1;
+      return nc - 1;
+    }
+    return c;
+  }
+  return cell_coord_fast((double)x, lo, cs, inv_cs, nc, oob);
+}
+
+template <class T>
+__device__ __forceinline__ int ns_cell(T x, const Params& P, int k, float inv_cs, int nc,
+                                       int& oob) {
+  if constexpr (sizeof(T) == 4) {
+    const float lo_hi = (float)P.lo[k];
+    const float lo_lo = (float)(P.lo[k] - (double)lo_hi);
+    return cell_coord_f32(x, P.lo[k], lo_hi, lo_lo, P.cs, inv_cs, nc, oob);
+  } else {
+    return cell_coord_fast(x, P.lo[k], P.cs, inv_cs, nc, oob);
+  }
+}
+
+// Cell key from float or double coordinates, with the same value as the
+// simulation path's formula on the coordinate widened to double (clamped;
+// this entry point reports no out-of-domain flag).
 template <class T>
 __global__ void k_ns_keys(Params P, const T* __restrict__ x, const T* __restrict__ y,
                           const T* __restrict__ z, int n, uint32_t* keys, uint32_t* vals,
@@ -84,10 +123,9 @@ __global__ void k_ns_keys(Params P, const T* __restrict__ x, const T* __restrict
   const float inv_cs = (float)(1.0 / P.cs);
   int oob = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int cx = cell_coord_fast((double)x[i], P.lo[0], P.cs, inv_cs, P.nx, oob);
-    const int cy = cell_coord_fast((double)y[i], P.lo[1], P.cs, inv_cs, P.ny, oob);
-    const int cz =
-        P.dim == 3 ? cell_coord_fast((double)z[i], P.lo[2], P.cs, inv_cs, P.nz, oob) : 0;
+    const int cx = ns_cell<T>(x[i], P, 0, inv_cs, P.nx, oob);
+    const int cy = ns_cell<T>(y[i], P, 1, inv_cs, P.ny, oob);
+    const int cz = P.dim == 3 ? ns_cell<T>(z[i], P, 2, inv_cs, P.nz, oob) : 0;
     keys[i] = ((uint32_t)cz * (uint32_t)P.ny + (uint32_t)cy) * (uint32_t)P.nx + (uint32_t)cx;
     vals[i] = (uint32_t)i;
   }

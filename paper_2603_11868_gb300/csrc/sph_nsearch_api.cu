@@ -156,6 +156,7 @@ __device__ __forceinline__ void ns_density_slots(const Params& P, const uint32_t
                                                  const typename Vec4<T>::type* __restrict__ sp,
                                                  double* sigma, const Slots& slots) {
   const T r2max = (T)P.r2max, inv_h = (T)(1.0 / P.h), cw = (T)P.walpha;
+  const float m_half_inv_h = (float)(-0.5 / P.h), two_inv_h = (float)(2.0 / P.h);
   slots.each([&](const int i) {
     const uint32_t key = keys[i];
     const uint32_t r = key / (uint32_t)P.nx;
@@ -175,24 +176,29 @@ __device__ __forceinline__ void ns_density_slots(const Params& P, const uint32_t
         const uint32_t c0 = row + (uint32_t)(cx > 0 ? cx - 1 : cx);
         const uint32_t c1 = row + (uint32_t)(cx + 1 < P.nx ? cx + 1 : cx);
         const uint32_t e = cb[c1 + 1];
+#pragma unroll 4  // measured +1% with the folded constants (-1% without)
         for (uint32_t j = cb[c0]; j < e; ++j) {  // the row's 3 cells are contiguous
           const typename Vec4<T>::type pj = sp[j];
           const T dx = xi - pj.x, dyv = yi - pj.y, dzv = zi - pj.z;
           const T r2 = dx * dx + dyv * dyv + dzv * dzv;
           if (r2 < r2max) {
-            T q;
             if constexpr (sizeof(T) == 4) {
-              // r = r^2 / sqrt(r^2) by the approximate reciprocal square root
-              // (relative error about 2^-22; r^2 = 0 gives q = 0)
+              // W / walpha = t^4 (2q + 1), t = 1 - q/2, q = r / h, with r from
+              // the approximate reciprocal square root (relative error about
+              // 2^-22; r^2 = 0 gives r = 0) and the constants folded: the
+              // accepted branch runs for the warp at nearly every candidate
               float rs;
-              asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(fmaxf(r2, 1e-30f)));
-              q = r2 * rs * inv_h;
+              asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(r2 + 1e-30f));
+              const float r = r2 * rs;
+              const float t = fmaf(r, m_half_inv_h, 1.0f);
+              const float t2 = t * t;
+              sig = fmaf(t2 * t2, fmaf(r, two_inv_h, 1.0f), sig);
             } else {
-              q = sqrt(r2) * inv_h;
+              const T q = sqrt(r2) * inv_h;
+              const T t = T(1) - T(0.5) * q;
+              const T t2 = t * t;
+              sig += t2 * t2 * (T(2) * q + T(1));
             }
-            const T t = T(1) - T(0.5) * q;
-            const T t2 = t * t;
-            sig += t2 * t2 * (T(2) * q + T(1));
           }
         }
       }

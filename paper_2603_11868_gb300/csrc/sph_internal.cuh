@@ -275,6 +275,9 @@ struct LaunchCfg {
   int radix_passes;
   int key_bits;
   int tiles;  // radix tiles
+  // 1: the sort histograms group equal digits by ballots, not __match_any_sync
+  // (faster for keys in random order, slower for nearly sorted ones)
+  int hist_ballot = 0;
 };
 
 // ---------------------------------------------------------------------------

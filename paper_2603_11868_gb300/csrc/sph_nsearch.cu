@@ -65,6 +65,24 @@ __device__ __forceinline__ void sort_count(int& n, int& tiles, const int* n_dev)
   }
 }
 
+// Lanes holding the same digit (a valid lane's d < 2^nbits): one ballot per
+// digit bit and one for validity, ANDed; the same mask as __match_any_sync on
+// (valid, d), from full-rate instructions.
+__device__ __forceinline__ unsigned match_digit(uint32_t d, bool valid, int nbits) {
+  const unsigned vb = __ballot_sync(kFull, valid);
+  unsigned m = valid ? vb : ~vb;
+  for (int b = 0; b < nbits; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const unsigned bb = __ballot_sync(kFull, bit);
+    m &= bit ? bb : ~bb;
+  }
+  return m;
+}
+
+// kBallot: equal digits grouped by match_digit (measured faster for keys in
+// random order: a warp then holds many distinct digits), else by
+// __match_any_sync (faster for the nearly sorted keys of a re-sort).
+template <bool kBallot>
 __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int n, int shift, uint32_t mask,
                              uint32_t* __restrict__ tile_hist, uint32_t* digit_total, int tiles,
                              const DevScalars* sc, int gated, const int* n_dev) {
@@ -84,8 +102,15 @@ __global__ void k_radix_hist(const uint32_t* __restrict__ keys, int n, int shift
   for (int it = 0; it < kSortItems; ++it) {
     long idx = base + it * 32 + lane;
     bool valid = idx < n;
-    uint32_t d = valid ? (keys[idx] >> shift) & mask : 0xffffffffu;
-    unsigned peers = __match_any_sync(kFull, d);
+    unsigned peers;
+    uint32_t d;
+    if constexpr (kBallot) {
+      d = valid ? (keys[idx] >> shift) & mask : 0u;
+      peers = match_digit(d, valid, __popc(mask));
+    } else {
+      d = valid ? (keys[idx] >> shift) & mask : 0xffffffffu;
+      peers = __match_any_sync(kFull, d);
+    }
     if (valid && lane == __ffs(peers) - 1) wh[w * bins + d] += __popc(peers);
     __syncwarp();
   }
@@ -770,8 +795,12 @@ static size_t scatter_smem(int bins) {
 }
 
 cudaError_t configure_sort_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(k_radix_hist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_radix_hist<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)hist_smem(1 << kMaxRadixBits));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_radix_hist<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)hist_smem(1 << kMaxRadixBits));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)scatter_smem(1 << kMaxRadixBits));
@@ -790,9 +819,12 @@ int radix_sort_impl(const LaunchCfg& L, uint32_t* keys[2], uint32_t* vals[2], in
     if (bits > L.radix_bits) bits = L.radix_bits;
     const uint32_t mask = (1u << bits) - 1u;
     const int bins = (int)mask + 1;
-    k_radix_hist<<<tiles, kSortThreads, hist_smem(bins), s>>>(keys[cur], n, shift, mask,
-                                                              tile_hist, digit_total, tiles, sc,
-                                                              gated, n_dev);
+    if (L.hist_ballot)
+      k_radix_hist<true><<<tiles, kSortThreads, hist_smem(bins), s>>>(
+          keys[cur], n, shift, mask, tile_hist, digit_total, tiles, sc, gated, n_dev);
+    else
+      k_radix_hist<false><<<tiles, kSortThreads, hist_smem(bins), s>>>(
+          keys[cur], n, shift, mask, tile_hist, digit_total, tiles, sc, gated, n_dev);
     k_radix_scan<<<bins, 256, 0, s>>>(tile_hist, digit_total, tiles, sc, gated, n_dev);
     k_radix_scatter<<<tiles, kSortThreads, scatter_smem(bins), s>>>(
         keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, shift, mask, tile_hist, tiles, sc,

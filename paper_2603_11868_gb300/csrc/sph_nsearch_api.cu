@@ -289,6 +289,7 @@ int sph_nsearch_create(const sph_domain* domain, double h, int pos_precision,
   s->L.block_stream = 256;
   s->L.blocks_stream = s->L.sms * 8;
   s->L.radix_bits = 8;
+  s->L.hist_ballot = 1;  // positions in any order: the keys are not nearly sorted
   s->L.key_bits = bits_for(P.ncell);
   s->L.radix_passes = radix_passes_for(s->L.key_bits, s->L.radix_bits);
   s->cell_begin = (uint32_t*)ns_alloc(s, ((size_t)P.ncell + 1) * 4, s->fixed);

@@ -36,6 +36,7 @@ struct sph_nsearch {
   uint32_t *keys[2] = {}, *vals[2] = {}, *tile_hist = nullptr, *digit_total = nullptr,
            *cell_begin = nullptr;
   void* sp = nullptr;  // sorted positions, packed (x, y, z, 0) of the position type
+  void* pk = nullptr;  // the same packing in input order (written with the keys)
   double* sigma = nullptr;
   // brick processing order of the density pass (the one-tank loops' scheme):
   // DevBuffers fields units, unit_brick, brick_start, brick_fill, unit_ctr, parts
@@ -114,38 +115,43 @@ __device__ __forceinline__ int ns_cell(T x, const Params& P, int k, float inv_cs
 // Cell key from float or double coordinates, with the same value as the
 // simulation path's formula on the coordinate widened to double (clamped;
 // this entry point reports no out-of-domain flag).
+// Also packs each particle's coordinates into one vector (pk, input order),
+// so that the reorder gathers one vector per particle instead of one sector
+// per coordinate.
 template <class T>
 __global__ void k_ns_keys(Params P, const T* __restrict__ x, const T* __restrict__ y,
                           const T* __restrict__ z, int n, uint32_t* keys, uint32_t* vals,
-                          uint32_t* digit_total, int bins) {
+                          uint32_t* digit_total, int bins, typename Vec4<T>::type* pk) {
   if (blockIdx.x == 0)
     for (int t = threadIdx.x; t < bins; t += blockDim.x) digit_total[t] = 0;
   const float inv_cs = (float)(1.0 / P.cs);
   int oob = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int cx = ns_cell<T>(x[i], P, 0, inv_cs, P.nx, oob);
-    const int cy = ns_cell<T>(y[i], P, 1, inv_cs, P.ny, oob);
-    const int cz = P.dim == 3 ? ns_cell<T>(z[i], P, 2, inv_cs, P.nz, oob) : 0;
+    const T xi = x[i], yi = y[i], zi = P.dim == 3 ? z[i] : T(0);
+    const int cx = ns_cell<T>(xi, P, 0, inv_cs, P.nx, oob);
+    const int cy = ns_cell<T>(yi, P, 1, inv_cs, P.ny, oob);
+    const int cz = P.dim == 3 ? ns_cell<T>(zi, P, 2, inv_cs, P.nz, oob) : 0;
+    typename Vec4<T>::type v;
+    v.x = xi;
+    v.y = yi;
+    v.z = zi;
+    v.w = T(0);
+    pk[i] = v;
     keys[i] = ((uint32_t)cz * (uint32_t)P.ny + (uint32_t)cy) * (uint32_t)P.nx + (uint32_t)cx;
     vals[i] = (uint32_t)i;
   }
 }
 
 // Sorted positions packed as one vector per particle (x, y, z, 0): the density
-// pass then reads each candidate with a single load.
+// pass then reads each candidate with a single load.  The gather takes the
+// packed input (one sector per particle; three 4-byte gathers from the
+// coordinate arrays fetched about 240 B of DRAM per particle).
 template <class T>
-__global__ void k_ns_reorder(const uint32_t* __restrict__ perm, const T* __restrict__ x,
-                             const T* __restrict__ y, const T* __restrict__ z, int n, int dim,
+__global__ void k_ns_reorder(const uint32_t* __restrict__ perm,
+                             const typename Vec4<T>::type* __restrict__ pk, int n,
                              typename Vec4<T>::type* sp) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const uint32_t j = perm[k];
-    typename Vec4<T>::type v;
-    v.x = x[j];
-    v.y = y[j];
-    v.z = dim == 3 ? z[j] : T(0);
-    v.w = T(0);
-    sp[k] = v;
-  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    sp[k] = pk[perm[k]];
 }
 
 // sigma_i = sum over the 3^d cells of W(r_ij), r < 2h, self included (the
@@ -324,7 +330,8 @@ int sph_nsearch_run(sph_nsearch* s, size_t n, const void* x, const void* y, cons
       ok &= s->keys[p] && s->vals[p];
     }
     s->sp = ns_alloc(s, n * 4 * ts, s->blocks);
-    ok &= s->sp != nullptr;
+    s->pk = ns_alloc(s, n * 4 * ts, s->blocks);
+    ok &= s->sp != nullptr && s->pk != nullptr;
     s->sigma = (double*)ns_alloc(s, n * 8, s->blocks);
     s->U.units = (uint32_t*)ns_alloc(s, ((n + 31) / 32) * 4, s->blocks);
     s->U.unit_brick = (uint32_t*)ns_alloc(s, ((n + 31) / 32) * 4, s->blocks);
@@ -350,11 +357,12 @@ int sph_nsearch_run(sph_nsearch* s, size_t n, const void* x, const void* y, cons
   cudaEventRecord(s->ev[0], st);
   if (s->fp32)
     k_ns_keys<float><<<gs, 256, 0, st>>>(s->P, (const float*)x, (const float*)y, (const float*)z,
-                                         ni, s->keys[0], s->vals[0], s->digit_total, bins);
+                                         ni, s->keys[0], s->vals[0], s->digit_total, bins,
+                                         (float4*)s->pk);
   else
     k_ns_keys<double><<<gs, 256, 0, st>>>(s->P, (const double*)x, (const double*)y,
                                           (const double*)z, ni, s->keys[0], s->vals[0],
-                                          s->digit_total, bins);
+                                          s->digit_total, bins, (double4_32a*)s->pk);
   cudaEventRecord(s->ev[1], st);
   s->sorted = launch_radix_sort(s->L, s->keys, s->vals, ni, s->tile_hist, s->digit_total,
                                 nullptr, 0, st);
@@ -362,11 +370,9 @@ int sph_nsearch_run(sph_nsearch* s, size_t n, const void* x, const void* y, cons
   const uint32_t* perm = s->vals[s->sorted];
   const uint32_t* keys = s->keys[s->sorted];
   if (s->fp32)
-    k_ns_reorder<float><<<gs, 256, 0, st>>>(perm, (const float*)x, (const float*)y,
-                                            (const float*)z, ni, s->P.dim, (float4*)s->sp);
+    k_ns_reorder<float><<<gs, 256, 0, st>>>(perm, (const float4*)s->pk, ni, (float4*)s->sp);
   else
-    k_ns_reorder<double><<<gs, 256, 0, st>>>(perm, (const double*)x, (const double*)y,
-                                             (const double*)z, ni, s->P.dim,
+    k_ns_reorder<double><<<gs, 256, 0, st>>>(perm, (const double4_32a*)s->pk, ni,
                                              (double4_32a*)s->sp);
   cudaEventRecord(s->ev[3], st);
   launch_cell_offsets(keys, ni, s->P.ncell, s->cell_begin, nullptr, 0, 0, st);

@@ -94,8 +94,8 @@ def source_fingerprint() -> str:
 # depend on size at fixed h / dp), warp instructions by the list entries
 # (nearly all instructions are spent per entry).
 NCU_CAPTURES = {
-    ("pressure", "1e8047bd5d9d"): {"fluid": 643200, "dram_bytes": 294704896 + 22504704,
-                                   "warp_inst": 134504296, "list_entries_per_particle": None},
+    ("pressure", "e957191bc427"): {"fluid": 643200, "dram_bytes": 294767360 + 22382592,
+                                   "warp_inst": 134538007, "list_entries_per_particle": None},
 }
 
 

@@ -637,7 +637,8 @@ __global__ void k_units_count(Params P, DevBuffers B, int gated) {
 // exclusive scan of the brick counts in place (one block of kUnitScanThreads)
 constexpr int kUnitScanThreads = 1024;
 template <int D>
-__global__ void __launch_bounds__(kUnitScanThreads) k_units_scan(Params P, DevBuffers B, int gated) {
+__global__ void __launch_bounds__(kUnitScanThreads) k_units_scan(Params P, DevBuffers B,
+                                                                 int gated) {
   if (gated && !B.sc->new_adv) return;
   __shared__ uint32_t part[kUnitScanThreads / 32];
   const uint32_t nb = brick_count(P);
@@ -1037,7 +1038,9 @@ __device__ __forceinline__ T wall_acc_dot(const DevBuffers& B, int j, T rx, T ry
 // particle leaves its budget, a pair left out stays farther than 2h.  Each
 // candidate is one 16-byte gather of its build record (position, budget).
 template <int D, class T, class Slots>
-__device__ __forceinline__ void build_lists_slots(const Params& P, const DevBuffers& B, const KC<T>& k, DevScalars* sc, const Slots& slots) {
+__device__ __forceinline__ void build_lists_slots(const Params& P, const DevBuffers& B,
+                                                  const KC<T>& k, DevScalars* sc,
+                                                  const Slots& slots) {
   using R = Rec<D, T>;
   using BV = typename Vec4<T>::type;
   const BV* __restrict__ brec = (const BV*)B.brec;
@@ -1076,7 +1079,9 @@ __device__ __forceinline__ void build_lists_slots(const Params& P, const DevBuff
 }
 
 template <int D, class T>
-__device__ __forceinline__ void build_lists_range(const Params& P, const DevBuffers& B, const KC<T>& k, DevScalars* sc, int i, int end, int stride) {
+__device__ __forceinline__ void build_lists_range(const Params& P, const DevBuffers& B,
+                                                  const KC<T>& k, DevScalars* sc, int i, int end,
+                                                  int stride) {
   build_lists_slots<D, T>(P, B, k, sc, StrideSlots{i, end, stride});
 }
 
@@ -1169,7 +1174,8 @@ __device__ __forceinline__ unsigned long long fx_r2(const typename FxRec<D>::V& 
 }
 
 template <int D, class Slots>
-__device__ __forceinline__ void density_summation_fx_slots(const Params& P, const DevBuffers& B, DevScalars* sc, const Slots& slots) {
+__device__ __forceinline__ void density_summation_fx_slots(const Params& P, const DevBuffers& B,
+                                                           DevScalars* sc, const Slots& slots) {
   using R = Rec<D, float>;
   using FV = typename FxRec<D>::V;
   const bool use_list = list_ok(P, sc, sc->drift_bad_p, sc->t_reb);
@@ -1200,7 +1206,9 @@ __device__ __forceinline__ void density_summation_fx_slots(const Params& P, cons
 }
 
 template <int D>
-__device__ __forceinline__ void density_summation_fx_range(const Params& P, const DevBuffers& B, DevScalars* sc, int i, int end, int stride) {
+__device__ __forceinline__ void density_summation_fx_range(const Params& P, const DevBuffers& B,
+                                                           DevScalars* sc, int i, int end,
+                                                           int stride) {
   density_summation_fx_slots<D>(P, B, sc, StrideSlots{i, end, stride});
 }
 
@@ -1335,7 +1343,9 @@ __global__ void k_transport_apply(Params P, DevBuffers B, int gated) {
 // factor folded into its volume).  Positions are those of the rebuild, so the
 // lists are always usable here (unless one overflowed).
 template <int D, class T, class Slots>
-__device__ __forceinline__ void viscous_slots(const Params& P, const DevBuffers& B, const KC<T>& k, DevScalars* sc, const Slots& slots, const ShiftTable* tab) {
+__device__ __forceinline__ void viscous_slots(const Params& P, const DevBuffers& B, const KC<T>& k,
+                                              DevScalars* sc, const Slots& slots,
+                                              const ShiftTable* tab) {
   using R = Rec<D, T>;
   const bool use_list = list_ok(P, sc, sc->drift_bad_p, sc->t_reb);
   const RecArr<D, T> rec(B, 0);
@@ -1400,7 +1410,9 @@ __device__ __forceinline__ void viscous_slots(const Params& P, const DevBuffers&
 }
 
 template <int D, class T>
-__device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers& B, const KC<T>& k, DevScalars* sc, int i, int end, int stride, const ShiftTable* tab) {
+__device__ __forceinline__ void viscous_range(const Params& P, const DevBuffers& B, const KC<T>& k,
+                                              DevScalars* sc, int i, int end, int stride,
+                                              const ShiftTable* tab) {
   viscous_slots<D, T>(P, B, k, sc, StrideSlots{i, end, stride}, tab);
 }
 
@@ -1607,7 +1619,8 @@ __device__ __forceinline__ void pressure_range(const Params& P, const DevBuffers
 
 // kUnits: the slots in brick order (one tank, 3D mixed), else strided.
 template <int D, class T, bool kWallVel, bool kAccel = false, bool kUnits = false>
-__global__ void __launch_bounds__(256, kMinBlocksPres<D, T>) k_pressure(Params P, DevBuffers B, KC<T> k) {
+__global__ void __launch_bounds__(256, kMinBlocksPres<D, T>) k_pressure(Params P, DevBuffers B,
+                                                                         KC<T> k) {
   __shared__ ShiftTable tab;
   if constexpr (Local<T>::kLocal && !kShiftBits<D>) fill_shift_table(tab);
   if constexpr (kUnits)
@@ -1706,7 +1719,8 @@ __device__ __forceinline__ void density_relax_range(const Params& P, const DevBu
 // One tank: block 0 also publishes this step's velocity maximum for the next
 // step's schedule (a batch does that in its schedule kernel).
 template <int D, class T, bool kWallVel, bool kAccel = false, bool kUnits = false>
-__global__ void __launch_bounds__(256, kMinBlocksP<D, T>) k_density_relax(Params P, DevBuffers B, KC<T> k) {
+__global__ void __launch_bounds__(256, kMinBlocksP<D, T>) k_density_relax(Params P, DevBuffers B,
+                                                                          KC<T> k) {
   DevScalars* sc = B.sc;
   __shared__ ShiftTable tab;
   if constexpr (Local<T>::kLocal && !kShiftBits<D>) fill_shift_table(tab);
@@ -2023,8 +2037,8 @@ void enqueue_acoustic_t(const StageArgs& a, cudaStream_t s, cudaEvent_t* ev = nu
   if (accel)
     k_pressure<D, T, true, true><<<gl, L.block_loop, 0, s>>>(P, B, k);
   else if (wall_vel && units)
-    k_pressure<D, T, true, false, kU><<<one_wave(k_pressure<D, T, true, false, kU>, L), L.block_loop,
-                                        0, s>>>(P, B, k);
+    k_pressure<D, T, true, false, kU><<<one_wave(k_pressure<D, T, true, false, kU>, L),
+                                        L.block_loop, 0, s>>>(P, B, k);
   else if (wall_vel)
     k_pressure<D, T, true><<<gl, L.block_loop, 0, s>>>(P, B, k);
   else if (units)

@@ -94,8 +94,8 @@ def source_fingerprint() -> str:
 # depend on size at fixed h / dp), warp instructions by the list entries
 # (nearly all instructions are spent per entry).
 NCU_CAPTURES = {
-    ("pressure", "e957191bc427"): {"fluid": 643200, "dram_bytes": 294767360 + 22382592,
-                                   "warp_inst": 134538007, "list_entries_per_particle": None},
+    ("pressure", "3bb064232c63"): {"fluid": 643200, "dram_bytes": 294713088 + 22424832,
+                                   "warp_inst": 134546052, "list_entries_per_particle": None},
 }
 
 

@@ -65,8 +65,11 @@ typedef struct {
 } sph_material;
 
 /* Device memory provider.  alloc returns device memory of at least `bytes`
- * bytes usable on `stream` (NULL on failure: the call then returns
- * SPH_E_OOM); free releases a block obtained from alloc. */
+ * bytes usable on `stream`, aligned to 256 bytes as cudaMalloc's blocks are
+ * (the kernels read some arrays with 16- and 32-byte vector loads).  NULL on
+ * failure: the call then returns SPH_E_OOM; a block that is not so aligned
+ * is handed back to free and counts as a failure.  free releases a block
+ * obtained from alloc. */
 typedef struct {
   void* (*alloc)(size_t bytes, void* stream, void* user);
   void (*free)(void* ptr, size_t bytes, void* stream, void* user);

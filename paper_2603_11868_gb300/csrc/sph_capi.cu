@@ -111,6 +111,10 @@ void* dev_alloc(sph_ctx* c, size_t bytes, std::vector<Block>& list) {
   void* p = nullptr;
   if (c->has_alloc) {
     p = c->alloc.alloc(bytes, (void*)c->stream, c->alloc.user);
+    if (p && ((uintptr_t)p & 255u)) {  // unaligned: the vector loads would fault
+      c->alloc.free(p, bytes, (void*)c->stream, c->alloc.user);
+      p = nullptr;
+    }
   } else {
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
       cudaGetLastError();

@@ -40,6 +40,10 @@ struct DevMem {
     void* p = nullptr;
     if (has_alloc) {
       p = alloc.alloc(bytes, (void*)stream, alloc.user);
+      if (p && ((uintptr_t)p & 255u)) {  // unaligned: the vector loads would fault
+        alloc.free(p, bytes, (void*)stream, alloc.user);
+        p = nullptr;
+      }
     } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
       cudaGetLastError();
       p = nullptr;

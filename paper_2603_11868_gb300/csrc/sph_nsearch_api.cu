@@ -55,6 +55,10 @@ void* ns_alloc(sph_nsearch* s, size_t bytes, std::vector<sph_nsearch::Blk>& list
   void* p = nullptr;
   if (s->has_alloc) {
     p = s->alloc.alloc(bytes, (void*)s->stream, s->alloc.user);
+    if (p && ((uintptr_t)p & 255u)) {  // unaligned: the vector loads would fault
+      s->alloc.free(p, bytes, (void*)s->stream, s->alloc.user);
+      p = nullptr;
+    }
   } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;

@@ -90,3 +90,33 @@ def test_batch_allocation_failure_is_an_oom(sph):
                 sph.sph_batch_destroy(bb)
         assert e.value.code == sph.SPH_E_OOM, (limit, e.value)
         assert not a.live, limit
+
+
+def test_misaligned_allocator_block_is_refused(sph):
+    """Device blocks must be 256-byte aligned (the kernels use 16- and
+    32-byte vector loads on them): a block 16 bytes off is handed back to the
+    allocator's free and the call fails with SPH_E_OOM, leaking nothing."""
+    class Misaligned(sph.TorchAllocator):
+        def __init__(self):
+            super().__init__()
+            self.base = {}
+            self.n_alloc = 0
+
+        def _on_alloc(self, nbytes, stream, user):
+            p = super()._on_alloc(nbytes + 256, stream, user)
+            if not p:
+                return None
+            self.n_alloc += 1
+            q = int(p) + 16
+            self.base[q] = int(p)
+            return q
+
+        def _on_free(self, ptr, nbytes, stream, user):
+            super()._on_free(self.base.pop(int(ptr)), nbytes + 256, stream, user)
+
+    case = cases.dam_break_2d(dp=0.05)
+    a = Misaligned()
+    with pytest.raises(sph.SphError) as e:
+        _single(sph, case, a)
+    assert e.value.code == sph.SPH_E_OOM
+    assert a.n_alloc >= 1 and not a.base

@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -78,23 +79,33 @@ WALL_RECORD_BYTES_3D = 16  # one float4 per wall particle, read once per loop
 LIST_ENTRY_BYTES = {"pressure": 4, "density_relax": 4, "viscous": 4, "density_sum": 8}
 
 
+def code_only(text: str) -> str:
+    """C++ source with comments and whitespace removed: what a compiled kernel
+    depends on (string literals here hold no comment markers)."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return re.sub(r"\s+", "", text)
+
+
 def source_fingerprint() -> str:
+    """Fingerprint of the kernel sources' code (comments and layout ignored)."""
     h = hashlib.sha1()
     for f in ("sph_stages.cuh", "sph_nsearch.cu", "sph_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2603_11868_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2603_11868_gb300", "csrc", f)) as fh:
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:12]
 
 
 # Counters of one launch of the named stage from an ncu capture of a smaller
 # case of the same geometry and kernel (3D dam break at dp = 0.005, 643 200
-# fluid particles), keyed by the fingerprint of the kernel sources it was
-# taken on; a stale fingerprint reports them as null.  DRAM traffic is scaled
+# fluid particles), keyed by the fingerprint of the kernel sources' code it was
+# taken on (comments and layout ignored); a stale fingerprint reports them as
+# null.  DRAM traffic is scaled
 # to the bench's launch by the fluid count (traffic per particle does not
 # depend on size at fixed h / dp), warp instructions by the list entries
 # (nearly all instructions are spent per entry).
 NCU_CAPTURES = {
-    ("pressure", "3bb064232c63"): {"fluid": 643200, "dram_bytes": 294713088 + 22424832,
+    ("pressure", "5cdecf4501c5"): {"fluid": 643200, "dram_bytes": 294713088 + 22424832,
                                    "warp_inst": 134546052, "list_entries_per_particle": None},
 }
 

@@ -196,7 +196,7 @@ struct DevBuffers {
   // what the list build reads of every slot: Vec4<T> (x, y, z, b), its
   // record-frame position (2D: z = 0) and drift budget
   void* brec;
-  // processing order of the one-tank 3D mixed relaxation loops: the 32-slot
+  // processing order of the one-tank 3D mixed neighbour loops: the 32-slot
   // groups sorted by brick of 4 x 4 x 4 cells and split into `parts` equal
   // runs, each taken group by group by the warps of one multiprocessor (a
   // warp that finds its run done takes groups from the others)

@@ -594,13 +594,15 @@ __global__ void k_reorder(Params P, DevBuffers B, int gated) {
 }
 
 // ---------------------------------------------------------------------------
-// Processing order of the one-tank 3D mixed relaxation loops, made at every
-// rebuild: the 32-slot groups (a warp's slots and list block) sorted by the
-// brick of 4 x 4 x 4 cells that holds each group's first slot.  The warps of
-// one multiprocessor then walk neighbouring bricks together, so the records
-// they gather stay in its L1 longer than along the cell rows of the storage
-// order.  The order of the groups within a brick is left to the atomics: the
-// loops give the same results in any order.
+// Processing order of the one-tank 3D mixed neighbour loops (list build,
+// density summation, viscous force, pressure and density relaxation; the
+// neighbour-search benchmark's density pass too), made at every rebuild: the
+// 32-slot groups (a warp's slots and list block) sorted by the brick of
+// 2^kBrickLog2 cells per axis (4 x 4 x 4) that holds each group's first slot.
+// The warps of one multiprocessor then walk neighbouring bricks together, so
+// the records they gather stay in its L1 longer than along the cell rows of
+// the storage order.  The order of the groups within a brick is left to the
+// atomics: the loops give the same results in any order.
 __device__ __forceinline__ uint32_t brick_of(const Cell& c, const Params& P) {
   const int nbx = (P.nx + (1 << kBrickLog2X) - 1) >> kBrickLog2X;
   const int nby = (P.ny + (1 << kBrickLog2Y) - 1) >> kBrickLog2Y;
